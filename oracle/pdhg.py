@@ -1,0 +1,248 @@
+"""Oracle restarted Halpern PDHG for the SiPO LP (FP64, CPU, explicit sparse A).
+
+The paper solves the LP with a matrix-free primal-dual hybrid gradient method
+driven by the KKT conditions (Sec. 2.8, Sec. 6.1) and gives no further recipe.
+The readings implemented here (and by the GPU solver) are published methods:
+
+* The PDHG step T (Chambolle-Pock, primal first, primal extrapolation) on
+  min_x max_{lam>=0} c^T x + lam^T (G x - h), x = (y, u~, v~):
+      g      = A (lam_up - lam_lo)                         [Eq. 51]
+      y+     = max(0, y - tau_y g)        (tau_y = 0 on masked rays)
+      u+     = max(0, u - tau_u (c_u - sum_band lam_up))   [Eq. 48]
+      v+     = max(1, v - tau_v (c_v - sum_gel f~ lam_up)) [Eq. 49]
+      y_bar  = 2 y+ - y,  u_bar = 2 u+ - u,  v_bar = 2 v+ - v
+      d_bar  = A^T y_bar                                   [Eqs. 2-3]
+      lam_up+ = max(0, lam_up + sigma_up (d_bar - U(u_bar, v_bar)))
+      lam_lo+ = max(0, lam_lo + sigma_lo (L - d_bar))
+* Diagonal Pock-Chambolle preconditioning (alpha = 1): tau = eta / (omega *
+  column abs-sum of G), sigma = eta * omega / row abs-sum, eta = 0.99, with a
+  primal weight omega.
+* Reflected Halpern iteration with restarts (restarted Halpern PDHG, Lu & Yang
+  2024): z <- w (2 T(z) - z) + (1 - w) z0, w = (k+1)/(k+2), k counted from the
+  last restart point z0.
+* Every `check_every` iterations: the KKT error of T(z) in the unscaled
+  problem decides termination (relative primal residual, relative dual
+  residual and relative gap all <= tol); the fixed-point residual
+  r = ||z - T(z)|| (preconditioned norm weighted by omega) decides restarts:
+  sufficient decay r <= 0.2 r0, necessary decay r <= 0.8 r0 without progress
+  since the previous check, or an artificial restart when the epoch reaches
+  36% of all iterations.  A restart moves z and z0 to T(z) and updates omega by
+  log-smoothing (0.5) towards ||lam - lam0|| / ||x - x0|| (scaled norms).
+* Primal infeasibility (Secs. 2.7.1-2.7.2 treat an infeasible LP as a
+  diagnostic): at each check, the dual difference lam+ - lam0 since the last
+  restart is tested as a Farkas ray: its reduced costs G^T dlam must be
+  non-negative on every primal column, it must be non-negative, and its dual
+  objective must be positive; violations relative to the objective <= 1e-6.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .lp import LPData, kkt, metrics, up_bound
+from .operators import Operators
+
+OPTIMAL, PRIMAL_INFEASIBLE, DUAL_INFEASIBLE, ITER_LIMIT = 0, 1, 2, 3
+
+ETA = 0.99
+BETA_SUFFICIENT = 0.2
+BETA_NECESSARY = 0.8
+BETA_ARTIFICIAL = 0.36
+OMEGA_SMOOTHING = 0.5
+INFEAS_TOL = 1e-6
+
+
+class Preconditioner:
+    """Pock-Chambolle (alpha = 1) column and row abs-sums of the LP matrix G."""
+
+    def __init__(self, lp: LPData, ops: Operators):
+        band, gel = lp.band, lp.gel
+        g = ops.geo
+        ind = band.astype(np.float64) + 2.0 * gel.astype(np.float64)
+        col = ops.A(ind.reshape(g.vol_shape)).ravel()
+        self.col_y = np.where(lp.active, col, 0.0)
+        self.col_u = float(band.sum()) if lp.has_u else 0.0
+        self.col_v = float(np.sum(lp.ft[gel])) if lp.has_v else 0.0
+        row = ops.AT(lp.active.astype(np.float64).reshape(g.sino_shape)).ravel()
+        up = row.copy()
+        if lp.has_u:
+            up[band] += 1.0
+        if lp.has_v:
+            up[gel] += lp.ft[gel]
+        self.row_up = np.where(band | gel, up, 0.0)
+        self.row_lo = np.where(gel, row, 0.0)
+
+    @staticmethod
+    def inv(a):
+        out = np.zeros_like(a)
+        nz = a > 0
+        out[nz] = 1.0 / a[nz]
+        return out
+
+
+def _scaled_residuals(lp, pc, d, g, u, v, lam_up, lam_lo):
+    """Squared primal and dual residuals in the preconditioned space."""
+    band, gel = lp.band, lp.gel
+    U = up_bound(lp, u, v)
+    iu = Preconditioner.inv(pc.row_up)
+    il = Preconditioner.inv(pc.row_lo)
+    m = band | gel
+    rp2 = np.sum(np.maximum(d[m] - U[m], 0.0) ** 2 * iu[m])
+    rp2 += np.sum(np.maximum(lp.lower[gel] - d[gel], 0.0) ** 2 * il[gel])
+    ic = Preconditioner.inv(pc.col_y)
+    rd2 = np.sum(np.minimum(g[lp.active], 0.0) ** 2 * ic[lp.active])
+    if lp.has_u:
+        rd2 += min(lp.c_u - lam_up[band].sum(), 0.0) ** 2 / pc.col_u
+    if lp.has_v:
+        rd2 += min(lp.c_v - np.sum(lp.ft[gel] * lam_up[gel]), 0.0) ** 2 / pc.col_v
+    return rp2, rd2
+
+
+def _farkas(lp, pc, dq_g, dlam_up, dlam_lo):
+    """True if the dual difference is (approximately) a primal-infeasibility ray."""
+    band, gel = lp.band, lp.gel
+    obj = np.sum(lp.lower[gel] * dlam_lo[gel])
+    if lp.has_u:
+        ru = -dlam_up[band].sum()
+    else:
+        obj -= lp.band_rhs() * dlam_up[band].sum()
+        ru = 0.0
+    sgel = np.sum(lp.ft[gel] * dlam_up[gel])
+    if lp.has_v:
+        rv = -sgel
+        obj += max(rv, 0.0)
+    else:
+        obj -= np.sum(lp.upper[gel] * dlam_up[gel])
+        rv = 0.0
+    if not obj > 0:
+        return False
+    scale = 1.0 / obj
+    viol2 = np.sum(np.minimum(dq_g[lp.active], 0.0) ** 2)
+    viol2 += min(ru, 0.0) ** 2 + min(rv, 0.0) ** 2
+    viol2 += np.sum(np.minimum(dlam_up, 0.0) ** 2) + np.sum(np.minimum(dlam_lo, 0.0) ** 2)
+    return math.sqrt(viol2) * scale <= INFEAS_TOL
+
+
+def solve(lp: LPData, ops: Operators, kkt_tol=1e-4, max_iter=10000,
+          check_every=64, omega0=None, verbose=False, history=None):
+    """Run the restarted Halpern PDHG; returns a dict with status, T(z) and KKT data.
+
+    `iters` counts PDHG steps; the returned point is T(z) at the last check.
+    """
+    geo = ops.geo
+    pc = Preconditioner(lp, ops)
+    band, gel = lp.band, lp.gel
+    m_up = band | gel
+    S = lp.active.size
+    V = lp.labels.size
+    inv_col = Preconditioner.inv(pc.col_y)
+    inv_up = Preconditioner.inv(pc.row_up)
+    inv_lo = Preconditioner.inv(pc.row_lo)
+    if omega0 is None:
+        omega = initial_omega(lp, pc)
+    else:
+        omega = float(omega0)
+
+    def AT(s):
+        return ops.AT(s.reshape(geo.sino_shape)).ravel()
+
+    def A(vv):
+        return ops.A(vv.reshape(geo.vol_shape)).ravel()
+
+    y, u, v = np.zeros(S), 0.0, 1.0
+    lam_up, lam_lo = np.zeros(V), np.zeros(V)
+    y0, u0, v0, lam_up0, lam_lo0 = y.copy(), u, v, lam_up.copy(), lam_lo.copy()
+    g0 = np.zeros(S)
+    k_in = 0
+    r0 = None
+    r_prev = None
+    restarts = 0
+    k = 0
+    while True:
+        # one PDHG step T(z)
+        g = A(lam_up - lam_lo)
+        y_p = np.maximum(0.0, y - ETA * inv_col / omega * g)
+        S_band = lam_up[band].sum()
+        S_gel = np.sum(lp.ft[gel] * lam_up[gel])
+        u_p = max(0.0, u - ETA / (omega * pc.col_u) * (lp.c_u - S_band)) if lp.has_u else u
+        v_p = max(1.0, v - ETA / (omega * pc.col_v) * (lp.c_v - S_gel)) if lp.has_v else v
+        y_bar = 2.0 * y_p - y
+        d_bar = AT(y_bar)
+        U = up_bound(lp, 2.0 * u_p - u, 2.0 * v_p - v)
+        lam_up_p = np.where(m_up, np.maximum(0.0, lam_up + ETA * omega * inv_up * (d_bar - U)), 0.0)
+        lam_lo_p = np.where(gel, np.maximum(0.0, lam_lo + ETA * omega * inv_lo * (lp.lower - d_bar)), 0.0)
+        restart = False
+        if k % check_every == 0 or k == max_iter:
+            d_p = AT(y_p)
+            g_p = A(lam_up_p - lam_lo_p)
+            info = kkt(lp, d_p, g_p, u_p, v_p, lam_up_p, lam_lo_p)
+            if history is not None:
+                history.append(dict(k=k, omega=omega, restarts=restarts, **info))
+            if verbose:
+                print(f"k={k} kkt={info['kkt']:.3e} p={info['rel_primal']:.2e} "
+                      f"d={info['rel_dual']:.2e} gap={info['rel_gap']:.2e} "
+                      f"obj={info['pobj']:.6f} omega={omega:.3e}")
+            status = None
+            if (info["rel_primal"] <= kkt_tol and info["rel_dual"] <= kkt_tol
+                    and info["rel_gap"] <= kkt_tol):
+                status = OPTIMAL
+            elif k > 0 and _farkas(lp, pc, g_p - g0, lam_up_p - lam_up0, lam_lo_p - lam_lo0):
+                status = PRIMAL_INFEASIBLE
+            elif k == max_iter:
+                status = ITER_LIMIT
+            if status is not None:
+                out = dict(status=status, iters=k, y=y_p, u=u_p, v=v_p, lam_up=lam_up_p,
+                           lam_lo=lam_lo_p, d=d_p, g=g_p, omega=omega, restarts=restarts,
+                           info=info, obj=info["pobj"])
+                out["metrics"] = metrics(lp, d_p)
+                return out
+            dx2 = np.sum(pc.col_y * (y - y_p) ** 2) + pc.col_u * (u - u_p) ** 2 \
+                + pc.col_v * (v - v_p) ** 2
+            dl2 = np.sum(pc.row_up * (lam_up - lam_up_p) ** 2) \
+                + np.sum(pc.row_lo * (lam_lo - lam_lo_p) ** 2)
+            r = math.sqrt(omega * dx2 + dl2 / omega)
+            if r0 is None:
+                r0 = r
+            elif (r <= BETA_SUFFICIENT * r0 or (r <= BETA_NECESSARY * r0 and r > r_prev)
+                  or k_in >= BETA_ARTIFICIAL * k):
+                restart = True
+            r_prev = r
+        if restart:
+            ex2 = np.sum(pc.col_y * (y_p - y0) ** 2) + pc.col_u * (u_p - u0) ** 2 \
+                + pc.col_v * (v_p - v0) ** 2
+            el2 = np.sum(pc.row_up * (lam_up_p - lam_up0) ** 2) \
+                + np.sum(pc.row_lo * (lam_lo_p - lam_lo0) ** 2)
+            if ex2 > 1e-30 and el2 > 1e-30:
+                omega = math.exp(OMEGA_SMOOTHING * 0.5 * math.log(el2 / ex2)
+                                 + (1.0 - OMEGA_SMOOTHING) * math.log(omega))
+            y, u, v, lam_up, lam_lo = y_p, u_p, v_p, lam_up_p, lam_lo_p
+            y0, u0, v0 = y_p.copy(), u_p, v_p
+            lam_up0, lam_lo0 = lam_up_p.copy(), lam_lo_p.copy()
+            g0 = g_p
+            k_in = 0
+            r0 = r
+            r_prev = r
+            restarts += 1
+        else:
+            w = (k_in + 1.0) / (k_in + 2.0)
+            y = w * y_bar + (1.0 - w) * y0
+            u = w * (2.0 * u_p - u) + (1.0 - w) * u0
+            v = w * (2.0 * v_p - v) + (1.0 - w) * v0
+            lam_up = w * (2.0 * lam_up_p - lam_up) + (1.0 - w) * lam_up0
+            lam_lo = w * (2.0 * lam_lo_p - lam_lo) + (1.0 - w) * lam_lo0
+            k_in += 1
+        k += 1
+
+
+def initial_omega(lp: LPData, pc: Preconditioner) -> float:
+    """omega0 = ||c|| / ||h|| in the preconditioned space (1 if either is 0)."""
+    gel = lp.gel
+    m_up = lp.band | gel
+    inv_up = Preconditioner.inv(pc.row_up)
+    inv_lo = Preconditioner.inv(pc.row_lo)
+    c_hat2 = (lp.c_u ** 2 / pc.col_u if lp.has_u else 0.0) + \
+             (lp.c_v ** 2 / pc.col_v if lp.has_v else 0.0)
+    U0 = up_bound(lp, 0.0, 0.0)
+    h_hat2 = np.sum(U0[m_up] ** 2 * inv_up[m_up]) + np.sum(lp.lower[gel] ** 2 * inv_lo[gel])
+    return math.sqrt(c_hat2 / h_hat2) if c_hat2 > 0 and h_hat2 > 0 else 1.0

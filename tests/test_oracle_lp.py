@@ -1,0 +1,219 @@
+"""Pins for the oracle LP and PDHG (CPU only).
+
+The PDHG oracle is checked against exact LP optima (a dense simplex with
+Bland's rule, and scipy's HiGHS as an independent library routine), against
+the KKT stationarity conditions of Sec. 6.1 (Eqs. 48-49), against the exactness
+of the Charnes-Cooper transform (Sec. 2.6.2: the LP optimum equals the
+fractional objective of its solution), against scale invariance (Secs. 2.5 and
+2.6.2) and against the closed-form post-scaling factor (Eq. 27).
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.optimize import linprog, minimize_scalar
+
+from oracle import pdhg, simplex
+from oracle.lp import (BAND, CASE1, CASE2, EXT, GEL, GENERAL, CaseParams, build_lp,
+                       metrics, partition)
+from oracle.operators import Geometry
+from synthetic.targets import discs_2d, uniform_angles
+
+TINY = [
+    (GENERAL, {}),
+    (CASE1, dict(tol_lo=0.1, tol_hi=0.1)),
+    (CASE2, dict(inhibit_ratio=0.6)),
+]
+
+
+def _tiny(case, extra, n=10, na=8, nd=15, seed=3, scale=1.0):
+    tgt = discs_2d(n, n_discs=1, r_range=(2.0, 3.0), container_radius=4.0, seed=seed) * scale
+    geo = Geometry(n, n, 1, uniform_angles(na), nd)
+    return build_lp(geo, tgt, CaseParams(case=case, band_width=2, **extra))
+
+
+@pytest.fixture(scope="module")
+def tiny_solutions():
+    out = {}
+    for case, extra in TINY:
+        lp, ops = _tiny(case, extra)
+        st, obj, _ = simplex.solve_dense(lp, ops)
+        res = pdhg.solve(lp, ops, kkt_tol=1e-10, max_iter=60000)
+        out[case] = (lp, ops, st, obj, res)
+    return out
+
+
+def test_partition_single_voxel():
+    f = np.zeros((9, 9, 1))
+    f[4, 4, 0] = 1.0
+    geo = Geometry(9, 9, 1, np.zeros(1), 9)
+    lab = partition(geo, f, 2)
+    assert (lab == GEL).sum() == 1
+    # lattice points with 0 < a^2 + b^2 <= 4
+    assert (lab == BAND).sum() == 12
+    assert (partition(geo, f, 0) == BAND).sum() == 0
+    assert (partition(geo, f, -1) == BAND).sum() == 80
+    geo_k = Geometry(9, 9, 1, np.zeros(1), 9, psf_sigma=(0.25, 0.25, 0.0))  # radius 1
+    assert (partition(geo_k, f, 0) == BAND).sum() == 8
+    geo_v = Geometry(9, 9, 1, np.zeros(1), 9, vial_radius=1.2)
+    lab_v = partition(geo_v, f, 2)
+    assert (lab_v == BAND).sum() == 4 and (lab_v == EXT).sum() == 76
+
+
+@pytest.mark.parametrize("case", [GENERAL, CASE1, CASE2])
+def test_pdhg_matches_dense_simplex(tiny_solutions, case):
+    lp, ops, st, obj, res = tiny_solutions[case]
+    assert st == "optimal"
+    assert res["status"] == pdhg.OPTIMAL
+    assert abs(res["obj"] - obj) <= 1e-7 * abs(obj)
+
+
+@pytest.mark.parametrize("case", [GENERAL, CASE1, CASE2])
+def test_kkt_stationarity_and_cct_exactness(tiny_solutions, case):
+    """Eqs. 48-49 at the optimum; the recovered scale s = min_gel(d / f~) = 1 (t = 1/s,
+    Eq. 18) and the fractional objective of y* equals the LP objective (Sec. 2.6.2)."""
+    lp, ops, st, obj, res = tiny_solutions[case]
+    info, m = res["info"], res["metrics"]
+    # with the implied bounds u~ >= 0, v~ >= 1 a bound multiplier takes up the
+    # slack when the bound is active; otherwise Eqs. 48-49 hold as printed
+    if lp.has_u:
+        if res["u"] > 1e-6:
+            assert abs(info["S_band"] - lp.c_u) < 1e-6
+        else:
+            assert info["S_band"] <= lp.c_u + 1e-6
+    if lp.has_v:
+        if res["v"] > 1.0 + 1e-6:
+            assert abs(info["S_gel"] - lp.c_v) < 1e-6
+        else:
+            assert info["S_gel"] <= lp.c_v + 1e-6
+    assert abs(m["s"] - 1.0) < 1e-6
+    frac = 0.0
+    if lp.has_u:
+        frac += lp.c_u * m["band_max"]
+    if lp.has_v:
+        frac += lp.c_v * m["gel_max_ratio"]
+    if not lp.has_u and not lp.has_v:
+        pytest.skip("no objective")
+    assert abs(frac - obj) <= 1e-6 * abs(obj)
+    if case == CASE2:
+        assert abs(m["dtvr_f"] - obj) <= 1e-6 * obj      # DTVR(y*) = v~* when min ratio = 1
+
+
+def test_infeasible_case2_reported_by_both():
+    lp, ops = _tiny(CASE2, dict(inhibit_ratio=0.3))
+    st, _, _ = simplex.solve_dense(lp, ops)
+    assert st == "infeasible"
+    res = pdhg.solve(lp, ops, kkt_tol=1e-9, max_iter=20000)
+    assert res["status"] == pdhg.PRIMAL_INFEASIBLE
+
+
+def _highs(lp, ops):
+    act = np.flatnonzero(lp.active)
+    M = ops.PT[:, act]
+    band, gel = np.flatnonzero(lp.band), np.flatnonzero(lp.gel)
+    nb, ng, ny = band.size, gel.size, act.size
+    ucol = sp.csr_matrix((-np.ones(nb) if lp.has_u else np.zeros(nb),
+                          (np.arange(nb), np.zeros(nb, int))), shape=(nb, 1))
+    vcol = sp.csr_matrix((-lp.ft[gel] if lp.has_v else np.zeros(ng),
+                          (np.arange(ng), np.zeros(ng, int))), shape=(ng, 1))
+    zb, zg = sp.csr_matrix((nb, 1)), sp.csr_matrix((ng, 1))
+    G = sp.vstack([sp.hstack([M[band], ucol, zb]), sp.hstack([M[gel], zg, vcol]),
+                   sp.hstack([-M[gel], zg, zg])]).tocsr()
+    h = np.concatenate([np.zeros(nb) if lp.has_u else np.ones(nb),
+                        np.zeros(ng) if lp.has_v else lp.upper[gel], -lp.lower[gel]])
+    c = np.zeros(ny + 2)
+    c[ny] = lp.c_u if lp.has_u else 0.0
+    c[ny + 1] = lp.c_v if lp.has_v else 0.0
+    bounds = [(0, None)] * ny + [(None, None) if lp.has_u else (0, 0),
+                                 (None, None) if lp.has_v else (0, 0)]
+    res = linprog(c, A_ub=G, b_ub=h, bounds=bounds, method="highs")
+    return res
+
+
+@pytest.mark.parametrize("case,extra", [(CASE1, dict(tol_lo=0.05, tol_hi=0.05)),
+                                        (CASE2, dict(inhibit_ratio=0.7))])
+def test_pdhg_matches_highs_on_small_slice(case, extra):
+    tgt = discs_2d(24, n_discs=2, r_range=(3.0, 5.0), container_radius=10.0, seed=11)
+    geo = Geometry(24, 24, 1, uniform_angles(32), 35)
+    lp, ops = build_lp(geo, tgt, CaseParams(case=case, band_width=3, **extra))
+    ref = _highs(lp, ops)
+    assert ref.status == 0
+    res = pdhg.solve(lp, ops, kkt_tol=1e-8, max_iter=40000)
+    assert res["status"] == pdhg.OPTIMAL
+    assert abs(res["obj"] - ref.fun) <= 1e-6 * abs(ref.fun)
+
+
+def test_scale_invariance_bitwise_and_general():
+    """f_T -> 2^k f_T leaves the normalised LP and the iterates bitwise unchanged;
+    a general factor leaves the optimum unchanged (Sec. 2.5, Eq. 18)."""
+    for case, extra in TINY:
+        lp1, ops1 = _tiny(case, extra)
+        lp2, ops2 = _tiny(case, extra, scale=8.0)
+        for name in ("ft", "lower", "upper", "labels", "active"):
+            assert np.array_equal(getattr(lp1, name), getattr(lp2, name)), name
+        r1 = pdhg.solve(lp1, ops1, kkt_tol=0.0, max_iter=300)
+        r2 = pdhg.solve(lp2, ops2, kkt_tol=0.0, max_iter=300)
+        assert np.array_equal(r1["y"], r2["y"])
+        assert r1["obj"] == r2["obj"]
+    lp3, ops3 = _tiny(CASE2, dict(inhibit_ratio=0.6), scale=3.7)
+    r3 = pdhg.solve(lp3, ops3, kkt_tol=1e-10, max_iter=60000)
+    lp1, ops1 = _tiny(CASE2, dict(inhibit_ratio=0.6))
+    r1 = pdhg.solve(lp1, ops1, kkt_tol=1e-10, max_iter=60000)
+    assert abs(r3["obj"] - r1["obj"]) < 1e-8
+
+
+def test_metrics_zero_homogeneous(tiny_solutions):
+    lp, ops, _, _, res = tiny_solutions[GENERAL]
+    m1 = metrics(lp, res["d"])
+    m2 = metrics(lp, 7.3 * res["d"])
+    for key in ("dtvr_f", "dsr", "psr_f"):
+        assert abs(m1[key] - m2[key]) <= 1e-12 * abs(m1[key])
+
+
+def test_post_scaling_closed_form(tiny_solutions):
+    """Eq. 27: alpha* = <f~*, f_T> / <f~*, f~*> minimises Phi_f; Case 2 gives alpha* <= f_crit."""
+    for case in (GENERAL, CASE2):
+        lp, ops, _, _, res = tiny_solutions[case]
+        d = res["d"]
+        gel = lp.gel
+        phi = lambda a: np.sum((a * d[gel] - lp.f_T[gel]) ** 2)
+        brute = minimize_scalar(phi, bounds=(1e-6, 10.0), method="bounded",
+                                options=dict(xatol=1e-12)).x
+        assert abs(res["metrics"]["alpha"] - brute) < 1e-6
+        if case == CASE2:
+            assert res["metrics"]["alpha"] <= lp.f_crit * (1 + 1e-9)
+
+
+def test_case1_objective_monotone_in_tolerance():
+    """Widening the Case-1 tolerance grows the feasible set, so u~*(delta) cannot increase."""
+    objs = []
+    for delta in (0.05, 0.1, 0.2):
+        lp, ops = _tiny(CASE1, dict(tol_lo=delta, tol_hi=delta))
+        st, obj, _ = simplex.solve_dense(lp, ops)
+        assert st == "optimal"
+        objs.append(obj)
+    assert objs[0] >= objs[1] - 1e-12 >= objs[2] - 2e-12
+
+
+def test_planted_sign_error_is_caught(monkeypatch):
+    """A sign slip in the detector coordinate (y sin -> -y sin) breaks the disc pin."""
+    import oracle.operators as O
+    orig = O.detector_coordinate
+
+    def flipped(x, y, c, s, off, precision="f64"):
+        return orig(x, -y, c, s, off, precision)
+
+    monkeypatch.setattr(O, "detector_coordinate", flipped)
+    n, r = 64, 14
+    cx, cy = 0.07 * n, -0.05 * n
+    c = np.arange(n) - (n - 1) / 2
+    Y, X = np.meshgrid(c, c, indexing="ij")
+    f = ((X - cx) ** 2 + (Y - cy) ** 2 <= r * r).astype(float)
+    th = 1.0
+    geo = Geometry(n, n, 1, np.array([th]), 93)
+    p = O.Operators(geo).project_raw(f[:, :, None])[0, :, 0]
+    s = np.arange(93) - 46.0
+    s0 = cx * math.cos(th) + cy * math.sin(th)
+    ana = 2 * np.sqrt(np.maximum(r * r - (s - s0) ** 2, 0))
+    assert np.linalg.norm(p - ana) / np.linalg.norm(ana) > 0.05
