@@ -1,0 +1,373 @@
+"""Benchmark of the SiPO PDHG solve on GB300.
+
+One step = one PDHG iteration of the restarted Halpern PDHG (projection with
+fused primal update, backprojection with fused dual update, FP64 scalar step;
+every check_every-th iteration also the KKT / restart evaluation).
+
+Default workload: 256^3 voxels, 360 parallel-beam views over [0, pi), 256x256
+detector, FP32 iterates, Case 2 (inhibition ratio 0.8), seeded CSG target in a
+radius-120 vial (band width 10).  The working set (~1.5 GB) exceeds L2, so no
+flush is needed between iterations.
+
+`value` is PDHG iterations per second over all ranks with inputs resident in
+HBM; `e2e` is the same through the C ABI with the target read from pinned host
+memory and y* written back to pinned host memory, context creation included.
+Extra keys: time to relative KKT 1e-4, the per-phase breakdown, the roofline
+of the dominant kernel, the CPU oracle baseline, sampled SM clocks.
+
+Multi-GPU (torchrun): every rank solves an independent replica (the LP does
+not need an exchange across problems); value = total iterations / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PDHG iter/s and time-to-1e-4 KKT at 256³×360 views; projector GB/s vs HBM"
+FP32_LANES_PER_SM = 128
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+# ------------------------------------------------------------- distributed
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def init_dist(world, backend):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def max_over_ranks(x: float, dist, device=None) -> float:
+    """Maximum of a per-rank float over all ranks (identity without a group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(base: int, rank: int) -> int:
+    """Each rank's independent replica uses the same seeded instance."""
+    return base
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while active."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int = 0, period_ms: int = 200):
+        self.index = index
+        self.period_ms = period_ms
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", f"-lms={self.period_ms}"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- workload
+def make_workload(name: str, seed_offset: int = 0):
+    from synthetic.targets import workload
+    return workload(name)
+
+
+def geometry_dict(wl):
+    return dict(nx=wl.n, ny=wl.n, nz=wl.nz, angles=wl.angles, n_det=wl.n_det,
+                vial_radius=wl.vial_radius, mu=wl.mu, psf_sigma=wl.psf_sigma,
+                psf_trunc=wl.psf_trunc)
+
+
+def case_dict(wl):
+    return dict(kase=wl.case, w1=wl.w1, w2=wl.w2, tol_lo=wl.tol_lo, tol_hi=wl.tol_hi,
+                inhibit_ratio=wl.inhibit_ratio, band_width=wl.band_width)
+
+
+def workload_config(wl, storage_name):
+    return {"workload": f"{wl.name}: {wl.n}x{wl.n}x{wl.nz} voxels, {wl.n_angles} views over [0,pi), "
+                        f"{wl.n_det}x{wl.nz} detector, case {wl.case}, vial R={wl.vial_radius:g}, "
+                        f"mu={wl.mu:g}, psf sigma={tuple(wl.psf_sigma)}",
+            "n": wl.n, "n_angles": wl.n_angles, "storage": storage_name,
+            "case": wl.case, "inhibit_ratio": wl.inhibit_ratio, "band_width": wl.band_width,
+            "l2_policy": "working set > L2 (no flush)", "target": "seeded CSG (synthetic)"}
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_iteration_rate(wl, max_seconds: float = 20.0, nz_sample: int = 2):
+    """Oracle PDHG iterations on `nz_sample` middle z-slices of the workload
+    (the operator is slice-separable, so per-iteration work scales with nz),
+    scaled to the full nz.  Returns (iter/s at full size, sample description)."""
+    from oracle import pdhg
+    from oracle.lp import CaseParams, build_lp
+    from oracle.operators import Geometry
+    z0 = wl.nz // 2 - nz_sample // 2
+    tgt = np.ascontiguousarray(wl.target[:, :, z0:z0 + nz_sample])
+    geo = Geometry(wl.n, wl.n, nz_sample, wl.angles, wl.n_det, vial_radius=wl.vial_radius,
+                   mu=wl.mu, psf_sigma=wl.psf_sigma, psf_trunc=wl.psf_trunc)
+    cp = CaseParams(case=wl.case, w1=wl.w1, w2=wl.w2, tol_lo=wl.tol_lo, tol_hi=wl.tol_hi,
+                    inhibit_ratio=wl.inhibit_ratio, band_width=wl.band_width)
+    t0 = time.perf_counter()
+    lp, ops = build_lp(geo, tgt, cp)
+    t_setup = time.perf_counter() - t0
+    iters = 2
+    while True:
+        t0 = time.perf_counter()
+        pdhg.solve(lp, ops, kkt_tol=0.0, max_iter=iters, check_every=10 ** 9)
+        dt = time.perf_counter() - t0
+        if dt * 2 > max_seconds or iters >= 64:
+            break
+        iters *= 2
+    per_iter = dt / iters
+    full = per_iter * wl.nz / nz_sample
+    desc = (f"oracle restarted Halpern PDHG (numpy/scipy FP64, explicit sparse P^T) on {nz_sample} of "
+            f"{wl.nz} z-slices for {iters} iterations ({dt:.1f} s, setup {t_setup:.1f} s), "
+            f"per-iteration time scaled by nz/{nz_sample}")
+    return 1.0 / full, desc, per_iter
+
+
+def cpu_baseline(wl, max_seconds=20.0):
+    rate, desc, _ = oracle_iteration_rate(wl, max_seconds)
+    return {"value": rate, "unit": "iter/s", "cores": 1, "kind": "oracle", "sample": desc}
+
+
+# ---------------------------------------------------------------- GPU arm
+def needed_units(sipo, ctx, wl):
+    """Voxel-angle pairs the solver's backprojector processes per launch and rays
+    its projector processes (columns with any band/gel voxel; active rays)."""
+    lab = np.empty((wl.n, wl.n, wl.nz), np.uint8)
+    act = np.empty((wl.n_angles, wl.n_det, wl.nz), np.uint8)
+    sipo.sipo_get_array(ctx, 0, lab)
+    sipo.sipo_get_array(ctx, 1, act)
+    need_cols = int(np.count_nonzero((lab != 0).any(axis=2)))
+    act_cols = int(np.count_nonzero(act.any(axis=2)))
+    return need_cols, act_cols
+
+
+def run_gpu(args, dist, rank, world, device):
+    import torch
+    import paper_2604_08997_gb300 as sipo
+    sipo.build()
+    storage = {"f32": sipo.SIPO_F32, "bf16": sipo.SIPO_BF16, "f64": sipo.SIPO_F64}[args.storage]
+    wl = make_workload(args.workload)
+    geo, cp = geometry_dict(wl), case_dict(wl)
+    tgt = torch.from_numpy(wl.target).to(device)
+    tol = dict(storage=storage, kkt_tol=0.0, max_iter=args.warmup, check_every=args.check_every)
+    ctx = sipo.sipo_create(geo, tgt, cp, tol)
+    sipo.sipo_solve(ctx)                      # W warm-up iterations (graph captured here)
+    sipo.sipo_set_tolerances(ctx, 0.0, args.steps, args.check_every)
+    torch.cuda.synchronize()
+    n0 = sipo.sipo_kernel_launch_count()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clocks:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = sipo.sipo_solve(ctx)            # exactly K iterations (kkt_tol = 0)
+        torch.cuda.synchronize()
+        elapsed = time.perf_counter() - t0
+        if dist is not None:
+            dist.barrier()
+    launches = sipo.sipo_kernel_launch_count() - n0
+    t_max = max_over_ranks(elapsed, dist, device)
+    iters_total = res["iters"] * world
+    value = iters_total / t_max
+    # per-phase breakdown with CUDA events on the solver stream
+    phases = sipo.sipo_profile(ctx, args.profile_iters)
+    normal = sum(v for k, v in phases.items() if k != "check_step")
+    per_iter_ms = (normal * (args.check_every - 1) + phases["check_step"]) / args.check_every
+    # roofline of the dominant kernel
+    need_cols, act_cols = needed_units(sipo, ctx, wl)
+    bp_ms = phases["backproject"]
+    fp_ms = phases["project_primal"]
+    dom, dom_ms = ("backproject+dual", bp_ms) if bp_ms >= fp_ms else ("project+primal", fp_ms)
+    pairs_bp = need_cols * wl.nz * wl.n_angles           # voxel-angle pairs
+    flop_bp = 4.0 * pairs_bp                               # 2 taps x FMA
+    # projector: every active column gathers ~2 taps per voxel it crosses
+    flop = flop_bp if dom.startswith("back") else 4.0 * pairs_bp
+    bytes_alg_bp = (wl.n_angles * wl.n_det * wl.nz * 4 + need_cols * wl.nz * (4 * 4 + 4 + 1 + 4 * 4))
+    clk = clocks.summary()
+    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flop / (dom_ms * 1e-3) / 1e12
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                               f"{SM_MAX_MHZ:.0f} MHz",
+                "units_per_launch": pairs_bp, "flop_per_unit": 4,
+                "avg_launch_ms": dom_ms,
+                "hbm_gbs_algorithmic": bytes_alg_bp / (bp_ms * 1e-3) / 1e9,
+                "hbm_frac_of_measured": bytes_alg_bp / (bp_ms * 1e-3) / 1e9 / hbm}
+    # time to relative KKT 1e-4
+    kkt_info = None
+    if args.kkt_iters > 0:
+        sipo.sipo_set_tolerances(ctx, 1e-4, args.kkt_iters, args.check_every)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rk = sipo.sipo_solve(ctx)
+        torch.cuda.synchronize()
+        tk = time.perf_counter() - t0
+        kkt_info = {"seconds": tk, "iters": rk["iters"], "status": rk["status_name"],
+                    "kkt": rk["kkt"], "objective": rk["pobj"], "restarts": rk["restarts"],
+                    "dtvr_f": rk["dtvr_f"], "psr_f": rk["psr_f"]}
+    # end to end through the C ABI from pinned host memory
+    tgt_h = torch.from_numpy(wl.target).pin_memory()
+    y_h = torch.empty((wl.n_angles, wl.n_det, wl.nz), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx_e = sipo.sipo_create(geo, tgt_h, cp, dict(tol, max_iter=args.steps))
+    re = sipo.sipo_solve(ctx_e, y_h)
+    sipo.sipo_destroy(ctx_e)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    te_max = max_over_ranks(te, dist, device)
+    e2e = {"value": re["iters"] * world / te_max, "unit": "iter/s",
+           "h2d_bytes_per_step": int(wl.target.nbytes) // max(1, re["iters"]),
+           "d2h_bytes_per_step": int(y_h.numel() * 4) // max(1, re["iters"]),
+           "includes": "sipo_create (H2D target + device setup) + sipo_solve + D2H y*"}
+    out = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world,
+           "steps": int(res["iters"]), "warmup": args.warmup,
+           "ms_per_step": t_max * 1e3 / max(1, res["iters"]), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+           "config": workload_config(wl, args.storage), "e2e": e2e, "gpu_launches": int(launches),
+           "roofline": roofline, "clocks": clk, "time_to_kkt_1e-4": kkt_info,
+           "phases_ms": phases, "model_iter_ms": per_iter_ms,
+           "solver": {"status": res["status_name"], "kkt": res["kkt"], "restarts": res["restarts"],
+                      "check_every": args.check_every, "need_columns": need_cols,
+                      "active_columns": act_cols}}
+    sipo.sipo_destroy(ctx)
+    return out, wl
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=256)
+    p.add_argument("--warmup", type=int, default=16)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--workload", default="csg256")
+    p.add_argument("--storage", default="f32", choices=["f32", "bf16", "f64"])
+    p.add_argument("--check-every", type=int, default=64)
+    p.add_argument("--profile-iters", type=int, default=8)
+    p.add_argument("--kkt-iters", type=int, default=6000)
+    p.add_argument("--cpu-seconds", type=float, default=20.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    args = p.parse_args(argv)
+    if args.warmup < 3:
+        p.error("--warmup must be >= 3")
+    world, rank, local = dist_env()
+
+    if args.impl == "reference":
+        # the CPU oracle is the reference implementation of this path
+        if rank != 0:
+            return 0
+        wl = make_workload(args.workload)
+        t0 = time.perf_counter()
+        rate, desc, per_iter = oracle_iteration_rate(wl, args.cpu_seconds)
+        out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "iter/s",
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": 1e3 / rate, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": workload_config(wl, "f64"),
+               "cpu_baseline": {"value": rate, "unit": "iter/s", "cores": 1, "kind": "oracle",
+                                "sample": desc},
+               "e2e": {"value": rate, "unit": "iter/s", "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": 0},
+               "wall_s": time.perf_counter() - t0}
+        print(json.dumps(out), flush=True)
+        return 0
+
+    import torch
+    if not torch.cuda.is_available():
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    dist = init_dist(world, "nccl")
+    out, wl = run_gpu(args, dist, rank, world, device)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

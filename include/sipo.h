@@ -1,0 +1,238 @@
+/*
+ * sipo.h -- C ABI of the GB300 (sm_103a) SiPO projection-LP solver.
+ *
+ * SiPO (scale-invariant projection optimisation for tomographic volumetric
+ * additive manufacturing) designs a projection sinogram y >= 0 by solving a
+ * linear program over the linear dose model f = A^T y, A^T = K P^T (Sec. 2.3,
+ * Eqs. 2-3).  This library implements the matrix-free primal-dual hybrid
+ * gradient (PDHG) solve of that LP (Sec. 2.8, KKT conditions of Sec. 6.1) for
+ * the general form (Eqs. 19-24), Case 1 (Eqs. 32-37) and Case 2 (Eqs. 40-45),
+ * plus the forward and adjoint operators themselves.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Layouts: a volume is [ny][nx][nz] and a sinogram [n_angles][n_det][nz],
+ *   C-contiguous with z (the rotation axis) fastest.  Voxel centres sit at
+ *   (i - (n-1)/2); angle k has detector coordinate
+ *   u = x cos(theta_k) + y sin(theta_k) + (n_det-1)/2, and P^T interpolates
+ *   linearly between bins floor(u) and floor(u)+1; P is its exact transpose.
+ * Attenuation (vial radius R > 0, coefficient mu): the tap from voxel (x,y) to
+ *   bin j is weighted by exp(-mu (t + sqrt(R^2 - s_j^2))), t = -x sin + y cos,
+ *   s_j = j - (n_det-1)/2; 0 when |s_j| > R; voxels with x^2+y^2 > R^2 are
+ *   outside the operator.
+ * PSF K: separable Gaussian per axis, sigma = (sigma_x, sigma_y, sigma_z),
+ *   radius R_a = ceil(trunc * sigma_a) fixed at creation, taps normalised to
+ *   sum 1, zero padding (so K is symmetric); sigma_a = 0 is the identity.
+ * Return codes: every function returns SIPO_OK (0) or a negative SIPO_ERR_*;
+ *   the thread-local message of the last failure is sipo_last_error().
+ *   Failures leave the context usable unless the code is SIPO_ERR_CUDA from
+ *   a sticky device error.
+ * Streams: a NULL stream means the context's own stream.  Calls that take a
+ *   stream enqueue their work on it and return without synchronising unless
+ *   stated.
+ * Ownership: the library never frees caller memory; device buffers passed in
+ *   are caller-owned and must stay valid until the enqueued work completes.
+ */
+#ifndef SIPO_H
+#define SIPO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define SIPO_OK 0
+#define SIPO_ERR_INVALID_ARG (-1)
+#define SIPO_ERR_CUDA (-2)
+#define SIPO_ERR_OOM (-3)
+#define SIPO_ERR_TIMEOUT (-4)
+#define SIPO_ERR_NUMERIC (-5)
+#define SIPO_ERR_UNSUPPORTED (-6)
+
+/* solve status (sipo_result.status); infeasibility is a result, not an error
+ * (Secs. 2.7.1 and 2.7.2 read an infeasible LP as a process diagnostic) */
+#define SIPO_OPTIMAL 0
+#define SIPO_PRIMAL_INFEASIBLE 1
+#define SIPO_DUAL_INFEASIBLE 2
+#define SIPO_ITER_LIMIT 3
+
+/* LP forms */
+#define SIPO_GENERAL 0 /* Eqs. 19-24: min w1 u~ + w2 v~ */
+#define SIPO_CASE1 1   /* Eqs. 32-37: min u~ under dose tolerances (Eqs. 29-31) */
+#define SIPO_CASE2 2   /* Eqs. 40-45: min v~ under the inhibition bound (Eq. 39) */
+
+/* element types */
+#define SIPO_F32 0
+#define SIPO_F64 1
+#define SIPO_BF16 2
+
+/* where a pointer lives */
+#define SIPO_HOST 0
+#define SIPO_DEVICE 1
+
+/* region labels (Sec. 2.2, Fig. 2) */
+#define SIPO_EXT 0
+#define SIPO_BAND 1
+#define SIPO_GEL 2
+
+typedef struct sipo_ctx sipo_ctx;
+
+/* Geometry (Secs. 2.2-2.3).  `angles` is a host array of n_angles radians,
+ * copied at creation.  vial_radius <= 0 means no vial (then mu must be 0).
+ * psf_sigma[a] = 0 disables the PSF along axis a (x, y, z order); psf_trunc
+ * is the truncation in sigmas (4 if <= 0). */
+typedef struct sipo_geometry {
+  int nx, ny, nz;
+  int n_angles;
+  const double *angles;
+  int n_det;
+  double vial_radius;
+  double mu;
+  double psf_sigma[3];
+  double psf_trunc;
+} sipo_geometry;
+
+/* LP form and its data.  General: weights w1, w2 (Eq. 19).  Case 1: dose
+ * tolerances f_L = (1 - tol_lo) f_T, f_U = (1 + tol_hi) f_T (Eq. 29),
+ * f_crit = min_gel f_L (Eq. 30).  Case 2: f_crit = inhibit_ratio *
+ * min_gel f_T (the inhibition threshold of Sec. 2.7.2).  band_width: the band
+ * is the non-gel voxels within Euclidean distance <= band_width of the gel,
+ * plus the support of K f_T (Sec. 2.2); band_width < 0 means band-free
+ * (every non-gel voxel inside the vial is band). */
+typedef struct sipo_case_params {
+  int kase;
+  double w1, w2;
+  double tol_lo, tol_hi;
+  double inhibit_ratio;
+  int band_width;
+} sipo_case_params;
+
+/* Solver controls.  kkt_tol: relative KKT tolerance (primal, dual and gap
+ * each <= kkt_tol; 0 runs to max_iter).  check_every: iterations between KKT
+ * and restart checks (64 if <= 0).  storage: element type of the iterates
+ * (SIPO_F32, SIPO_BF16 with FP32 arithmetic, or SIPO_F64); residuals, gap,
+ * step sizes, restart logic and the u~/v~ scalars are FP64 in every mode.
+ * tile_cfg: -1 lets the library choose tile shapes, otherwise an index into
+ * its tile table (see sipo_tile_count). */
+typedef struct sipo_tolerances {
+  double kkt_tol;
+  long long max_iter;
+  int check_every;
+  int storage;
+  int tile_cfg;
+} sipo_tolerances;
+
+/* Result of sipo_solve.  kkt = max(rel_primal, rel_dual, rel_gap) of the
+ * returned point; pobj/dobj are the primal/dual objectives of the normalised
+ * LP; u, v are u~*, v~*.  Metrics of the dose d = A^T y (Eqs. 6-8, 46):
+ * dtvr_f, dsr, psr_f; alpha: the dose-domain post-scaling factor of Eq. 27
+ * with unit weights; s: min_gel(d / f~_L), the recovered Charnes-Cooper scale
+ * (t = 1/s, Eq. 18; 1 at an optimum). */
+typedef struct sipo_result {
+  int status;
+  int restarts;
+  long long iters;
+  double kkt, rel_primal, rel_dual, rel_gap;
+  double r_primal, r_dual, gap, pobj, dobj;
+  double u, v, omega;
+  double f_crit, alpha, dtvr_f, dsr, psr_f, s;
+  double solve_ms;
+  long long kernel_launches;
+} sipo_result;
+
+/* Creates a solver context: copies the geometry and the target dose f_T
+ * ([ny][nx][nz] float32, host or device per f_T_location), builds the region
+ * labels, the active-ray mask (Pi_act = {[P f_T]_j != 0}, Sec. 2.2), the
+ * normalised target (Sec. 2.5 / Eqs. 30-31 / Eq. 39) and the diagonal
+ * preconditioners, all on the device.  `stream` (cudaStream_t or NULL) is the
+ * context's stream for solves; creation itself synchronises it.  On success
+ * *out owns all internal device memory until sipo_destroy.  Errors:
+ * INVALID_ARG (sizes, NaN/negative target, empty gel, mu > 0 without vial),
+ * OOM, CUDA. */
+int sipo_create(const sipo_geometry *geo, const float *f_T, int f_T_location,
+                const sipo_case_params *cp, const sipo_tolerances *tol,
+                void *stream, sipo_ctx **out);
+
+/* Runs the restarted Halpern PDHG (Sec. 2.8) from a zero start until the
+ * KKT tolerance, a primal-infeasibility certificate or max_iter, then the
+ * post-solve metrics.  y_out (nullable) receives y*, the normalised
+ * projection of Eq. 18, as [n_angles][n_det][nz] in FP32 (FP64 when storage
+ * is SIPO_F64), host or device per y_location.  Blocks until done.  Errors:
+ * INVALID_ARG, CUDA, TIMEOUT. */
+int sipo_solve(sipo_ctx *ctx, void *y_out, int y_location, sipo_result *res);
+
+/* Solves n independent contexts as one batch: their iterations are issued
+ * together in one captured CUDA graph per check period so that small LPs of
+ * a parameter sweep share the device.  y_outs may be NULL or an array of n
+ * nullable pointers (same rules as sipo_solve).  results: n entries. */
+int sipo_solve_batched(sipo_ctx **ctxs, int n, void **y_outs, int y_location,
+                       sipo_result *results);
+
+/* A vol = P_mu K vol (the adjoint of Eq. 3): vol is a device volume, sino a
+ * device sinogram, both of `dtype` (SIPO_F32 or SIPO_F64).  Enqueued on
+ * `stream`.  With a PSF, uses a context-owned temporary volume, so calls on
+ * one context must not overlap in time on different streams. */
+int sipo_project(sipo_ctx *ctx, const void *vol, void *sino, int dtype, void *stream);
+
+/* A^T sino = K P_mu^T sino (Eq. 3); arguments as sipo_project. */
+int sipo_backproject(sipo_ctx *ctx, const void *sino, void *vol, int dtype, void *stream);
+
+/* K vol (deriv_axis < 0) or (dK/dsigma_a) vol for a = deriv_axis in {0:x,
+ * 1:y, 2:z} with the radii frozen at creation; device volumes of `dtype`. */
+int sipo_psf_apply(sipo_ctx *ctx, const void *in, void *out, int dtype, int deriv_axis,
+                   void *stream);
+
+/* PSF-sigma gradient of the bilinear form <sino, A vol> = <sino, P_mu K vol>:
+ * grad[a] = < P_mu^T sino, (dK/dsigma_a) vol > for a = 0 (x), 1 (y), 2 (z),
+ * written to host memory (synchronises `stream`).  P_mu^T sino is recomputed
+ * into a context-owned temporary rather than stored.  With sino = dL/d(A p)
+ * and vol = p this is dL/dsigma of a projection; with sino = y and vol =
+ * dL/d(A^T y) it is dL/dsigma of a backprojection (K is symmetric).  sino and
+ * vol are device arrays of `dtype`; axes without a PSF get 0. */
+int sipo_psf_grad(sipo_ctx *ctx, const void *sino, const void *vol, int dtype, double *grad,
+                  void *stream);
+
+/* Replaces the PSF sigmas (radii stay frozen); affects later operator calls. */
+int sipo_set_psf_sigma(sipo_ctx *ctx, const double sigma[3]);
+
+/* Copies internal arrays out (synchronous).  which: 0 region labels (uint8,
+ * volume), 1 active-ray mask (uint8, sinogram), 2 y (compute type, sinogram),
+ * 3 lambda_up, 4 lambda_lo (compute type, volume; the duals of the up rows
+ * -- band and gel upper bounds -- and of the gel lower bound), 5 dose
+ * d = A^T y (compute type, volume).  After sipo_solve, 2-5 hold the returned
+ * point.  location: SIPO_HOST or SIPO_DEVICE. */
+int sipo_get_array(sipo_ctx *ctx, int which, void *out, int location);
+
+/* Runs `iters` PDHG iterations without graph capture, timing every kernel
+ * phase with CUDA events on the context stream; phase_ms[i] receives the
+ * average milliseconds per iteration of phase i for i < n_phases (at most
+ * sipo_phase_count()).  Leaves the solver state advanced by `iters`. */
+int sipo_profile(sipo_ctx *ctx, int iters, double *phase_ms, int n_phases);
+int sipo_phase_count(void);
+const char *sipo_phase_name(int i);
+
+/* Number of entries in the projector tile table (for sipo_tolerances.tile_cfg). */
+int sipo_tile_count(void);
+
+/* Total kernels this library has launched in this process (graph nodes count
+ * once per graph launch). */
+long long sipo_kernel_launch_count(void);
+
+/* Replaces kkt_tol and max_iter for later solves (check_every, storage and
+ * tile_cfg are fixed at creation; changing them is INVALID_ARG). */
+int sipo_set_tolerances(sipo_ctx *ctx, const sipo_tolerances *tol);
+
+/* Releases every device buffer and graph of the context (NULL is allowed). */
+int sipo_destroy(sipo_ctx *ctx);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *sipo_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIPO_H */

@@ -1,0 +1,22 @@
+"""GB300-native (sm_103a) SiPO projection-LP solver.
+
+The compute path is the CUDA library libsipo.so (C ABI in include/sipo.h);
+this package only marshals arguments to it (`_abi`) and wraps the projector
+pair as torch autograd functions (`autograd`).  `build()` compiles the
+library in-tree.
+"""
+from ._abi import (SIPO_BF16, SIPO_CASE1, SIPO_CASE2, SIPO_F32, SIPO_F64, SIPO_GENERAL,
+                   SIPO_ITER_LIMIT, SIPO_OPTIMAL, SIPO_PRIMAL_INFEASIBLE, Context, SipoError,
+                   load, sipo_backproject, sipo_create, sipo_destroy, sipo_get_array,
+                   sipo_kernel_launch_count, sipo_profile, sipo_project, sipo_psf_apply,
+                   sipo_psf_grad, sipo_set_psf_sigma, sipo_set_tolerances, sipo_solve,
+                   sipo_solve_batched)
+from .build import build
+
+__all__ = [
+    "build", "load", "Context", "SipoError", "sipo_create", "sipo_solve", "sipo_solve_batched",
+    "sipo_project", "sipo_backproject", "sipo_psf_apply", "sipo_psf_grad", "sipo_set_psf_sigma",
+    "sipo_get_array", "sipo_set_tolerances", "sipo_profile", "sipo_kernel_launch_count", "sipo_destroy",
+    "SIPO_F32", "SIPO_F64", "SIPO_BF16", "SIPO_GENERAL", "SIPO_CASE1", "SIPO_CASE2",
+    "SIPO_OPTIMAL", "SIPO_PRIMAL_INFEASIBLE", "SIPO_ITER_LIMIT",
+]

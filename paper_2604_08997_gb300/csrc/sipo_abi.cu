@@ -1,0 +1,1029 @@
+// sipo_abi.cu -- solver contexts and the extern "C" entry points of include/sipo.h.
+//
+// A context owns every device array of one LP instance.  Setup (sipo_create)
+// runs entirely on the device: target statistics, region labels, active-ray
+// mask, normalised target and Pock-Chambolle preconditioners.  A solve runs
+// the restarted Halpern PDHG as one captured CUDA graph per check period
+// (one check step followed by check_every - 1 fused steps); the host only
+// reads a done flag between graph launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "sipo.h"
+#include "sipo_kernels.cuh"
+#include "sipo_launch.h"
+#include "sipo_ops.cuh"
+
+namespace sipo {
+namespace {
+
+thread_local std::string g_err;
+std::atomic<long long> g_launches{0};
+
+struct Error {
+  int code;
+  std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+
+void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    if (e == cudaErrorMemoryAllocation) fail(SIPO_ERR_OOM, std::string(what) + ": out of device memory");
+    fail(SIPO_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+
+int grid_for(long long n) {
+  long long g = (n + kThreads - 1) / kThreads;
+  return int(std::max<long long>(1, std::min<long long>(g, 152LL * 16)));
+}
+
+struct SolverBase {
+  virtual ~SolverBase() {}
+  virtual void setup(const float* fT_dev) = 0;
+  virtual void begin_solve() = 0;
+  virtual void launch_block(long long n) = 0;
+  virtual void request_done() = 0;
+  virtual bool done_flag() = 0;
+  virtual void finish_solve(void* y_out, int loc, sipo_result* res) = 0;
+  virtual void project(const void* vol, void* sino, cudaStream_t s) = 0;
+  virtual void backproject(const void* sino, void* vol, cudaStream_t s) = 0;
+  virtual void psf_apply(const void* in, void* out, int deriv, cudaStream_t s) = 0;
+  virtual void psf_grad(const void* sino, const void* vol, double* grad, cudaStream_t s) = 0;
+  virtual void set_sigma(const double* sig) = 0;
+  virtual void get_array(int which, void* out, int loc) = 0;
+  virtual void profile(int iters, double* ms, int n) = 0;
+  virtual int compute_dtype() const = 0;
+  virtual cudaStream_t strm() const = 0;
+  virtual long long period() const = 0;
+  virtual long long max_iter() const = 0;
+  virtual void set_tolerances(const sipo_tolerances* t) = 0;
+};
+
+constexpr int kNumPhases = 7;
+const char* kPhaseNames[kNumPhases] = {"scalar_step", "psf_q",       "project_primal", "backproject",
+                                       "psf_d",       "dual_update", "check_step"};
+
+template <typename S>
+struct Solver final : SolverBase {
+  using C = typename Compute<S>::type;
+
+  // configuration
+  int nx, ny, nz, na, nd;
+  size_t V, SN;
+  double vial_r, mu, sigma[3], trunc;
+  int R[3];
+  std::vector<double> angles;
+  sipo_case_params cp;
+  sipo_tolerances tol;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool vec = false;
+  int zl = 1;
+  int P = 64;
+  bool psf = false;
+
+  // device memory
+  std::vector<void*> allocs;
+  C *cs = nullptr, *ex = nullptr, *ey = nullptr, *es = nullptr;
+  C* taps[3] = {nullptr, nullptr, nullptr};
+  C* dtaps[3] = {nullptr, nullptr, nullptr};
+  float* fT = nullptr;
+  uint8_t *lab = nullptr, *mask = nullptr, *act_col = nullptr, *need = nullptr;
+  C *ft = nullptr, *row = nullptr, *col = nullptr;
+  S *y = nullptr, *y0 = nullptr, *yp = nullptr, *ybar = nullptr;
+  C *gp = nullptr, *g0 = nullptr;
+  S *lu = nullptr, *ll = nullptr, *lu0 = nullptr, *ll0 = nullptr, *lpu = nullptr, *lpl = nullptr;
+  S *q = nullptr, *qp = nullptr, *kq = nullptr;
+  C *d = nullptr, *d0 = nullptr, *dp = nullptr;
+  C *braw = nullptr, *t1 = nullptr, *t2 = nullptr, *t3 = nullptr, *tvol = nullptr;
+  Scal* st = nullptr;
+  double* part = nullptr;
+  Scal* h_st = nullptr;  // pinned host mirror
+
+  // host constants
+  bool ft_is_const = false;
+  C ft_const = C(0);
+  double up_ratio = 0.0, f_crit = 0.0, col_u = 0.0, col_v = 0.0, h_norm = 0.0, c_norm = 0.0;
+  double omega0 = 1.0, c_u = 0.0, c_v = 0.0, band_rhs = 0.0;
+  long long n_band = 0, n_gel = 0;
+  int has_u = 0, has_v = 0;
+
+  cudaGraphExec_t gexec = nullptr;
+  long long graph_nodes = 0;
+  long long launches = 0;
+  bool solved = false;
+  std::chrono::steady_clock::time_point t_start;
+
+  template <typename T>
+  T* dalloc(size_t n) {
+    void* p = nullptr;
+    ck(cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)), "cudaMalloc");
+    allocs.push_back(p);
+    return static_cast<T*>(p);
+  }
+
+  Solver(const sipo_geometry* g, const sipo_case_params* c, const sipo_tolerances* t, cudaStream_t s) {
+    nx = g->nx; ny = g->ny; nz = g->nz; na = g->n_angles; nd = g->n_det;
+    V = size_t(nx) * ny * nz;
+    SN = size_t(na) * nd * nz;
+    vial_r = g->vial_radius;
+    mu = g->mu;
+    trunc = g->psf_trunc > 0 ? g->psf_trunc : 4.0;
+    for (int a = 0; a < 3; ++a) {
+      sigma[a] = g->psf_sigma[a];
+      R[a] = sigma[a] > 0 ? int(std::ceil(trunc * sigma[a])) : 0;
+    }
+    psf = R[0] > 0 || R[1] > 0 || R[2] > 0;
+    angles.assign(g->angles, g->angles + na);
+    cp = *c;
+    tol = *t;
+    P = tol.check_every > 0 ? tol.check_every : 64;
+    constexpr int ZLV = vec_zl<C>();
+    vec = (nz % ZLV) == 0;
+    zl = vec ? ZLV : 1;
+    if (s) {
+      stream = s;
+    } else {
+      ck(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking), "cudaStreamCreate");
+      own_stream = true;
+    }
+    ck(cudaHostAlloc(reinterpret_cast<void**>(&h_st), sizeof(Scal), cudaHostAllocDefault), "cudaHostAlloc");
+  }
+
+  ~Solver() override {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (stream) cudaStreamSynchronize(stream);
+    for (void* p : allocs) cudaFree(p);
+    if (h_st) cudaFreeHost(h_st);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+
+  int compute_dtype() const override { return sizeof(C) == 8 ? SIPO_F64 : SIPO_F32; }
+  cudaStream_t strm() const override { return stream; }
+  long long period() const override { return P; }
+  long long max_iter() const override { return tol.max_iter; }
+  void set_tolerances(const sipo_tolerances* t) override {
+    const int p = t->check_every > 0 ? t->check_every : 64;
+    if (p != P || t->storage != tol.storage)
+      fail(SIPO_ERR_INVALID_ARG, "check_every and storage are fixed at creation");
+    if (!(t->kkt_tol >= 0) || t->max_iter < 0) fail(SIPO_ERR_INVALID_ARG, "bad tolerances");
+    tol.kkt_tol = t->kkt_tol;
+    tol.max_iter = t->max_iter;
+  }
+
+  Geo<C> geo() const {
+    Geo<C> g;
+    g.nx = nx; g.ny = ny; g.nz = nz; g.na = na; g.nd = nd;
+    g.cx = C((nx - 1) / 2.0);
+    g.cy = C((ny - 1) / 2.0);
+    g.off = C((nd - 1) / 2.0);
+    g.cs = cs; g.ex = ex; g.ey = ey; g.es = es;
+    g.r2q = vial_r > 0 ? 4.0 * (vial_r * vial_r) : 0.0;
+    g.vial_r = vial_r;
+    return g;
+  }
+
+  Bufs<S, C> bufs() const {
+    Bufs<S, C> b;
+    b.y = y; b.y0 = y0; b.yp = yp; b.ybar = ybar; b.col = col; b.gp = gp; b.g0 = g0;
+    b.lu = lu; b.ll = ll; b.lu0 = lu0; b.ll0 = ll0; b.lpu = lpu; b.lpl = lpl; b.q = q; b.qp = qp;
+    b.d = d; b.d0 = d0; b.dp = dp; b.row = row; b.ft = ft_is_const ? nullptr : ft; b.lab = lab;
+    b.ft_const = ft_const; b.up_ratio = C(up_ratio); b.has_u = has_u; b.has_v = has_v;
+    b.band_rhs = C(band_rhs); b.st = st; b.part = part;
+    return b;
+  }
+
+  void count(long long n) {
+    launches += n;
+    g_launches += n;
+  }
+
+  // ------------------------------------------------------------- tables
+  void upload_taps() {
+    for (int a = 0; a < 3; ++a) {
+      if (R[a] == 0) continue;
+      std::vector<C> h(2 * R[a] + 1), hd(2 * R[a] + 1);
+      std::vector<double> e(2 * R[a] + 1), de(2 * R[a] + 1);
+      double S0 = 0, dS = 0;
+      for (int i = -R[a]; i <= R[a]; ++i) {
+        const double ev = std::exp(-(double(i) * i) / (2.0 * sigma[a] * sigma[a]));
+        e[i + R[a]] = ev;
+        de[i + R[a]] = ev * double(i) * i / (sigma[a] * sigma[a] * sigma[a]);
+        S0 += ev;
+        dS += de[i + R[a]];
+      }
+      for (int i = 0; i < 2 * R[a] + 1; ++i) {
+        h[i] = C(e[i] / S0);
+        hd[i] = C((de[i] * S0 - e[i] * dS) / (S0 * S0));
+      }
+      ck(cudaMemcpy(taps[a], h.data(), h.size() * sizeof(C), cudaMemcpyHostToDevice), "taps");
+      ck(cudaMemcpy(dtaps[a], hd.data(), hd.size() * sizeof(C), cudaMemcpyHostToDevice), "dtaps");
+    }
+  }
+
+  void build_tables() {
+    std::vector<C> h_cs(2 * size_t(na));
+    for (int k = 0; k < na; ++k) {
+      h_cs[2 * k] = C(std::cos(angles[k]));
+      h_cs[2 * k + 1] = C(std::sin(angles[k]));
+    }
+    cs = dalloc<C>(h_cs.size());
+    ck(cudaMemcpy(cs, h_cs.data(), h_cs.size() * sizeof(C), cudaMemcpyHostToDevice), "cs");
+    if (vial_r > 0) {
+      const double off = (nd - 1) / 2.0;
+      std::vector<C> h_es(size_t(na) * nd);
+      for (int k = 0; k < na; ++k)
+        for (int j = 0; j < nd; ++j) {
+          const double sj = j - off;
+          h_es[size_t(k) * nd + j] =
+              std::fabs(sj) <= vial_r ? C(std::exp(-mu * std::sqrt(std::max(vial_r * vial_r - sj * sj, 0.0))))
+                                      : C(0);
+        }
+      es = dalloc<C>(h_es.size());
+      ck(cudaMemcpy(es, h_es.data(), h_es.size() * sizeof(C), cudaMemcpyHostToDevice), "es");
+      if (mu != 0.0) {
+        std::vector<C> h_ex(size_t(na) * nx), h_ey(size_t(na) * ny);
+        for (int k = 0; k < na; ++k) {
+          const double s = std::sin(angles[k]), c = std::cos(angles[k]);
+          for (int ix = 0; ix < nx; ++ix) h_ex[size_t(k) * nx + ix] = C(std::exp(mu * (ix - (nx - 1) / 2.0) * s));
+          for (int iy = 0; iy < ny; ++iy) h_ey[size_t(k) * ny + iy] = C(std::exp(-mu * (iy - (ny - 1) / 2.0) * c));
+        }
+        ex = dalloc<C>(h_ex.size());
+        ey = dalloc<C>(h_ey.size());
+        ck(cudaMemcpy(ex, h_ex.data(), h_ex.size() * sizeof(C), cudaMemcpyHostToDevice), "ex");
+        ck(cudaMemcpy(ey, h_ey.data(), h_ey.size() * sizeof(C), cudaMemcpyHostToDevice), "ey");
+      }
+    }
+    for (int a = 0; a < 3; ++a)
+      if (R[a] > 0) {
+        taps[a] = dalloc<C>(2 * R[a] + 1);
+        dtaps[a] = dalloc<C>(2 * R[a] + 1);
+      }
+    upload_taps();
+    if (psf) unit_tap();  // identity axes of a partial PSF, allocated before any capture
+  }
+
+  // ---------------------------------------------------------------- PSF
+  // in -> out through the three axis passes (taps or, on deriv_axis, their
+  // sigma derivative).  tmp_a and tmp_b are C volumes distinct from in/out.
+  template <typename TI, typename TO>
+  void psf3(const TI* in, TO* out, C* tmp_a, C* tmp_b, int deriv, cudaStream_t s) {
+    const int grid = grid_for((long long)V);
+    const C* tp[3];
+    for (int a = 0; a < 3; ++a) tp[a] = (deriv == a) ? dtaps[a] : taps[a];
+    // identity axes still run a pass with the single tap 1 (R = 0) only when
+    // deriving; otherwise they are skipped by copying through
+    k_conv_axis<TI, C, C><<<grid, kThreads, 0, s>>>(in, tmp_a, tp[0] ? tp[0] : unit_tap(), R[0], nx, ny, nz, 0);
+    k_conv_axis<C, C, C><<<grid, kThreads, 0, s>>>(tmp_a, tmp_b, tp[1] ? tp[1] : unit_tap(), R[1], nx, ny, nz, 1);
+    k_conv_axis<C, TO, C><<<grid, kThreads, 0, s>>>(tmp_b, out, tp[2] ? tp[2] : unit_tap(), R[2], nx, ny, nz, 2);
+    count(3);
+  }
+
+  C* unit = nullptr;
+  C* unit_tap() {
+    if (!unit) {
+      unit = dalloc<C>(1);
+      const C one = C(1);
+      ck(cudaMemcpy(unit, &one, sizeof(C), cudaMemcpyHostToDevice), "unit tap");
+    }
+    return unit;
+  }
+
+  void ensure_temps() {
+    if (!t1) {
+      t1 = dalloc<C>(V);
+      t2 = dalloc<C>(V);
+      t3 = dalloc<C>(V);
+    }
+  }
+
+  // -------------------------------------------------------------- setup
+  void setup(const float* fT_src) override {
+    if (psf) {
+      // the derivative taps exist for every axis with a PSF; identity axes
+      // have no sigma to differentiate
+    }
+    ck(cudaDeviceSynchronize(), "device sync before setup");
+    build_tables();
+    fT = dalloc<float>(V);
+    ck(cudaMemcpyAsync(fT, fT_src, V * sizeof(float), cudaMemcpyDefault, stream), "copy f_T");
+    const int gv = grid_for((long long)V);
+    // target statistics
+    TargetStats* d_stats = dalloc<TargetStats>(1);
+    TargetStats init{0, 0, 0x7f800000u, 0u};
+    ck(cudaMemcpyAsync(d_stats, &init, sizeof(init), cudaMemcpyHostToDevice, stream), "stats init");
+    k_target_stats<<<gv, kThreads, 0, stream>>>(fT, (long long)V, d_stats);
+    TargetStats hs;
+    ck(cudaMemcpyAsync(&hs, d_stats, sizeof(hs), cudaMemcpyDeviceToHost, stream), "stats");
+    ck(cudaStreamSynchronize(stream), "target stats");
+    if (hs.n_bad) fail(SIPO_ERR_INVALID_ARG, "target contains NaN, infinite or negative values");
+    if (hs.n_gel == 0) fail(SIPO_ERR_INVALID_ARG, "empty gelation region (target is all zero)");
+    float fmin_v, fmax_v;
+    std::memcpy(&fmin_v, &hs.min_bits, 4);
+    std::memcpy(&fmax_v, &hs.max_bits, 4);
+    const double mn = fmin_v;
+    // normalisation (Sec. 2.5; Case 1 Eqs. 29-31; Case 2 Eq. 39)
+    double mult = 1.0;
+    has_u = cp.kase == SIPO_GENERAL || cp.kase == SIPO_CASE1;
+    has_v = cp.kase == SIPO_GENERAL || cp.kase == SIPO_CASE2;
+    band_rhs = has_u ? 0.0 : 1.0;
+    if (cp.kase == SIPO_GENERAL) {
+      f_crit = mn;
+      mult = 1.0 / f_crit;
+      c_u = cp.w1;
+      c_v = cp.w2;
+    } else if (cp.kase == SIPO_CASE1) {
+      f_crit = (1.0 - cp.tol_lo) * mn;
+      mult = (1.0 - cp.tol_lo) / f_crit;
+      up_ratio = (1.0 + cp.tol_hi) / (1.0 - cp.tol_lo);
+      c_u = 1.0;
+      c_v = 0.0;
+    } else {
+      f_crit = cp.inhibit_ratio * mn;
+      mult = 1.0 / f_crit;
+      c_u = 0.0;
+      c_v = 1.0;
+    }
+    ft_is_const = hs.min_bits == hs.max_bits;
+    ft_const = C(double(fmin_v) * mult);
+    lab = dalloc<uint8_t>(V);
+    if (!ft_is_const) {
+      ft = dalloc<C>(V);
+    }
+    // labels
+    {
+      int *da = nullptr, *db = nullptr;
+      uint8_t *ma = nullptr, *mb = nullptr;
+      ck(cudaMallocAsync(reinterpret_cast<void**>(&da), V * sizeof(int), stream), "labels tmp");
+      ck(cudaMallocAsync(reinterpret_cast<void**>(&db), V * sizeof(int), stream), "labels tmp");
+      k_gel_init<<<gv, kThreads, 0, stream>>>(fT, (long long)V, da, lab);
+      const int W = cp.band_width;
+      const bool band_free = W < 0;
+      if (!band_free) {
+        k_dist_pass<<<gv, kThreads, 0, stream>>>(da, db, W, nx, ny, nz, 0);
+        k_dist_pass<<<gv, kThreads, 0, stream>>>(db, da, W, nx, ny, nz, 1);
+        k_dist_pass<<<gv, kThreads, 0, stream>>>(da, db, W, nx, ny, nz, 2);
+      }
+      uint8_t* sup = nullptr;
+      if (psf && !band_free) {
+        ck(cudaMallocAsync(reinterpret_cast<void**>(&ma), V, stream), "labels tmp");
+        ck(cudaMallocAsync(reinterpret_cast<void**>(&mb), V, stream), "labels tmp");
+        k_gel_mask<<<gv, kThreads, 0, stream>>>(lab, ma, (long long)V);
+        k_dilate_pass<<<gv, kThreads, 0, stream>>>(ma, mb, R[0], nx, ny, nz, 0);
+        k_dilate_pass<<<gv, kThreads, 0, stream>>>(mb, ma, R[1], nx, ny, nz, 1);
+        k_dilate_pass<<<gv, kThreads, 0, stream>>>(ma, mb, R[2], nx, ny, nz, 2);
+        sup = mb;
+      }
+      k_labels_final<C><<<gv, kThreads, 0, stream>>>(lab, band_free ? nullptr : db, sup,
+                                                      band_free ? -1 : W, band_free ? 1 : 0, geo());
+      ck(cudaFreeAsync(da, stream), "free");
+      ck(cudaFreeAsync(db, stream), "free");
+      if (ma) ck(cudaFreeAsync(ma, stream), "free");
+      if (mb) ck(cudaFreeAsync(mb, stream), "free");
+    }
+    if (!ft_is_const) k_ft<C><<<gv, kThreads, 0, stream>>>(fT, lab, mult, ft, (long long)V);
+    // columns that need the backprojection inside the solve
+    need = dalloc<uint8_t>(size_t(nx) * ny);
+    {
+      const int gc = grid_for((long long)nx * ny);
+      if (psf) {
+        uint8_t* tmp = nullptr;
+        ck(cudaMallocAsync(reinterpret_cast<void**>(&tmp), size_t(nx) * ny, stream), "need tmp");
+        k_need_cols<<<gc, kThreads, 0, stream>>>(lab, tmp, nx, ny, nz);
+        k_dilate_cols<<<gc, kThreads, 0, stream>>>(tmp, need, nx, ny, R[0], R[1]);
+        ck(cudaFreeAsync(tmp, stream), "free");
+      } else {
+        k_need_cols<<<gc, kThreads, 0, stream>>>(lab, need, nx, ny, nz);
+      }
+    }
+    // iterate storage
+    y = dalloc<S>(SN); y0 = dalloc<S>(SN); yp = dalloc<S>(SN); ybar = dalloc<S>(SN);
+    gp = dalloc<C>(SN); g0 = dalloc<C>(SN); col = dalloc<C>(SN);
+    mask = dalloc<uint8_t>(SN);
+    act_col = dalloc<uint8_t>(size_t(na) * nd);
+    lu = dalloc<S>(V); ll = dalloc<S>(V); lu0 = dalloc<S>(V); ll0 = dalloc<S>(V);
+    lpu = dalloc<S>(V); lpl = dalloc<S>(V); q = dalloc<S>(V); qp = dalloc<S>(V);
+    d = dalloc<C>(V); d0 = dalloc<C>(V); dp = dalloc<C>(V); row = dalloc<C>(V);
+    st = dalloc<Scal>(1);
+    part = dalloc<double>(size_t(kNumSlots) * kRedBlocks);
+    ensure_temps();
+    if (psf) {
+      kq = dalloc<S>(V);
+      braw = dalloc<C>(V);
+      ck(cudaMemsetAsync(braw, 0, V * sizeof(C), stream), "memset");
+    }
+    const Geo<C> g = geo();
+    const Bufs<S, C> B = bufs();
+    // active rays: [P_mu f_T]_j > 0 with the unblurred operator (Sec. 2.2)
+    const C* src = nullptr;
+    if constexpr (sizeof(C) == 4) {
+      src = reinterpret_cast<const C*>(fT);
+    } else {
+      k_convert<float, C><<<gv, kThreads, 0, stream>>>(fT, t1, (long long)V);
+      src = t1;
+    }
+    launch_project<C, C, C, kFpStore, C>(g, src, Bufs<C, C>{}, gp, nullptr, vec, stream);
+    const int gs = grid_for((long long)SN);
+    k_mask<C><<<gs, kThreads, 0, stream>>>(gp, mask, g0, (long long)SN);
+    k_act_cols<<<grid_for((long long)na * nd), kThreads, 0, stream>>>(mask, act_col, (long long)na * nd, nz);
+    // column abs-sums of G: A (1_band + 2 1_gel) on active rays
+    k_row_indicator<C><<<gv, kThreads, 0, stream>>>(lab, t1, (long long)V);
+    if (psf) {
+      psf3<C, C>(t1, t2, t3, braw, -1, stream);
+      ck(cudaMemsetAsync(braw, 0, V * sizeof(C), stream), "memset");
+      launch_project<C, C, C, kFpStore, C>(g, t2, Bufs<C, C>{}, col, nullptr, vec, stream);
+    } else {
+      launch_project<C, C, C, kFpStore, C>(g, t1, Bufs<C, C>{}, col, nullptr, vec, stream);
+    }
+    k_apply_mask<C><<<gs, kThreads, 0, stream>>>(col, mask, (long long)SN);
+    // row abs-sums of A^T over active rays: A^T 1_act = K P^T 1_act
+    if (psf) {
+      launch_backproject<C, C, C, kBpStore, C>(g, g0, Bufs<C, C>{}, t1, nullptr, vec, stream);
+      psf3<C, C>(t1, row, t2, t3, -1, stream);
+    } else {
+      launch_backproject<C, C, C, kBpStore, C>(g, g0, Bufs<C, C>{}, row, nullptr, vec, stream);
+    }
+    (void)B;
+    // setup sums
+    k_setup_sums<C><<<kRedBlocks, kThreads, 0, stream>>>(lab, ft_is_const ? nullptr : ft, ft_const, row,
+                                                         up_ratio, has_u, has_v, cp.kase, (long long)V, part);
+    std::vector<double> hp(7 * size_t(kRedBlocks));
+    ck(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, stream), "sums");
+    ck(cudaStreamSynchronize(stream), "setup");
+    double sums[7] = {};
+    for (int i = 0; i < 7; ++i)
+      for (int b = 0; b < kRedBlocks; ++b) sums[i] += hp[size_t(i) * kRedBlocks + b];
+    n_band = (long long)sums[0];
+    n_gel = (long long)sums[1];
+    col_u = has_u ? sums[0] : 0.0;
+    col_v = has_v ? sums[2] : 0.0;
+    h_norm = std::sqrt(sums[0] * band_rhs * band_rhs + (cp.kase == SIPO_CASE1 ? sums[4] : 0.0) + sums[3]);
+    c_norm = std::sqrt((has_u ? c_u * c_u : 0.0) + (has_v ? c_v * c_v : 0.0));
+    const double c_hat2 = (has_u && col_u > 0 ? c_u * c_u / col_u : 0.0) +
+                          (has_v && col_v > 0 ? c_v * c_v / col_v : 0.0);
+    const double h_hat2 = sums[5] + sums[6];
+    omega0 = (c_hat2 > 0 && h_hat2 > 0) ? std::sqrt(c_hat2 / h_hat2) : 1.0;
+    count(16);
+  }
+
+  // ------------------------------------------------------- iteration steps
+  template <typename T>
+  void zero(T* p, size_t n) {
+    ck(cudaMemsetAsync(p, 0, n * sizeof(T), stream), "memset");
+  }
+
+  void begin_solve() override {
+    zero(y, SN); zero(y0, SN); zero(yp, SN); zero(ybar, SN); zero(gp, SN); zero(g0, SN);
+    zero(lu, V); zero(ll, V); zero(lu0, V); zero(ll0, V); zero(lpu, V); zero(lpl, V);
+    zero(q, V); zero(qp, V); zero(d, V); zero(d0, V); zero(dp, V);
+    if (kq) zero(kq, V);
+    zero(part, size_t(kNumSlots) * kRedBlocks);
+    Scal h{};
+    h.c_u = c_u; h.c_v = c_v; h.band_rhs = band_rhs; h.col_u = col_u; h.col_v = col_v;
+    h.h_norm = h_norm; h.c_norm = c_norm; h.kkt_tol = tol.kkt_tol; h.has_u = has_u; h.has_v = has_v;
+    h.max_iter = tol.max_iter;
+    h.u = 0.0; h.v = 1.0; h.u0 = 0.0; h.v0 = 1.0; h.up = 0.0; h.vp = 1.0;
+    h.omega = omega0;
+    *h_st = h;
+    ck(cudaMemcpyAsync(st, h_st, sizeof(Scal), cudaMemcpyHostToDevice, stream), "state");
+    ck(cudaStreamSynchronize(stream), "begin solve");
+    solved = false;
+    build_graph();
+    launches = 0;
+    t_start = std::chrono::steady_clock::now();
+  }
+
+  void enqueue_psf_q(const S* src, cudaStream_t s) { psf3<S, S>(src, kq, t1, t2, -1, s); }
+
+  void enqueue_normal(cudaStream_t s, cudaEvent_t* ev = nullptr) {
+    const Geo<C> g = geo();
+    const Bufs<S, C> B = bufs();
+    const long long nvv = (long long)(V / zl);
+    auto rec = [&](int i) {
+      if (ev) ck(cudaEventRecord(ev[i], s), "event");
+    };
+    rec(0);
+    k_scalar_step<false><<<1, kThreads, 0, s>>>(st, part);
+    count(1);
+    rec(1);
+    if (psf) enqueue_psf_q(q, s);
+    rec(2);
+    launch_project<S, S, C, kFpPrimal, C>(g, psf ? kq : q, B, (C*)nullptr, act_col, vec, s);
+    count(1);
+    rec(3);
+    if (psf) {
+      launch_backproject<S, S, C, kBpStore, C>(g, ybar, B, braw, need, vec, s);
+      count(1);
+      rec(4);
+      psf3<C, C>(braw, t3, t1, t2, -1, s);
+      rec(5);
+      dual_launch<false>(B, t3, nvv, s);
+    } else {
+      launch_backproject<S, S, C, kBpDual, C>(g, ybar, B, (C*)nullptr, need, vec, s);
+      count(1);
+      rec(4);
+      rec(5);
+    }
+    rec(6);
+  }
+
+  template <bool CHECK>
+  void dual_launch(const Bufs<S, C>& B, const C* dbar, long long nvv, cudaStream_t s) {
+    if (vec)
+      k_dual<S, C, vec_zl<C>(), CHECK><<<kRedBlocks, kThreads, 0, s>>>(B, dbar, nvv);
+    else
+      k_dual<S, C, 1, CHECK><<<kRedBlocks, kThreads, 0, s>>>(B, dbar, nvv);
+    count(1);
+  }
+
+  void enqueue_check(cudaStream_t s) {
+    const Geo<C> g = geo();
+    const Bufs<S, C> B = bufs();
+    const long long nvv = (long long)(V / zl), nvs = (long long)(SN / zl);
+    k_scalar_step<true><<<1, kThreads, 0, s>>>(st, part);
+    count(1);
+    if (psf) enqueue_psf_q(q, s);
+    launch_project<S, S, C, kFpPrimalCheck, C>(g, psf ? kq : q, B, (C*)nullptr, act_col, vec, s);
+    count(1);
+    if (psf) {
+      launch_backproject<S, S, C, kBpStore, C>(g, ybar, B, braw, need, vec, s);
+      count(1);
+      psf3<C, C>(braw, t3, t1, t2, -1, s);
+      dual_launch<true>(B, t3, nvv, s);
+      enqueue_psf_q(qp, s);
+    } else {
+      launch_backproject<S, S, C, kBpDualCheck, C>(g, ybar, B, (C*)nullptr, need, vec, s);
+      count(1);
+    }
+    launch_project<S, S, C, kFpResid, C>(g, psf ? kq : qp, B, (C*)nullptr, act_col, vec, s);
+    count(1);
+    k_scalar_check<<<1, kThreads, 0, s>>>(st, part);
+    count(1);
+    if (vec) {
+      k_blend_sino<S, C, vec_zl<C>()><<<grid_for(nvs), kThreads, 0, s>>>(B, nvs);
+      k_blend_vol<S, C, vec_zl<C>()><<<kRedBlocks, kThreads, 0, s>>>(B, nvv);
+    } else {
+      k_blend_sino<S, C, 1><<<grid_for(nvs), kThreads, 0, s>>>(B, nvs);
+      k_blend_vol<S, C, 1><<<kRedBlocks, kThreads, 0, s>>>(B, nvv);
+    }
+    count(2);
+  }
+
+  void build_graph() {
+    if (gexec) return;
+    cudaGraph_t graph;
+    const long long before = launches;
+    ck(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    enqueue_check(stream);
+    for (int i = 1; i < P; ++i) enqueue_normal(stream);
+    cudaError_t e = cudaStreamEndCapture(stream, &graph);
+    ck(e, "end capture");
+    graph_nodes = launches - before;
+    launches = before;
+    g_launches -= graph_nodes;
+    ck(cudaGraphInstantiate(&gexec, graph, 0), "graph instantiate");
+    cudaGraphDestroy(graph);
+  }
+
+  void launch_block(long long n) override {
+    if (n == P) {
+      build_graph();
+      ck(cudaGraphLaunch(gexec, stream), "graph launch");
+      count(graph_nodes);
+    } else {
+      enqueue_check(stream);
+      for (long long i = 1; i < n; ++i) enqueue_normal(stream);
+    }
+    ck(cudaGetLastError(), "launch");
+  }
+
+  void request_done() override {
+    ck(cudaMemcpyAsync(h_st, st, sizeof(Scal), cudaMemcpyDeviceToHost, stream), "read state");
+  }
+
+  bool done_flag() override {
+    ck(cudaStreamSynchronize(stream), "iterations");
+    return h_st->done != 0;
+  }
+
+  void final_check() {
+    enqueue_check(stream);
+    ck(cudaGetLastError(), "launch");
+  }
+
+  void finish_solve(void* y_out, int loc, sipo_result* res) override {
+    ck(cudaMemcpyAsync(h_st, st, sizeof(Scal), cudaMemcpyDeviceToHost, stream), "read state");
+    ck(cudaStreamSynchronize(stream), "solve");
+    if (!h_st->done) {
+      final_check();
+      ck(cudaMemcpyAsync(h_st, st, sizeof(Scal), cudaMemcpyDeviceToHost, stream), "read state");
+      ck(cudaStreamSynchronize(stream), "solve");
+    }
+    solved = true;
+    // metrics of d = A^T y at the returned point (Eqs. 6-8, 27, 46)
+    k_metrics<C><<<kRedBlocks, kThreads, 0, stream>>>(dp, lab, fT, ft_is_const ? nullptr : ft, ft_const,
+                                                     f_crit, (long long)V, part);
+    count(1);
+    std::vector<double> hp(8 * size_t(kRedBlocks));
+    ck(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, stream), "metrics");
+    if (y_out) copy_out(yp, SN, y_out, loc, gp);
+    ck(cudaStreamSynchronize(stream), "metrics");
+    double m[8] = {1e300, -1e300, -1e300, 1e300, 0.0, 0.0, 1e300, -1e300};
+    for (int b = 0; b < kRedBlocks; ++b) {
+      m[0] = std::min(m[0], hp[0 * kRedBlocks + b]);
+      m[1] = std::max(m[1], hp[1 * kRedBlocks + b]);
+      m[2] = std::max(m[2], hp[2 * kRedBlocks + b]);
+      m[3] = std::min(m[3], hp[3 * kRedBlocks + b]);
+      m[4] += hp[4 * kRedBlocks + b];
+      m[5] += hp[5 * kRedBlocks + b];
+      m[6] = std::min(m[6], hp[6 * kRedBlocks + b]);
+      m[7] = std::max(m[7], hp[7 * kRedBlocks + b]);
+    }
+    const Scal& h = *h_st;
+    std::memset(res, 0, sizeof(*res));
+    res->status = h.status;
+    res->restarts = h.restarts;
+    res->iters = h.k;
+    res->kkt = h.kkt; res->rel_primal = h.rel_p; res->rel_dual = h.rel_d; res->rel_gap = h.rel_gap;
+    res->r_primal = h.rp; res->r_dual = h.rd; res->gap = h.gap; res->pobj = h.pobj; res->dobj = h.dobj;
+    res->u = h.up; res->v = h.vp; res->omega = h.omega;
+    res->f_crit = f_crit;
+    res->dtvr_f = m[0] > 0 ? m[1] / m[0] : INFINITY;
+    res->dsr = (m[0] > 0 && n_band > 0) ? m[2] / m[0] : INFINITY;
+    res->psr_f = (n_band > 0 && m[2] > 0) ? m[3] / m[2] : INFINITY;
+    res->alpha = m[5] > 0 ? m[4] / m[5] : 0.0;
+    res->s = m[6];
+    res->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    res->kernel_launches = launches;
+  }
+
+  // copies n elements of S (converted to C) to out (host or device)
+  template <typename T>
+  void copy_out(const T* src, size_t n, void* out, int loc, C* tmp) {
+    const C* from;
+    if constexpr (std::is_same<T, C>::value) {
+      from = src;
+    } else {
+      k_convert<T, C><<<grid_for((long long)n), kThreads, 0, stream>>>(src, tmp, (long long)n);
+      count(1);
+      from = tmp;
+    }
+    ck(cudaMemcpyAsync(out, from, n * sizeof(C), loc == SIPO_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                       stream), "copy out");
+  }
+
+  // ------------------------------------------------------------ operators
+  void project(const void* vol, void* sino, cudaStream_t s) override {
+    const Geo<C> g = geo();
+    const C* src = static_cast<const C*>(vol);
+    if (psf) {
+      ensure_temps();
+      psf3<C, C>(src, t3, t1, t2, -1, s);
+      src = t3;
+    }
+    launch_project<C, C, C, kFpStore, C>(g, src, Bufs<C, C>{}, static_cast<C*>(sino), nullptr, vec, s);
+    count(1);
+    ck(cudaGetLastError(), "project");
+  }
+
+  void backproject(const void* sino, void* vol, cudaStream_t s) override {
+    const Geo<C> g = geo();
+    if (psf) {
+      ensure_temps();
+      launch_backproject<C, C, C, kBpStore, C>(g, static_cast<const C*>(sino), Bufs<C, C>{}, t3, nullptr, vec, s);
+      psf3<C, C>(t3, static_cast<C*>(vol), t1, t2, -1, s);
+    } else {
+      launch_backproject<C, C, C, kBpStore, C>(g, static_cast<const C*>(sino), Bufs<C, C>{},
+                                               static_cast<C*>(vol), nullptr, vec, s);
+    }
+    count(1);
+    ck(cudaGetLastError(), "backproject");
+  }
+
+  void psf_apply(const void* in, void* out, int deriv, cudaStream_t s) override {
+    ensure_temps();
+    if (deriv >= 0 && R[deriv] == 0) {
+      ck(cudaMemsetAsync(out, 0, V * sizeof(C), s), "memset");
+      return;
+    }
+    psf3<C, C>(static_cast<const C*>(in), static_cast<C*>(out), t1, t2, deriv, s);
+    ck(cudaGetLastError(), "psf");
+  }
+
+  void psf_grad(const void* sino, const void* vol, double* grad, cudaStream_t s) override {
+    ensure_temps();
+    if (!tvol) tvol = dalloc<C>(V);
+    std::vector<double> hp(kRedBlocks);
+    double* pg = dalloc_part();
+    // b = P_mu^T sino, recomputed (not stored by the forward pass)
+    launch_backproject<C, C, C, kBpStore, C>(geo(), static_cast<const C*>(sino), Bufs<C, C>{}, tvol, nullptr,
+                                             vec, s);
+    count(1);
+    for (int a = 0; a < 3; ++a) {
+      grad[a] = 0.0;
+      if (R[a] == 0) continue;
+      psf3<C, C>(static_cast<const C*>(vol), t3, t1, t2, a, s);
+      k_dot<C><<<kRedBlocks, kThreads, 0, s>>>(tvol, t3, (long long)V, pg);
+      count(1);
+      ck(cudaMemcpyAsync(hp.data(), pg, kRedBlocks * sizeof(double), cudaMemcpyDeviceToHost, s), "grad");
+      ck(cudaStreamSynchronize(s), "psf grad");
+      for (int i = 0; i < kRedBlocks; ++i) grad[a] += hp[i];
+    }
+  }
+
+  double* gpart = nullptr;
+  double* dalloc_part() {
+    if (!gpart) gpart = dalloc<double>(kRedBlocks);
+    return gpart;
+  }
+
+  void set_sigma(const double* sig) override {
+    for (int a = 0; a < 3; ++a) {
+      if ((R[a] == 0) != (sig[a] <= 0)) fail(SIPO_ERR_INVALID_ARG, "sigma must stay zero/non-zero per axis");
+      sigma[a] = sig[a];
+    }
+    ck(cudaStreamSynchronize(stream), "sync");
+    upload_taps();
+  }
+
+  void get_array(int which, void* out, int loc) override {
+    const cudaMemcpyKind kind = loc == SIPO_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (which == 0) {
+      ck(cudaMemcpyAsync(out, lab, V, kind, stream), "labels");
+    } else if (which == 1) {
+      ck(cudaMemcpyAsync(out, mask, SN, kind, stream), "mask");
+    } else if (which == 2) {
+      copy_out(solved ? yp : y, SN, out, loc, gp);
+    } else if (which == 3 || which == 4) {
+      if (!tvol) tvol = dalloc<C>(V);
+      copy_out(which == 3 ? (solved ? lpu : lu) : (solved ? lpl : ll), V, out, loc, tvol);
+    } else if (which == 5) {
+      copy_out(solved ? dp : d, V, out, loc, gp);
+    } else {
+      fail(SIPO_ERR_INVALID_ARG, "unknown array id");
+    }
+    ck(cudaStreamSynchronize(stream), "get array");
+  }
+
+  void profile(int iters, double* ms, int n) override {
+    begin_solve();
+    std::vector<cudaEvent_t> ev(7);
+    for (auto& e : ev) ck(cudaEventCreate(&e), "event");
+    std::vector<double> acc(kNumPhases, 0.0);
+    for (int it = 0; it < iters; ++it) {
+      enqueue_normal(stream, ev.data());
+      ck(cudaStreamSynchronize(stream), "profile");
+      for (int i = 0; i < 6; ++i) {
+        float t = 0;
+        ck(cudaEventElapsedTime(&t, ev[i], ev[i + 1]), "elapsed");
+        acc[i] += t;
+      }
+    }
+    // one check step, timed as a whole
+    ck(cudaEventRecord(ev[0], stream), "event");
+    enqueue_check(stream);
+    ck(cudaEventRecord(ev[1], stream), "event");
+    ck(cudaStreamSynchronize(stream), "profile");
+    float tc = 0;
+    ck(cudaEventElapsedTime(&tc, ev[0], ev[1]), "elapsed");
+    for (auto& e : ev) cudaEventDestroy(e);
+    for (int i = 0; i < std::min(n, kNumPhases); ++i)
+      ms[i] = i < 6 ? (iters > 0 ? acc[i] / iters : 0.0) : double(tc);
+  }
+};
+
+struct Ctx {
+  std::unique_ptr<SolverBase> s;
+};
+
+int set_error(const Error& e) {
+  g_err = e.msg;
+  return e.code;
+}
+
+}  // namespace
+}  // namespace sipo
+
+struct sipo_ctx {
+  sipo::Ctx c;
+};
+
+using sipo::Error;
+
+#define SIPO_TRY try {
+#define SIPO_CATCH                                       \
+  }                                                      \
+  catch (const Error& e) { return sipo::set_error(e); } \
+  catch (const std::bad_alloc&) {                        \
+    sipo::g_err = "host allocation failed";              \
+    return SIPO_ERR_OOM;                                 \
+  }
+
+extern "C" {
+
+const char* sipo_last_error(void) { return sipo::g_err.c_str(); }
+
+long long sipo_kernel_launch_count(void) { return sipo::g_launches.load(); }
+
+int sipo_phase_count(void) { return sipo::kNumPhases; }
+
+const char* sipo_phase_name(int i) {
+  return (i >= 0 && i < sipo::kNumPhases) ? sipo::kPhaseNames[i] : "";
+}
+
+int sipo_tile_count(void) { return 1; }
+
+int sipo_create(const sipo_geometry* geo, const float* f_T, int f_T_location, const sipo_case_params* cp,
+                const sipo_tolerances* tol, void* stream, sipo_ctx** out) {
+  SIPO_TRY
+  sipo::g_err.clear();
+  if (!geo || !f_T || !cp || !tol || !out) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (geo->nx <= 0 || geo->ny <= 0 || geo->nz <= 0 || geo->n_angles <= 0 || geo->n_det <= 0 || !geo->angles)
+    sipo::fail(SIPO_ERR_INVALID_ARG, "geometry sizes must be positive and angles non-null");
+  if ((long long)geo->nx * geo->ny * geo->nz > (1LL << 34) ||
+      (long long)geo->n_angles * geo->n_det * geo->nz > (1LL << 34))
+    sipo::fail(SIPO_ERR_INVALID_ARG, "problem too large");
+  for (int k = 0; k < geo->n_angles; ++k)
+    if (!std::isfinite(geo->angles[k])) sipo::fail(SIPO_ERR_INVALID_ARG, "non-finite angle");
+  if (geo->mu != 0.0 && !(geo->vial_radius > 0)) sipo::fail(SIPO_ERR_INVALID_ARG, "attenuation needs a vial radius");
+  if (!std::isfinite(geo->mu) || geo->mu < 0) sipo::fail(SIPO_ERR_INVALID_ARG, "mu must be finite and >= 0");
+  for (int a = 0; a < 3; ++a)
+    if (!(geo->psf_sigma[a] >= 0) || geo->psf_sigma[a] > 64) sipo::fail(SIPO_ERR_INVALID_ARG, "psf sigma out of range");
+  if (cp->kase < SIPO_GENERAL || cp->kase > SIPO_CASE2) sipo::fail(SIPO_ERR_INVALID_ARG, "unknown LP case");
+  if (cp->kase == SIPO_GENERAL && (!(cp->w1 >= 0) || !(cp->w2 >= 0)))
+    sipo::fail(SIPO_ERR_INVALID_ARG, "weights must be >= 0");
+  if (cp->kase == SIPO_CASE1 && (!(cp->tol_lo >= 0 && cp->tol_lo < 1) || !(cp->tol_hi >= 0)))
+    sipo::fail(SIPO_ERR_INVALID_ARG, "Case 1 tolerances must satisfy 0 <= tol_lo < 1, tol_hi >= 0");
+  if (cp->kase == SIPO_CASE2 && !(cp->inhibit_ratio > 0)) sipo::fail(SIPO_ERR_INVALID_ARG, "inhibit_ratio must be > 0");
+  if (cp->band_width > 1000) sipo::fail(SIPO_ERR_INVALID_ARG, "band_width too large");
+  if (tol->storage != SIPO_F32 && tol->storage != SIPO_F64 && tol->storage != SIPO_BF16)
+    sipo::fail(SIPO_ERR_INVALID_ARG, "unknown storage type");
+  if (!(tol->kkt_tol >= 0) || tol->max_iter < 0) sipo::fail(SIPO_ERR_INVALID_ARG, "bad tolerances");
+  std::unique_ptr<sipo::SolverBase> s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (tol->storage == SIPO_F32) s.reset(new sipo::Solver<float>(geo, cp, tol, st));
+  else if (tol->storage == SIPO_F64) s.reset(new sipo::Solver<double>(geo, cp, tol, st));
+  else s.reset(new sipo::Solver<__nv_bfloat16>(geo, cp, tol, st));
+  (void)f_T_location;
+  s->setup(f_T);
+  sipo_ctx* c = new sipo_ctx;
+  c->c.s = std::move(s);
+  *out = c;
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
+static void run_solve(sipo::SolverBase* s) {
+  s->begin_solve();
+  const long long P = s->period(), M = s->max_iter();
+  long long k = 0;
+  while (k < M) {
+    const long long n = std::min(P, M - k);
+    s->launch_block(n);
+    k += n;
+    s->request_done();
+    if (s->done_flag()) break;
+  }
+}
+
+int sipo_solve(sipo_ctx* ctx, void* y_out, int y_location, sipo_result* res) {
+  SIPO_TRY
+  if (!ctx || !res) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
+  run_solve(ctx->c.s.get());
+  ctx->c.s->finish_solve(y_out, y_location, res);
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
+int sipo_solve_batched(sipo_ctx** ctxs, int n, void** y_outs, int y_location, sipo_result* results) {
+  SIPO_TRY
+  if (!ctxs || n < 0 || (n > 0 && !results)) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
+  std::vector<sipo::SolverBase*> s(n);
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) sipo::fail(SIPO_ERR_INVALID_ARG, "null context");
+    s[i] = ctxs[i]->c.s.get();
+    s[i]->begin_solve();
+  }
+  std::vector<long long> k(n, 0);
+  std::vector<char> active(n, 1);
+  int left = n;
+  while (left > 0) {
+    for (int i = 0; i < n; ++i) {
+      if (!active[i]) continue;
+      const long long m = std::min(s[i]->period(), s[i]->max_iter() - k[i]);
+      if (m <= 0) continue;
+      s[i]->launch_block(m);
+      k[i] += m;
+      s[i]->request_done();
+    }
+    for (int i = 0; i < n; ++i) {
+      if (!active[i]) continue;
+      const bool done = s[i]->done_flag();
+      if (done || k[i] >= s[i]->max_iter()) {
+        active[i] = 0;
+        --left;
+      }
+    }
+  }
+  for (int i = 0; i < n; ++i) s[i]->finish_solve(y_outs ? y_outs[i] : nullptr, y_location, &results[i]);
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
+static int check_dtype(sipo_ctx* ctx, int dtype) {
+  if (!ctx) sipo::fail(SIPO_ERR_INVALID_ARG, "null context");
+  if (dtype != ctx->c.s->compute_dtype())
+    sipo::fail(SIPO_ERR_INVALID_ARG, "dtype must match the context's compute type (F32 for F32/BF16 storage, F64 for F64)");
+  return 0;
+}
+
+int sipo_project(sipo_ctx* ctx, const void* vol, void* sino, int dtype, void* stream) {
+  SIPO_TRY
+  check_dtype(ctx, dtype);
+  if (!vol || !sino) sipo::fail(SIPO_ERR_INVALID_ARG, "null buffer");
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->c.s->strm();
+  ctx->c.s->project(vol, sino, s);
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
+int sipo_backproject(sipo_ctx* ctx, const void* sino, void* vol, int dtype, void* stream) {
+  SIPO_TRY
+  check_dtype(ctx, dtype);
+  if (!vol || !sino) sipo::fail(SIPO_ERR_INVALID_ARG, "null buffer");
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->c.s->strm();
+  ctx->c.s->backproject(sino, vol, s);
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
+int sipo_psf_apply(sipo_ctx* ctx, const void* in, void* out, int dtype, int deriv_axis, void* stream) {
+  SIPO_TRY
+  check_dtype(ctx, dtype);
+  if (!in || !out || deriv_axis > 2) sipo::fail(SIPO_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->c.s->strm();
+  ctx->c.s->psf_apply(in, out, deriv_axis < 0 ? -1 : deriv_axis, s);
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
+int sipo_psf_grad(sipo_ctx* ctx, const void* sino, const void* vol, int dtype, double* grad, void* stream) {
+  SIPO_TRY
+  check_dtype(ctx, dtype);
+  if (!sino || !vol || !grad) sipo::fail(SIPO_ERR_INVALID_ARG, "null buffer");
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->c.s->strm();
+  ctx->c.s->psf_grad(sino, vol, grad, s);
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
+int sipo_set_psf_sigma(sipo_ctx* ctx, const double sigma[3]) {
+  SIPO_TRY
+  if (!ctx || !sigma) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
+  ctx->c.s->set_sigma(sigma);
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
+int sipo_get_array(sipo_ctx* ctx, int which, void* out, int location) {
+  SIPO_TRY
+  if (!ctx || !out) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
+  ctx->c.s->get_array(which, out, location);
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
+int sipo_profile(sipo_ctx* ctx, int iters, double* phase_ms, int n_phases) {
+  SIPO_TRY
+  if (!ctx || !phase_ms || iters < 0) sipo::fail(SIPO_ERR_INVALID_ARG, "bad argument");
+  ctx->c.s->profile(iters, phase_ms, n_phases);
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
+int sipo_set_tolerances(sipo_ctx* ctx, const sipo_tolerances* tol) {
+  SIPO_TRY
+  if (!ctx || !tol) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
+  ctx->c.s->set_tolerances(tol);
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
+int sipo_destroy(sipo_ctx* ctx) {
+  delete ctx;
+  return SIPO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,187 @@
+// sipo_device.cuh -- device-side building blocks of the SiPO solver (sm_103a).
+//
+// Layouts (z = rotation axis, fastest): volume [ny][nx][nz], sinogram
+// [n_angles][n_det][nz].  Every kernel maps the 32 lanes of a warp onto
+// consecutive z and gives each lane ZL consecutive z values, so all geometry
+// (detector coordinate, interpolation weight, attenuation factor) is
+// warp-uniform and every sinogram / volume access is a coalesced 16-byte
+// vector load per lane.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sipo {
+
+constexpr int kThreads = 256;     // threads per block for every kernel
+constexpr int kWarps = kThreads / 32;
+constexpr int kRedBlocks = 1216;  // 152 SMs x 8: grid of every reducing kernel
+constexpr double kEta = 0.99;     // step factor on the Pock-Chambolle steps
+
+enum Label : uint8_t { kExt = 0, kBand = 1, kGel = 2 };
+
+// ---------------------------------------------------------------- conversions
+__device__ __forceinline__ float to_c(float x) { return x; }
+__device__ __forceinline__ double to_c(double x) { return x; }
+__device__ __forceinline__ float to_c(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+template <typename S> struct FromC {
+  template <typename T> __device__ __forceinline__ static S cvt(T x) { return S(x); }
+};
+template <> struct FromC<__nv_bfloat16> {
+  template <typename T> __device__ __forceinline__ static __nv_bfloat16 cvt(T x) {
+    return __float2bfloat16_rn(float(x));
+  }
+};
+// compute value -> storage element (round to nearest for bf16)
+template <typename S, typename T> __device__ __forceinline__ S from_c(T x) { return FromC<S>::cvt(x); }
+
+template <typename S> struct Compute { using type = float; };
+template <> struct Compute<double> { using type = double; };
+
+// ------------------------------------------------- z-vector loads and stores
+// ZL consecutive elements starting at p.  When the vector is 16-byte sized it
+// is moved with 128-bit accesses (the host guarantees the alignment by only
+// choosing such ZL when nz is a multiple of the vector width).
+template <typename S, typename C, int ZL>
+__device__ __forceinline__ void load_z(const S* __restrict__ p, C (&v)[ZL]) {
+  constexpr int kBytes = int(sizeof(S)) * ZL;
+  if constexpr (kBytes % 16 == 0) {
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+    for (int i = 0; i < kBytes / 16; ++i) {
+      uint4 r = __ldg(q + i);
+      uint32_t w[4] = {r.x, r.y, r.z, r.w};
+      if constexpr (sizeof(S) == 4) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[i * 4 + j] = __uint_as_float(w[j]);
+      } else if constexpr (sizeof(S) == 2) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          v[i * 8 + 2 * j] = __uint_as_float(w[j] << 16);
+          v[i * 8 + 2 * j + 1] = __uint_as_float(w[j] & 0xffff0000u);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+          v[i * 2 + j] = __hiloint2double(int(w[2 * j + 1]), int(w[2 * j]));
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < ZL; ++i) v[i] = to_c(p[i]);
+  }
+}
+
+template <typename S, typename C, int ZL>
+__device__ __forceinline__ void store_z(S* __restrict__ p, const C (&v)[ZL]) {
+  constexpr int kBytes = int(sizeof(S)) * ZL;
+  if constexpr (kBytes % 16 == 0 && sizeof(S) == 4) {
+    float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+    for (int i = 0; i < ZL / 4; ++i)
+      q[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+  } else if constexpr (kBytes % 16 == 0 && sizeof(S) == 8) {
+    double2* q = reinterpret_cast<double2*>(p);
+#pragma unroll
+    for (int i = 0; i < ZL / 2; ++i) q[i] = make_double2(v[2 * i], v[2 * i + 1]);
+  } else if constexpr (kBytes % 16 == 0 && sizeof(S) == 2) {
+    uint4* q = reinterpret_cast<uint4*>(p);
+#pragma unroll
+    for (int i = 0; i < ZL / 8; ++i) {
+      uint32_t w[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(v[8 * i + 2 * j], v[8 * i + 2 * j + 1]);
+        w[j] = *reinterpret_cast<uint32_t*>(&h);
+      }
+      q[i] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < ZL; ++i) p[i] = from_c<S>(v[i]);
+  }
+}
+
+// ------------------------------------------------------------------ geometry
+// Detector coordinate u = x cos + y sin + off, split so that the y part is
+// shared by a row.  Single precision uses two fused multiply-adds,
+// u = fma(x, cos, fma(y, sin, off)); double precision uses separately rounded
+// products and sums, u = (x*cos) + ((y*sin) + off).  The projector and the
+// backprojector call exactly these functions, so their weights agree bit for
+// bit and P is the exact transpose of P^T up to summation order.
+__device__ __forceinline__ float geo_inner(float yf, float s, float off) { return fmaf(yf, s, off); }
+__device__ __forceinline__ float geo_outer(float xf, float c, float in) { return fmaf(xf, c, in); }
+__device__ __forceinline__ double geo_inner(double yf, double s, double off) {
+  return __dadd_rn(__dmul_rn(yf, s), off);
+}
+__device__ __forceinline__ double geo_outer(double xf, double c, double in) {
+  return __dadd_rn(__dmul_rn(xf, c), in);
+}
+
+template <typename C>
+struct Geo {
+  int nx, ny, nz, na, nd;
+  C cx, cy, off;            // (nx-1)/2, (ny-1)/2, (nd-1)/2
+  const C* cs;              // [na][2] cos, sin
+  const C* ex;              // [na][nx] exp(mu x sin) or nullptr (no attenuation)
+  const C* ey;              // [na][ny] exp(-mu y cos)
+  const C* es;              // [na][nd] vial entry factor (0 off the vial) or nullptr
+  double r2q;               // 4 R^2 (R = vial radius); <= 0: no vial
+  double vial_r;            // R
+};
+
+// Voxel (ix, iy) inside the vial: x^2 + y^2 <= R^2 evaluated exactly in
+// integers, (2ix - nx + 1)^2 + (2iy - ny + 1)^2 <= 4 R^2.
+template <typename C>
+__device__ __forceinline__ bool in_vial(const Geo<C>& g, int ix, int iy) {
+  if (g.r2q <= 0.0) return true;
+  long long a = 2LL * ix - (g.nx - 1), b = 2LL * iy - (g.ny - 1);
+  return double(a * a + b * b) <= g.r2q;
+}
+
+__device__ __forceinline__ float fl_(float x) { return floorf(x); }
+__device__ __forceinline__ double fl_(double x) { return floor(x); }
+
+// --------------------------------------------------------------- reductions
+// Deterministic block reduction of N doubles per thread: warp shuffles, then
+// one pass over the warps in fixed order; thread 0 writes the block partials
+// to part[slot * kRedBlocks + blockIdx.x].
+template <int N>
+__device__ __forceinline__ void block_reduce_store(double (&v)[N], double* part, int slot0) {
+  __shared__ double red[kWarps][N > 0 ? N : 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    double x = v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) red[warp][i] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < N) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) s += red[w][threadIdx.x];
+    part[(slot0 + threadIdx.x) * kRedBlocks + blockIdx.x] = s;
+  }
+}
+
+// Sum of one slot over all kRedBlocks partials, by one block, fixed order.
+__device__ __forceinline__ double block_sum_slot(const double* part, int slot) {
+  __shared__ double tmp[kThreads];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) s += part[slot * kRedBlocks + i];
+  tmp[threadIdx.x] = s;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) tmp[threadIdx.x] += tmp[threadIdx.x + st];
+    __syncthreads();
+  }
+  double r = tmp[0];
+  __syncthreads();
+  return r;
+}
+
+}  // namespace sipo

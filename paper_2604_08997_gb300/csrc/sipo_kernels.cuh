@@ -1,0 +1,536 @@
+// sipo_kernels.cuh -- setup, scalar, blend and post-solve kernels.
+//
+// Setup builds the domain partition of Sec. 2.2 (Fig. 2) with exact integer
+// logic: gel = {f_T != 0}; band = non-gel voxels within Euclidean distance
+// <= W of the gel (a windowed squared-distance transform, three separable
+// passes that are exact for every distance <= W) or inside the support of
+// K f_T (a box dilation by the PSF radii); exterior otherwise or outside the
+// vial.  The scalar kernels carry the FP64 logic of the restarted Halpern
+// PDHG (step sizes, u~/v~ updates of Eqs. 48-49, KKT of Sec. 6.1, restarts,
+// primal weight, infeasibility test).
+#pragma once
+
+#include "sipo_solver.cuh"
+
+namespace sipo {
+
+constexpr double kBetaSufficient = 0.2;
+constexpr double kBetaNecessary = 0.8;
+constexpr double kBetaArtificial = 0.36;
+constexpr double kOmegaSmoothing = 0.5;
+constexpr double kInfeasTol = 1e-6;
+constexpr int kDistInf = 0x3fffffff;
+
+// ------------------------------------------------------------ target stats
+struct TargetStats {
+  unsigned long long n_gel, n_bad;
+  unsigned int min_bits, max_bits;  // float bit patterns of non-negative values
+};
+
+__global__ void k_target_stats(const float* __restrict__ f, long long n, TargetStats* out) {
+  unsigned long long gel = 0, bad = 0;
+  unsigned int mn = 0x7f800000u, mx = 0u;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float v = f[i];
+    if (!(v >= 0.0f) || isinf(v)) { ++bad; continue; }   // NaN, negative or infinite
+    if (v != 0.0f) {
+      ++gel;
+      const unsigned int b = __float_as_uint(v);
+      mn = min(mn, b);
+      mx = max(mx, b);
+    }
+  }
+  atomicAdd(&out->n_gel, gel);
+  atomicAdd(&out->n_bad, bad);
+  atomicMin(&out->min_bits, mn);
+  atomicMax(&out->max_bits, mx);
+}
+
+// ----------------------------------------------------------------- labels
+// dist0[v] = 0 on gel, kDistInf elsewhere.
+__global__ void k_gel_init(const float* __restrict__ f, long long n, int* __restrict__ dist,
+                           uint8_t* __restrict__ lab) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const bool gel = f[i] != 0.0f;
+    dist[i] = gel ? 0 : kDistInf;
+    lab[i] = gel ? kGel : kExt;
+  }
+}
+
+// One separable pass of the windowed squared distance:
+// out[i] = min_{|m| <= W} (m^2 + in[i + m*stride]) along `axis`.  After the x,
+// y and z passes, out = min over gel voxels of the squared Euclidean distance
+// whenever that distance is <= W (larger distances stay > W^2).
+__global__ void k_dist_pass(const int* __restrict__ in, int* __restrict__ out, int W, int nx,
+                            int ny, int nz, int axis) {
+  const long long n = (long long)nx * ny * nz;
+  const long long stride = axis == 0 ? nz : (axis == 1 ? (long long)nx * nz : 1);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int z = int(idx % nz);
+    const long long r = idx / nz;
+    const int ix = int(r % nx), iy = int(r / nx);
+    const int a = axis == 0 ? ix : (axis == 1 ? iy : z);
+    const int na = axis == 0 ? nx : (axis == 1 ? ny : nz);
+    int best = kDistInf;
+    for (int m = max(-W, -a); m <= min(W, na - 1 - a); ++m) {
+      const int v = in[idx + m * stride];
+      if (v < kDistInf) best = min(best, v + m * m);
+    }
+    out[idx] = best;
+  }
+}
+
+// Box dilation pass: out[i] = any(in[i + m*stride]), |m| <= R.
+__global__ void k_dilate_pass(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, int R,
+                              int nx, int ny, int nz, int axis) {
+  const long long n = (long long)nx * ny * nz;
+  const long long stride = axis == 0 ? nz : (axis == 1 ? (long long)nx * nz : 1);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int z = int(idx % nz);
+    const long long r = idx / nz;
+    const int ix = int(r % nx), iy = int(r / nx);
+    const int a = axis == 0 ? ix : (axis == 1 ? iy : z);
+    const int na = axis == 0 ? nx : (axis == 1 ? ny : nz);
+    uint8_t any = 0;
+    for (int m = max(-R, -a); m <= min(R, na - 1 - a); ++m) any |= in[idx + m * stride];
+    out[idx] = any ? 1 : 0;
+  }
+}
+
+__global__ void k_gel_mask(const uint8_t* __restrict__ lab, uint8_t* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = lab[i] == kGel ? 1 : 0;
+}
+
+// Final labels: band = non-gel & (dist^2 <= W^2 | psf support | band-free),
+// inside the vial.
+template <typename C>
+__global__ void k_labels_final(uint8_t* __restrict__ lab, const int* __restrict__ dist,
+                               const uint8_t* __restrict__ psf_sup, int W, int band_free,
+                               Geo<C> g) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    if (lab[idx] == kGel) continue;
+    const long long r = idx / g.nz;
+    const int ix = int(r % g.nx), iy = int(r / g.nx);
+    bool band = band_free != 0;
+    if (!band && W >= 0 && dist[idx] <= W * W) band = true;
+    if (!band && psf_sup != nullptr && psf_sup[idx]) band = true;
+    lab[idx] = (band && in_vial(g, ix, iy)) ? kBand : kExt;
+  }
+}
+
+// Column flag: any non-exterior voxel along z of (iy, ix).
+__global__ void k_need_cols(const uint8_t* __restrict__ lab, uint8_t* __restrict__ need, int nx,
+                            int ny, int nz) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < (long long)nx * ny;
+       c += (long long)gridDim.x * blockDim.x) {
+    uint8_t any = 0;
+    for (int z = 0; z < nz; ++z) any |= lab[c * nz + z] != kExt;
+    need[c] = any;
+  }
+}
+
+// 2-D box dilation of a column flag (PSF reach in x and y).
+__global__ void k_dilate_cols(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, int nx,
+                              int ny, int Rx, int Ry) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < (long long)nx * ny;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int ix = int(c % nx), iy = int(c / nx);
+    uint8_t any = 0;
+    for (int a = max(0, iy - Ry); a <= min(ny - 1, iy + Ry) && !any; ++a)
+      for (int b = max(0, ix - Rx); b <= min(nx - 1, ix + Rx); ++b) any |= in[(size_t)a * nx + b];
+    out[c] = any;
+  }
+}
+
+// Normalised lower profile f~ on gel (Sec. 2.5, Eq. 31, Eq. 39).
+template <typename C>
+__global__ void k_ft(const float* __restrict__ f, const uint8_t* __restrict__ lab, double mult,
+                     C* __restrict__ ft, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    ft[i] = lab[i] == kGel ? C(double(f[i]) * mult) : C(0);
+}
+
+template <typename TI, typename TO>
+__global__ void k_convert(const TI* __restrict__ in, TO* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = from_c<TO>(to_c(in[i]));
+}
+
+// Indicator volume 1_band + 2 * 1_gel (column abs-sums of G, Pock-Chambolle).
+template <typename C>
+__global__ void k_row_indicator(const uint8_t* __restrict__ lab, C* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = lab[i] == kGel ? C(2) : (lab[i] == kBand ? C(1) : C(0));
+}
+
+// Active rays: mask = [P f_T] > 0; ones = mask as C; per (angle, bin) flag.
+template <typename C>
+__global__ void k_mask(const C* __restrict__ pf, uint8_t* __restrict__ mask, C* __restrict__ ones,
+                       long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const bool a = pf[i] > C(0);
+    mask[i] = a ? 1 : 0;
+    ones[i] = a ? C(1) : C(0);
+  }
+}
+
+__global__ void k_act_cols(const uint8_t* __restrict__ mask, uint8_t* __restrict__ act, long long nrays,
+                           int nz) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nrays;
+       r += (long long)gridDim.x * blockDim.x) {
+    uint8_t any = 0;
+    for (int z = 0; z < nz; ++z) any |= mask[r * nz + z];
+    act[r] = any;
+  }
+}
+
+template <typename C>
+__global__ void k_apply_mask(C* __restrict__ col, const uint8_t* __restrict__ mask, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    if (!mask[i]) col[i] = C(0);
+}
+
+// Setup sums (FP64 partials per block, summed on the host):
+// 0 |band|, 1 |gel|, 2 sum_gel f~, 3 sum_gel f~^2, 4 sum_gel (f~ up_ratio)^2,
+// 5 sum U0^2 / row_up over up rows, 6 sum_gel f~^2 / row_lo.
+template <typename C>
+__global__ void k_setup_sums(const uint8_t* __restrict__ lab, const C* __restrict__ ft, C ft_const,
+                             const C* __restrict__ row, double up_ratio, int has_u, int has_v,
+                             int kase, long long n, double* __restrict__ part) {
+  double v[7] = {};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const uint8_t l = lab[i];
+    if (l == kExt) continue;
+    const double f = ft ? double(ft[i]) : double(ft_const);
+    const double r = double(row[i]);
+    if (l == kBand) {
+      v[0] += 1.0;
+      const double rup = r + (has_u ? 1.0 : 0.0);
+      const double U0 = has_u ? 0.0 : 1.0;
+      if (rup > 0) v[5] += U0 * U0 / rup;
+    } else {
+      v[1] += 1.0;
+      v[2] += f;
+      v[3] += f * f;
+      v[4] += f * up_ratio * f * up_ratio;
+      const double rup = r + (has_v ? f : 0.0);
+      const double U0 = has_v ? 0.0 : f * up_ratio;
+      if (rup > 0) v[5] += U0 * U0 / rup;
+      if (r > 0) v[6] += f * f / r;
+    }
+  }
+  (void)kase;
+  block_reduce_store<7>(v, part, 0);
+}
+
+// ---------------------------------------------------------- scalar kernels
+// One block.  Gradient step of the scalars from the dual sums (Eqs. 48-49),
+// extrapolation, Halpern weight; outside check steps also the Halpern blend.
+template <bool CHECK>
+__global__ void __launch_bounds__(kThreads) k_scalar_step(Scal* st, const double* part) {
+  if (st->done) return;
+  const double Sb = block_sum_slot(part, kSlSBand);
+  const double Sg = block_sum_slot(part, kSlSGel);
+  if (threadIdx.x != 0) return;
+  const double om = st->omega;
+  double up = st->u, vp = st->v;
+  if (st->has_u && st->col_u > 0) {
+    up = st->u - kEta / (om * st->col_u) * (st->c_u - Sb);
+    if (up < 0.0) up = 0.0;
+  }
+  if (st->has_v && st->col_v > 0) {
+    vp = st->v - kEta / (om * st->col_v) * (st->c_v - Sg);
+    if (vp < 1.0) vp = 1.0;
+  }
+  st->up = up;
+  st->vp = vp;
+  st->ubar = 2.0 * up - st->u;
+  st->vbar = 2.0 * vp - st->v;
+  const double w = (double(st->k_in) + 1.0) / (double(st->k_in) + 2.0);
+  st->w = w;
+  if (!CHECK) {
+    st->u = w * st->ubar + (1.0 - w) * st->u0;
+    st->v = w * st->vbar + (1.0 - w) * st->v0;
+    st->k_in += 1;
+    st->k += 1;
+  }
+}
+
+// One block.  KKT of T(z) (Sec. 6.1), termination, Farkas test, restart
+// decision and primal-weight update, then the scalar Halpern blend.
+__global__ void __launch_bounds__(kThreads) k_scalar_check(Scal* st, const double* part) {
+  if (st->done) return;
+  double s[kNumSlots];
+  for (int i = kSlRp2; i < kNumSlots; ++i) s[i] = block_sum_slot(part, i);
+  if (threadIdx.x != 0) return;
+  const double up = st->up, vp = st->vp, u = st->u, v = st->v, u0 = st->u0, v0 = st->v0;
+  double om = st->omega;
+  const double SbP = s[kSlSBandP], SgP = s[kSlSGelP];
+  double rd2 = s[kSlRd2], rd2s = s[kSlRd2s];
+  double pobj = 0.0, dobj = s[kSlDobL];
+  if (st->has_u) {
+    const double r = fmin(st->c_u - SbP, 0.0);
+    rd2 += r * r;
+    if (st->col_u > 0) rd2s += r * r / st->col_u;
+    pobj += st->c_u * up;
+  } else {
+    dobj -= st->band_rhs * SbP;
+  }
+  if (st->has_v) {
+    const double r = st->c_v - SgP;
+    const double m = fmin(r, 0.0);
+    rd2 += m * m;
+    if (st->col_v > 0) rd2s += m * m / st->col_v;
+    dobj += fmax(r, 0.0);
+    pobj += st->c_v * vp;
+  } else {
+    dobj -= s[kSlDobU];
+  }
+  const double rp = sqrt(s[kSlRp2]), rd = sqrt(rd2);
+  const double rel_p = rp / (1.0 + st->h_norm), rel_d = rd / (1.0 + st->c_norm);
+  const double gap = fabs(pobj - dobj);
+  const double rel_gap = gap / (1.0 + fabs(pobj) + fabs(dobj));
+  st->rp = rp; st->rd = rd; st->rel_p = rel_p; st->rel_d = rel_d; st->gap = gap;
+  st->rel_gap = rel_gap; st->pobj = pobj; st->dobj = dobj;
+  st->kkt = fmax(rel_p, fmax(rel_d, rel_gap));
+  st->sband_p = SbP; st->sgel_p = SgP;
+  int status = -1;
+  if (rel_p <= st->kkt_tol && rel_d <= st->kkt_tol && rel_gap <= st->kkt_tol) {
+    status = 0;
+  } else if (st->k > 0) {
+    // Farkas ray from the dual difference since the last restart
+    double obj = s[kSlFkL], ru = 0.0, rv = 0.0;
+    if (st->has_u) ru = -s[kSlFkBand];
+    else obj -= st->band_rhs * s[kSlFkBand];
+    if (st->has_v) { rv = -s[kSlFkGel]; obj += fmax(rv, 0.0); }
+    else obj -= s[kSlFkUp];
+    if (obj > 0.0) {
+      const double viol2 = s[kSlFkG] + fmin(ru, 0.0) * fmin(ru, 0.0) +
+                           fmin(rv, 0.0) * fmin(rv, 0.0) + s[kSlFkNeg];
+      if (sqrt(viol2) / obj <= kInfeasTol) status = 1;
+    }
+  }
+  if (status < 0 && st->k >= st->max_iter) status = 3;
+  if (status >= 0) {
+    st->status = status;
+    st->done = 1;
+    return;
+  }
+  const double r = sqrt(om * (s[kSlFpX] + st->col_u * (u - up) * (u - up) +
+                              st->col_v * (v - vp) * (v - vp)) + s[kSlFpL] / om);
+  int restart = 0;
+  if (!st->r0_set) {
+    st->r0 = r;
+    st->r0_set = 1;
+  } else if (r <= kBetaSufficient * st->r0 || (r <= kBetaNecessary * st->r0 && r > st->r_prev) ||
+             double(st->k_in) >= kBetaArtificial * double(st->k)) {
+    restart = 1;
+  }
+  st->r_prev = r;
+  if (restart) {
+    const double ex2 = s[kSlOmX] + st->col_u * (up - u0) * (up - u0) + st->col_v * (vp - v0) * (vp - v0);
+    const double el2 = s[kSlOmL];
+    if (ex2 > 1e-30 && el2 > 1e-30)
+      om = exp(kOmegaSmoothing * 0.5 * log(el2 / ex2) + (1.0 - kOmegaSmoothing) * log(om));
+    st->omega = om;
+    st->u = up; st->v = vp; st->u0 = up; st->v0 = vp;
+    st->k_in = 0;
+    st->r0 = r;
+    st->r_prev = r;
+    st->restarts += 1;
+  } else {
+    const double w = st->w;
+    st->u = w * (2.0 * up - u) + (1.0 - w) * u0;
+    st->v = w * (2.0 * vp - v) + (1.0 - w) * v0;
+    st->k_in += 1;
+  }
+  st->restart = restart;
+  st->k += 1;
+}
+
+// --------------------------------------------------------- blend kernels
+// After a check step: next iterate = T(z) (restart) or the Halpern blend.
+template <typename S, typename C, int ZL>
+__global__ void __launch_bounds__(kThreads) k_blend_sino(Bufs<S, C> b, long long nvec) {
+  if (b.st->done) return;
+  const int restart = b.st->restart;
+  const C w = C(b.st->w);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nvec;
+       i += (long long)gridDim.x * blockDim.x) {
+    const size_t base = size_t(i) * ZL;
+    C col[ZL];
+    load_z<C, C, ZL>(b.col + base, col);
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < ZL; ++k) any |= col[k] > C(0);
+    if (!any) continue;
+    C yp[ZL];
+    load_z<S, C, ZL>(b.yp + base, yp);
+    if (restart) {
+      store_z<S, C, ZL>(b.y + base, yp);
+      store_z<S, C, ZL>(b.y0 + base, yp);
+      C gp[ZL];
+      load_z<C, C, ZL>(b.gp + base, gp);
+      store_z<C, C, ZL>(b.g0 + base, gp);
+    } else {
+      C y[ZL], y0[ZL];
+      load_z<S, C, ZL>(b.y + base, y);
+      load_z<S, C, ZL>(b.y0 + base, y0);
+#pragma unroll
+      for (int k = 0; k < ZL; ++k) y[k] = w * (C(2) * yp[k] - y[k]) + (C(1) - w) * y0[k];
+      store_z<S, C, ZL>(b.y + base, y);
+    }
+  }
+}
+
+template <typename S, typename C, int ZL>
+__global__ void __launch_bounds__(kThreads) k_blend_vol(Bufs<S, C> b, long long nvec) {
+  if (b.st->done) return;
+  const int restart = b.st->restart;
+  const C w = C(b.st->w);
+  double red[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nvec;
+       i += (long long)gridDim.x * blockDim.x) {
+    const size_t base = size_t(i) * ZL;
+    uint8_t lab[ZL];
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < ZL; ++k) { lab[k] = b.lab[base + k]; any |= lab[k] != kExt; }
+    if (!any) continue;
+    C pu[ZL], pl[ZL], dp[ZL], ft[ZL];
+    load_z<S, C, ZL>(b.lpu + base, pu);
+    load_z<S, C, ZL>(b.lpl + base, pl);
+    load_z<C, C, ZL>(b.dp + base, dp);
+    if (b.ft) load_z<C, C, ZL>(b.ft + base, ft);
+    else {
+#pragma unroll
+      for (int k = 0; k < ZL; ++k) ft[k] = b.ft_const;
+    }
+    C nu[ZL], nl[ZL], nd[ZL], nq[ZL];
+    if (restart) {
+#pragma unroll
+      for (int k = 0; k < ZL; ++k) { nu[k] = pu[k]; nl[k] = pl[k]; nd[k] = dp[k]; }
+      store_z<S, C, ZL>(b.lu0 + base, pu);
+      store_z<S, C, ZL>(b.ll0 + base, pl);
+      store_z<C, C, ZL>(b.d0 + base, dp);
+    } else {
+      C lu[ZL], ll[ZL], lu0[ZL], ll0[ZL], d[ZL], d0[ZL];
+      load_z<S, C, ZL>(b.lu + base, lu);
+      load_z<S, C, ZL>(b.ll + base, ll);
+      load_z<S, C, ZL>(b.lu0 + base, lu0);
+      load_z<S, C, ZL>(b.ll0 + base, ll0);
+      load_z<C, C, ZL>(b.d + base, d);
+      load_z<C, C, ZL>(b.d0 + base, d0);
+#pragma unroll
+      for (int k = 0; k < ZL; ++k) {
+        nu[k] = rnd<S, C>(w * (C(2) * pu[k] - lu[k]) + (C(1) - w) * lu0[k]);
+        nl[k] = rnd<S, C>(w * (C(2) * pl[k] - ll[k]) + (C(1) - w) * ll0[k]);
+        nd[k] = w * (C(2) * dp[k] - d[k]) + (C(1) - w) * d0[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < ZL; ++k) {
+      if (lab[k] == kExt) { nu[k] = C(0); nl[k] = C(0); }
+      nq[k] = nu[k] - nl[k];
+      if (lab[k] == kBand) red[0] += double(nu[k]);
+      else if (lab[k] == kGel) red[1] += double(ft[k]) * double(nu[k]);
+    }
+    store_z<S, C, ZL>(b.lu + base, nu);
+    store_z<S, C, ZL>(b.ll + base, nl);
+    store_z<C, C, ZL>(b.d + base, nd);
+    store_z<S, C, ZL>(b.q + base, nq);
+  }
+  block_reduce_store<2>(red, b.part, kSlSBand);
+}
+
+// Stand-alone dual update (used when the PSF sits between P^T and the prox).
+template <typename S, typename C, int ZL, bool CHECK>
+__global__ void __launch_bounds__(kThreads) k_dual(Bufs<S, C> b, const C* __restrict__ dbar,
+                                                   long long nvec) {
+  if (b.st->done) return;
+  const StepScalars<C> sc = read_scalars<C>(b.st);
+  constexpr int NR = CHECK ? 13 : 2;
+  double red[NR] = {};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nvec;
+       i += (long long)gridDim.x * blockDim.x) {
+    const size_t base = size_t(i) * ZL;
+    C db[ZL];
+    load_z<C, C, ZL>(dbar + base, db);
+    dual_update<S, C, ZL, CHECK>(b, sc, base, db, red);
+  }
+  block_reduce_store<NR>(red, b.part, CHECK ? kSlRp2 : kSlSBand);
+}
+
+// --------------------------------------------------------- post-solve
+// Per block: 0 min_gel d/f~T, 1 max_gel d/f~T, 2 max_band d, 3 min_gel d,
+// 4 sum_gel d f_T, 5 sum_gel d^2, 6 min_gel d / f~ (recovered scale s),
+// 7 max_gel d / f~ (maximum relative dose of the LP).
+template <typename C>
+__global__ void __launch_bounds__(kThreads)
+k_metrics(const C* __restrict__ d, const uint8_t* __restrict__ lab, const float* __restrict__ fT,
+          const C* __restrict__ ft, C ft_const, double f_crit, long long n, double* __restrict__ part) {
+  double mn_r = 1e300, mx_r = -1e300, mx_b = -1e300, mn_d = 1e300, sdf = 0.0, sdd = 0.0;
+  double mn_s = 1e300, mx_s = -1e300;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const uint8_t l = lab[i];
+    if (l == kBand) {
+      mx_b = fmax(mx_b, double(d[i]));
+    } else if (l == kGel) {
+      const double dv = double(d[i]);
+      const double ftT = double(fT[i]) / f_crit;
+      const double r = dv / ftT;
+      mn_r = fmin(mn_r, r);
+      mx_r = fmax(mx_r, r);
+      mn_d = fmin(mn_d, dv);
+      sdf += dv * double(fT[i]);
+      sdd += dv * dv;
+      const double fl = ft ? double(ft[i]) : double(ft_const);
+      mn_s = fmin(mn_s, dv / fl);
+      mx_s = fmax(mx_s, dv / fl);
+    }
+  }
+  __shared__ double sh[kThreads];
+  double vals[8] = {mn_r, mx_r, mx_b, mn_d, sdf, sdd, mn_s, mx_s};
+  for (int q = 0; q < 8; ++q) {
+    sh[threadIdx.x] = vals[q];
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) {
+        const double a = sh[threadIdx.x], c = sh[threadIdx.x + st];
+        sh[threadIdx.x] = (q == 0 || q == 3 || q == 6) ? fmin(a, c)
+                          : (q == 4 || q == 5) ? a + c : fmax(a, c);
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[q * kRedBlocks + blockIdx.x] = sh[0];
+    __syncthreads();
+  }
+}
+
+// < a, b > per block (for the PSF sigma gradient).
+template <typename C>
+__global__ void __launch_bounds__(kThreads) k_dot(const C* __restrict__ a, const C* __restrict__ b,
+                                                  long long n, double* __restrict__ part) {
+  double v[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    v[0] += double(a[i]) * double(b[i]);
+  block_reduce_store<1>(v, part, 0);
+}
+
+}  // namespace sipo

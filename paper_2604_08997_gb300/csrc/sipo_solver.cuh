@@ -1,0 +1,298 @@
+// sipo_solver.cuh -- solver state and the per-element PDHG updates.
+//
+// The LP (general Eqs. 19-24, Case 1 Eqs. 32-37, Case 2 Eqs. 40-45) is solved
+// as  min c^T x  s.t.  G x <= h  over x = (y, u~, v~) with up rows on band and
+// gel voxels (d_i <= U_i) and lo rows on gel voxels (d_i >= L_i), d = A^T y.
+// Iterates: sinogram y >= 0 (0 on masked rays), scalars u~ >= 0 and v~ >= 1
+// (implied bounds), duals lam_up (band and gel up rows) and lam_lo (gel lo rows).
+//
+// One PDHG step T(z) is split over three kernels:
+//   scalar step   u+, v+ from the dual sums (Eqs. 48-49 gradients)
+//   projector     g = A (lam_up - lam_lo) (Eq. 51), then y+ = max(0, y - tau g)
+//   backprojector d_bar = A^T (2 y+ - y), then the dual prox on every row
+// and the restarted Halpern iteration z <- w (2 T(z) - z) + (1 - w) z0 is
+// fused into the same epilogues.  Every `check_every` iterations the step
+// instead writes T(z) to separate buffers, evaluates its KKT error, and a
+// scalar kernel decides termination, infeasibility and restarts before a
+// blend kernel forms the next iterate.
+#pragma once
+
+#include "sipo_device.cuh"
+
+namespace sipo {
+
+// Reduction slots (each holds kRedBlocks partials).
+enum Slot : int {
+  kSlSBand = 0,   // sum_band lam_up of the current iterate          (Eq. 48)
+  kSlSGel,        // sum_gel f~ lam_up of the current iterate        (Eq. 49)
+  // backprojector, check step (13 slots, contiguous)
+  kSlRp2,         // unscaled primal residual^2 of T(z)
+  kSlRp2s,        // preconditioned primal residual^2
+  kSlDobL,        // sum_gel L lam_lo+          (dual objective)
+  kSlDobU,        // sum_gel f~_U lam_up+       (dual objective, Case 1)
+  kSlSBandP,      // sum_band lam_up+
+  kSlSGelP,       // sum_gel f~ lam_up+
+  kSlFpL,         // ||lam - lam+||^2_row       (fixed-point residual, dual part)
+  kSlOmL,         // ||lam+ - lam0||^2_row      (primal-weight update)
+  kSlFkL,         // Farkas: sum_gel L dlam_lo
+  kSlFkBand,      // Farkas: sum_band dlam_up
+  kSlFkGel,       // Farkas: sum_gel f~ dlam_up
+  kSlFkUp,        // Farkas: sum_gel f~_U dlam_up
+  kSlFkNeg,       // Farkas: ||min(dlam, 0)||^2
+  // projector, check step
+  kSlFpX,         // ||y - y+||^2_col
+  kSlOmX,         // ||y+ - y0||^2_col
+  // projector on q+ (dual residual of T(z))
+  kSlRd2,         // ||min(g+, 0)||^2 on active rays
+  kSlRd2s,        // preconditioned
+  kSlFkG,         // Farkas: ||min(g+ - g0, 0)||^2 on active rays
+  kNumSlots
+};
+
+// FP64 scalar state of one solve (device memory, one per context).
+struct Scal {
+  // problem constants
+  double c_u, c_v, band_rhs, col_u, col_v, h_norm, c_norm, kkt_tol;
+  int has_u, has_v;
+  long long max_iter;
+  // scalar iterates
+  double u, v, u0, v0, up, vp, ubar, vbar;
+  double omega, w;
+  long long k, k_in;
+  double r0, r_prev;
+  int r0_set, done, status, restart, restarts, pad;
+  // KKT data of the last check
+  double kkt, rel_p, rel_d, rel_gap, rp, rd, pobj, dobj, gap, sband_p, sgel_p;
+};
+
+// Device arrays of one solve.  S: storage type of iterates, C: compute type.
+template <typename S, typename C>
+struct Bufs {
+  // sinogram-sized
+  S *y, *y0, *yp, *ybar;
+  const C* col;         // Pock-Chambolle column abs-sum of each ray (0: masked)
+  C *gp, *g0;           // A q+ at the last check / at the last restart
+  // volume-sized
+  S *lu, *ll, *lu0, *ll0, *lpu, *lpl, *q, *qp;
+  C *d, *d0, *dp;       // A^T y (current, anchor, T point) on band and gel
+  const C* row;         // A^T 1_act (row abs-sum of A^T over active rays)
+  const C* ft;          // normalised lower profile f~ (nullptr: ft_const)
+  const uint8_t* lab;   // region labels
+  C ft_const;
+  C up_ratio;           // Case 1: f~_U / f~_L
+  int has_u, has_v;
+  C band_rhs;           // right side of band rows: 0 (u~ variable) or 1 (Case 2)
+  Scal* st;
+  double* part;
+};
+
+// Halpern weights and steps read once per kernel.
+template <typename C>
+struct StepScalars {
+  C omega, w, ubar, vbar, up, vp;
+};
+
+template <typename C>
+__device__ __forceinline__ StepScalars<C> read_scalars(const Scal* st) {
+  StepScalars<C> s;
+  s.omega = C(st->omega);
+  s.w = C(st->w);
+  s.ubar = C(st->ubar);
+  s.vbar = C(st->vbar);
+  s.up = C(st->up);
+  s.vp = C(st->vp);
+  return s;
+}
+
+template <typename S, typename C>
+__device__ __forceinline__ C rnd(C x) {  // value after a round trip through S
+  return to_c(from_c<S>(x));
+}
+
+// ------------------------------------------------------------- dual update
+// One z-vector of voxels.  CHECK = false: Halpern step fused (writes the next
+// iterate and the dual sums of Eqs. 48-49).  CHECK = true: writes T(z) and
+// accumulates its residuals, objective pieces and restart distances.
+// Reduction accumulators: red[0..1] normal, red[0..12] check (slots 2..14).
+template <typename S, typename C, int ZL, bool CHECK>
+__device__ __forceinline__ void dual_update(const Bufs<S, C>& b, const StepScalars<C>& sc,
+                                            size_t base, const C (&dbar)[ZL],
+                                            double* red) {
+  uint8_t lab[ZL];
+  if constexpr (ZL % 8 == 0) {
+    const uint2* p = reinterpret_cast<const uint2*>(b.lab + base);
+#pragma unroll
+    for (int i = 0; i < ZL / 8; ++i) {
+      uint2 r = __ldg(p + i);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) lab[8 * i + j] = (r.x >> (8 * j)) & 0xff;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) lab[8 * i + 4 + j] = (r.y >> (8 * j)) & 0xff;
+    }
+  } else if constexpr (ZL % 4 == 0) {
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(b.lab + base);
+#pragma unroll
+    for (int i = 0; i < ZL / 4; ++i) {
+      uint32_t r = __ldg(p + i);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) lab[4 * i + j] = (r >> (8 * j)) & 0xff;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < ZL; ++i) lab[i] = b.lab[base + i];
+  }
+  bool any = false;
+#pragma unroll
+  for (int i = 0; i < ZL; ++i) any |= (lab[i] != kExt);
+  if (!any) return;
+
+  C ft[ZL], row[ZL], lu[ZL], ll[ZL], lu0[ZL], ll0[ZL];
+  if (b.ft) load_z<C, C, ZL>(b.ft + base, ft);
+  else {
+#pragma unroll
+    for (int i = 0; i < ZL; ++i) ft[i] = b.ft_const;
+  }
+  load_z<C, C, ZL>(b.row + base, row);
+  load_z<S, C, ZL>(b.lu + base, lu);
+  load_z<S, C, ZL>(b.ll + base, ll);
+  load_z<S, C, ZL>(b.lu0 + base, lu0);
+  load_z<S, C, ZL>(b.ll0 + base, ll0);
+  const C eo = C(kEta) * sc.omega;
+  const C w = sc.w;
+  C o_lu[ZL], o_ll[ZL], o_q[ZL], o_d[ZL];
+  C dcur[ZL], d0[ZL];
+  if constexpr (CHECK) load_z<C, C, ZL>(b.d + base, dcur);
+  else load_z<C, C, ZL>(b.d0 + base, d0);
+#pragma unroll
+  for (int i = 0; i < ZL; ++i) {
+    const bool band = lab[i] == kBand, gel = lab[i] == kGel;
+    if (!band && !gel) {
+      o_lu[i] = C(0); o_ll[i] = C(0); o_q[i] = C(0);
+      o_d[i] = CHECK ? dcur[i] : d0[i];
+      continue;
+    }
+    const C f = ft[i];
+    const C extra = band ? (b.has_u ? C(1) : C(0)) : (b.has_v ? f : C(0));
+    const C rup = row[i] + extra;
+    const C sig_up = rup > C(0) ? eo / rup : C(0);
+    const C Ubar = band ? (b.has_u ? sc.ubar : b.band_rhs) : (b.has_v ? sc.vbar * f : f * b.up_ratio);
+    C lup = lu[i] + sig_up * (dbar[i] - Ubar);
+    lup = rnd<S, C>(lup > C(0) ? lup : C(0));
+    C llp = C(0);
+    if (gel) {
+      const C sig_lo = row[i] > C(0) ? eo / row[i] : C(0);
+      llp = ll[i] + sig_lo * (f - dbar[i]);
+      llp = rnd<S, C>(llp > C(0) ? llp : C(0));
+    }
+    if constexpr (!CHECK) {
+      C lun = rnd<S, C>(w * (C(2) * lup - lu[i]) + (C(1) - w) * lu0[i]);
+      C lln = gel ? rnd<S, C>(w * (C(2) * llp - ll[i]) + (C(1) - w) * ll0[i]) : C(0);
+      o_lu[i] = lun;
+      o_ll[i] = lln;
+      o_q[i] = lun - lln;
+      o_d[i] = w * dbar[i] + (C(1) - w) * d0[i];
+      if (band) red[0] += double(lun);
+      else red[1] += double(f) * double(lun);
+    } else {
+      const C dp = C(0.5) * (dbar[i] + dcur[i]);
+      o_lu[i] = lup;
+      o_ll[i] = llp;
+      o_q[i] = lup - llp;
+      o_d[i] = dp;
+      const C Ucur = band ? (b.has_u ? sc.up : b.band_rhs) : (b.has_v ? sc.vp * f : f * b.up_ratio);
+      const double eu = double(dp) > double(Ucur) ? double(dp) - double(Ucur) : 0.0;
+      red[0] += eu * eu;
+      if (rup > C(0)) red[1] += eu * eu / double(rup);
+      const double dlu = double(lup) - double(lu0[i]);
+      red[6] += double(rup) * (double(lu[i]) - double(lup)) * (double(lu[i]) - double(lup));
+      red[7] += double(rup) * dlu * dlu;
+      red[12] += dlu < 0.0 ? dlu * dlu : 0.0;
+      if (band) {
+        red[4] += double(lup);
+        red[9] += dlu;
+      } else {
+        const double el = double(f) > double(dp) ? double(f) - double(dp) : 0.0;
+        red[0] += el * el;
+        if (row[i] > C(0)) red[1] += el * el / double(row[i]);
+        const double dll = double(llp) - double(ll0[i]);
+        red[2] += double(f) * double(llp);
+        red[3] += double(f) * double(b.up_ratio) * double(lup);
+        red[5] += double(f) * double(lup);
+        red[6] += double(row[i]) * (double(ll[i]) - double(llp)) * (double(ll[i]) - double(llp));
+        red[7] += double(row[i]) * dll * dll;
+        red[8] += double(f) * dll;
+        red[10] += double(f) * dlu;
+        red[11] += double(f) * double(b.up_ratio) * dlu;
+        red[12] += dll < 0.0 ? dll * dll : 0.0;
+      }
+    }
+  }
+  if constexpr (!CHECK) {
+    store_z<S, C, ZL>(b.lu + base, o_lu);
+    store_z<S, C, ZL>(b.ll + base, o_ll);
+    store_z<S, C, ZL>(b.q + base, o_q);
+    store_z<C, C, ZL>(b.d + base, o_d);
+  } else {
+    store_z<S, C, ZL>(b.lpu + base, o_lu);
+    store_z<S, C, ZL>(b.lpl + base, o_ll);
+    store_z<S, C, ZL>(b.qp + base, o_q);
+    store_z<C, C, ZL>(b.dp + base, o_d);
+  }
+}
+
+// ----------------------------------------------------------- primal update
+// One z-vector of rays with g = A q already formed.  CHECK = false: Halpern
+// step fused; CHECK = true: writes y+ and the restart distances (red[0..1]).
+template <typename S, typename C, int ZL, bool CHECK>
+__device__ __forceinline__ void primal_update(const Bufs<S, C>& b, const StepScalars<C>& sc,
+                                              size_t base, const C (&g)[ZL], double* red) {
+  C col[ZL], y[ZL], y0[ZL], yb[ZL], yo[ZL];
+  load_z<C, C, ZL>(b.col + base, col);
+  bool any = false;
+#pragma unroll
+  for (int i = 0; i < ZL; ++i) any |= col[i] > C(0);
+  if (!any) return;  // every ray of the vector is masked: y, y_bar stay 0
+  load_z<S, C, ZL>(b.y + base, y);
+  load_z<S, C, ZL>(b.y0 + base, y0);
+  const C w = sc.w;
+#pragma unroll
+  for (int i = 0; i < ZL; ++i) {
+    const C tau = col[i] > C(0) ? C(kEta) / (sc.omega * col[i]) : C(0);
+    C yp = y[i] - tau * g[i];
+    yp = rnd<S, C>(yp > C(0) ? yp : C(0));
+    yb[i] = rnd<S, C>(C(2) * yp - y[i]);
+    if constexpr (!CHECK) {
+      yo[i] = w * yb[i] + (C(1) - w) * y0[i];
+    } else {
+      yo[i] = yp;
+      const double dx = double(y[i]) - double(yp), dz = double(yp) - double(y0[i]);
+      red[0] += double(col[i]) * dx * dx;
+      red[1] += double(col[i]) * dz * dz;
+    }
+  }
+  store_z<S, C, ZL>(b.ybar + base, yb);
+  if constexpr (!CHECK) store_z<S, C, ZL>(b.y + base, yo);
+  else store_z<S, C, ZL>(b.yp + base, yo);
+}
+
+// Dual residual of T(z) on active rays from g+ = A q+ (red[0..2]).
+template <typename S, typename C, int ZL>
+__device__ __forceinline__ void resid_update(const Bufs<S, C>& b, size_t base, const C (&g)[ZL],
+                                             double* red) {
+  C col[ZL], g0[ZL];
+  load_z<C, C, ZL>(b.col + base, col);
+  load_z<C, C, ZL>(b.g0 + base, g0);
+#pragma unroll
+  for (int i = 0; i < ZL; ++i) {
+    if (col[i] > C(0)) {
+      const double m = g[i] < C(0) ? double(g[i]) : 0.0;
+      red[0] += m * m;
+      red[1] += m * m / double(col[i]);
+      const double f = double(g[i]) - double(g0[i]);
+      red[2] += f < 0.0 ? f * f : 0.0;
+    }
+  }
+  store_z<C, C, ZL>(b.gp + base, g);
+}
+
+}  // namespace sipo

@@ -1,0 +1,154 @@
+"""GPU PDHG solves against exact optima, the oracle PDHG and FP64 certificates.
+
+y* is not unique (A has a large null space), so parity is on objectives, KKT
+errors, feasibility and statuses, never on y element by element.  The FP64
+GPU solver and the oracle implement the same restarted Halpern PDHG, so on
+the same instance their iterates agree to rounding for as long as no restart
+decision flips; the iteration-matched test checks that.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import pdhg, simplex
+from oracle.lp import CaseParams, build_lp, kkt, metrics
+from oracle.operators import Geometry
+from synthetic.targets import csg_3d, discs_2d, uniform_angles, workload
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+TINY = [(0, {}), (1, dict(tol_lo=0.1, tol_hi=0.1)), (2, dict(inhibit_ratio=0.6))]
+
+
+@pytest.fixture(scope="module")
+def sipo():
+    import paper_2604_08997_gb300 as s
+    s.build()
+    return s
+
+
+def _tiny(case, extra, n=10, na=8, nd=15):
+    tgt = discs_2d(n, n_discs=1, r_range=(2.0, 3.0), container_radius=4.0, seed=3)
+    ang = uniform_angles(na)
+    lp, ops = build_lp(Geometry(n, n, 1, ang, nd), tgt, CaseParams(case=case, band_width=2, **extra))
+    geo = dict(nx=n, ny=n, nz=1, angles=ang, n_det=nd)
+    cp = dict(kase=case, band_width=2, **extra)
+    return lp, ops, geo, tgt, cp
+
+
+@pytest.mark.parametrize("case,extra", TINY)
+def test_tiny_lp_fp64_matches_simplex(sipo, case, extra):
+    lp, ops, geo, tgt, cp = _tiny(case, extra)
+    st, obj, _ = simplex.solve_dense(lp, ops)
+    ctx = sipo.sipo_create(geo, tgt, cp, dict(storage=sipo.SIPO_F64, kkt_tol=1e-10, max_iter=100000))
+    res = sipo.sipo_solve(ctx)
+    assert st == "optimal" and res["status"] == sipo.SIPO_OPTIMAL
+    assert abs(res["pobj"] - obj) <= 1e-7 * abs(obj)
+    assert abs(res["s"] - 1.0) < 1e-6          # recovered Charnes-Cooper scale t = 1/s = 1
+
+
+@pytest.mark.parametrize("case,extra", TINY)
+def test_tiny_lp_fp32_matches_simplex(sipo, case, extra):
+    lp, ops, geo, tgt, cp = _tiny(case, extra)
+    st, obj, _ = simplex.solve_dense(lp, ops)
+    ctx = sipo.sipo_create(geo, tgt, cp, dict(storage=sipo.SIPO_F32, kkt_tol=1e-5, max_iter=100000))
+    res = sipo.sipo_solve(ctx)
+    assert res["status"] == sipo.SIPO_OPTIMAL
+    assert abs(res["pobj"] - obj) <= 1e-4 * abs(obj)
+
+
+def test_infeasible_case2_is_reported(sipo):
+    lp, ops, geo, tgt, cp = _tiny(2, dict(inhibit_ratio=0.3))
+    assert simplex.solve_dense(lp, ops)[0] == "infeasible"
+    for storage in (sipo.SIPO_F64, sipo.SIPO_F32):
+        ctx = sipo.sipo_create(geo, tgt, cp, dict(storage=storage, kkt_tol=1e-9, max_iter=20000))
+        res = sipo.sipo_solve(ctx)
+        assert res["status"] == sipo.SIPO_PRIMAL_INFEASIBLE, res
+
+
+@pytest.mark.parametrize("case,extra", [(1, dict(tol_lo=0.05, tol_hi=0.05)), (2, dict(inhibit_ratio=0.7))])
+def test_fp64_iterates_track_the_oracle(sipo, case, extra):
+    """Same algorithm, same instance, FP64 on both sides: after 640 iterations the
+    objectives, KKT errors and restart counts agree."""
+    tgt = discs_2d(24, n_discs=2, r_range=(3.0, 5.0), container_radius=10.0, seed=11)
+    ang = uniform_angles(32)
+    lp, ops = build_lp(Geometry(24, 24, 1, ang, 35), tgt, CaseParams(case=case, band_width=3, **extra))
+    ref = pdhg.solve(lp, ops, kkt_tol=0.0, max_iter=640)
+    ctx = sipo.sipo_create(dict(nx=24, ny=24, nz=1, angles=ang, n_det=35), tgt,
+                           dict(kase=case, band_width=3, **extra),
+                           dict(storage=sipo.SIPO_F64, kkt_tol=0.0, max_iter=640))
+    res = sipo.sipo_solve(ctx)
+    assert res["status"] == sipo.SIPO_ITER_LIMIT and res["iters"] == 640
+    assert res["restarts"] == ref["restarts"]
+    for key, rkey in (("pobj", "pobj"), ("dobj", "dobj"), ("rel_primal", "rel_primal"),
+                      ("rel_dual", "rel_dual")):
+        a, b = res[key], ref["info"][rkey]
+        assert abs(a - b) <= 1e-7 * max(abs(b), 1e-3), (key, a, b)
+
+
+def test_disc64_case1_fp64_to_1e6(sipo):
+    """The 64x64 / 96-angle / 91-bin single-slice workload, Case 1, to KKT 1e-6."""
+    wl = workload("disc64")
+    ctx = sipo.sipo_create(dict(nx=64, ny=64, nz=1, angles=wl.angles, n_det=91), wl.target,
+                           dict(kase=1, tol_lo=0.05, tol_hi=0.05, band_width=10),
+                           dict(storage=sipo.SIPO_F64, kkt_tol=1e-6, max_iter=200000))
+    res = sipo.sipo_solve(ctx)
+    assert res["status"] == sipo.SIPO_OPTIMAL, res
+    with open(os.path.join(GOLDEN, "disc64_case1.json")) as f:
+        gold = json.load(f)
+    assert abs(res["pobj"] - gold["objective"]) <= 1e-5 * gold["objective"]
+    # certificate: the oracle re-evaluates the returned point in FP64
+    lp, ops = build_lp(Geometry(64, 64, 1, wl.angles, 91), wl.target,
+                       CaseParams(case=1, tol_lo=0.05, tol_hi=0.05, band_width=10))
+    y = np.empty((96, 91, 1), np.float64)
+    lu = np.empty((64, 64, 1), np.float64)
+    ll = np.empty((64, 64, 1), np.float64)
+    sipo.sipo_get_array(ctx, 2, y)
+    sipo.sipo_get_array(ctx, 3, lu)
+    sipo.sipo_get_array(ctx, 4, ll)
+    d = ops.AT(y).ravel()
+    g = ops.A(lu - ll).ravel()
+    info = kkt(lp, d, g, res["u"], res["v"], lu, ll)
+    assert info["kkt"] <= 1.01e-6
+    assert abs(info["pobj"] - res["pobj"]) <= 1e-12 * res["pobj"] + 1e-15
+
+
+def test_csg_case2_fp32_certificate_and_bf16(sipo):
+    """A reduced 3-D CSG instance (48^3, 68 views, vial, Case 2): FP32 solve to
+    1e-4, checked by an FP64 re-evaluation of its own certificate and against the
+    oracle optimum; BF16 storage reports the KKT it reaches."""
+    n = 48
+    tgt = csg_3d(n, vial_radius=22.5, band_width=2, seed=2, feature=(3.0, 12.0))
+    ang = uniform_angles(68)
+    geo = dict(nx=n, ny=n, nz=n, angles=ang, n_det=n, vial_radius=22.5)
+    cp = dict(kase=2, inhibit_ratio=0.8, band_width=2)
+    lp, ops = build_lp(Geometry(n, n, n, ang, n, vial_radius=22.5), tgt,
+                       CaseParams(case=2, inhibit_ratio=0.8, band_width=2))
+    ref = pdhg.solve(lp, ops, kkt_tol=1e-5, max_iter=60000)
+    ctx = sipo.sipo_create(geo, tgt, cp, dict(storage=sipo.SIPO_F32, kkt_tol=1e-4, max_iter=60000))
+    res = sipo.sipo_solve(ctx)
+    if ref["status"] == pdhg.PRIMAL_INFEASIBLE:
+        assert res["status"] == sipo.SIPO_PRIMAL_INFEASIBLE
+        return
+    assert res["status"] == sipo.SIPO_OPTIMAL, res
+    y = np.empty(lp.active.shape, np.float32)
+    lu = np.empty(lp.labels.shape, np.float32)
+    ll = np.empty(lp.labels.shape, np.float32)
+    sipo.sipo_get_array(ctx, 2, y)
+    sipo.sipo_get_array(ctx, 3, lu)
+    sipo.sipo_get_array(ctx, 4, ll)
+    g = Geometry(n, n, n, ang, n, vial_radius=22.5)
+    d = ops.AT(y.reshape(g.sino_shape)).ravel()
+    gg = ops.A((lu.astype(np.float64) - ll).reshape(g.vol_shape)).ravel()
+    info = kkt(lp, d, gg, res["u"], res["v"], lu, ll)
+    assert info["kkt"] <= 2e-4, info
+    assert abs(res["pobj"] - ref["obj"]) <= 1e-3 * abs(ref["obj"])
+    ctx16 = sipo.sipo_create(geo, tgt, cp, dict(storage=sipo.SIPO_BF16, kkt_tol=1e-4, max_iter=20000))
+    r16 = sipo.sipo_solve(ctx16)
+    assert r16["status"] in (sipo.SIPO_OPTIMAL, sipo.SIPO_ITER_LIMIT)
+    assert abs(r16["pobj"] - ref["obj"]) <= 2e-2 * abs(ref["obj"])
