@@ -7,7 +7,9 @@ stored).  `SipoBackproject` is A^T y = K P_mu^T y with backward A g and
 dL/dsigma_a = < P_mu^T y, dK/dsigma_a g >.  Both call only the C ABI.
 
 The context's PSF radii are frozen at creation; `sigma` is written into the
-context on every forward call.
+context on every forward call, and the backward writes the forward's sigma
+back before it runs (the context may have been used with other sigmas in
+between).
 """
 from __future__ import annotations
 
@@ -33,12 +35,15 @@ class SipoProject(torch.autograd.Function):
         ctx.save_for_backward(p)
         ctx.handle = handle
         ctx.sigma_dtype = None if sigma is None else sigma.dtype
+        ctx.sigma_vals = _sigma_list(sigma)
         return out
 
     @staticmethod
     def backward(ctx, g):
         (p,) = ctx.saved_tensors
         h = ctx.handle
+        if ctx.sigma_vals is not None:
+            _abi.sipo_set_psf_sigma(h, ctx.sigma_vals)
         g = g.contiguous()
         grad_p = grad_s = None
         if ctx.needs_input_grad[0]:
@@ -60,12 +65,15 @@ class SipoBackproject(torch.autograd.Function):
         ctx.save_for_backward(y)
         ctx.handle = handle
         ctx.sigma_dtype = None if sigma is None else sigma.dtype
+        ctx.sigma_vals = _sigma_list(sigma)
         return out
 
     @staticmethod
     def backward(ctx, g):
         (y,) = ctx.saved_tensors
         h = ctx.handle
+        if ctx.sigma_vals is not None:
+            _abi.sipo_set_psf_sigma(h, ctx.sigma_vals)
         g = g.contiguous()
         grad_y = grad_s = None
         if ctx.needs_input_grad[0]:
