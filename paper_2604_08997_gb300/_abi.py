@@ -82,6 +82,8 @@ SIGNATURES = {
     "sipo_tile_count": (c_int, []),
     "sipo_kernel_launch_count": (c_longlong, []),
     "sipo_set_tolerances": (c_int, [c_void_p, POINTER(sipo_tolerances)]),
+    "sipo_dose_metrics_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_longlong, c_double,
+                                          c_double, POINTER(c_double), c_void_p]),
     "sipo_destroy": (c_int, [c_void_p]),
     "sipo_last_error": (c_char_p, []),
 }
@@ -319,6 +321,22 @@ def sipo_set_tolerances(ctx: Context, kkt_tol: float, max_iter: int, check_every
     tl = sipo_tolerances(float(kkt_tol), int(max_iter), int(check_every),
                          int(ctx.storage if storage is None else storage), -1)
     _check(load().sipo_set_tolerances(ctx.handle, ctypes.byref(tl)))
+
+
+def sipo_dose_metrics_noalloc(dose, labels, f_T, f_crit: float, lower_scale: float,
+                              stream=None) -> np.ndarray:
+    """Metrics of a device dose field without device allocation (see include/sipo.h):
+    returns [dtvr_f, dsr, psr_f, alpha, s]."""
+    pd, ld = _ptr(dose)
+    pl, ll = _ptr(labels)
+    pf, lf = _ptr(f_T)
+    if SIPO_HOST in (ld, ll, lf):
+        raise ValueError("dose, labels and f_T must be device tensors")
+    out = (c_double * 5)()
+    _check(load().sipo_dose_metrics_noalloc(c_void_p(pd), _dtype_code(dose), c_void_p(pl),
+                                            c_void_p(pf), int(dose.numel()), float(f_crit),
+                                            float(lower_scale), out, _stream(stream)))
+    return np.array(list(out))
 
 
 def sipo_destroy(ctx: Context):

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsipo.so")
-SOURCES = ["sipo_abi.cu", "sipo_project.cu", "sipo_backproject.cu"]
+SOURCES = ["sipo_abi.cu", "sipo_project.cu", "sipo_backproject.cu", "sipo_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -813,6 +813,9 @@ int set_error(const Error& e) {
 }
 
 }  // namespace
+
+void set_last_error(const std::string& msg) { g_err = msg; }
+
 }  // namespace sipo
 
 struct sipo_ctx {
