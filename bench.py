@@ -202,15 +202,45 @@ def cpu_baseline(wl, max_seconds=20.0):
 
 # ---------------------------------------------------------------- GPU arm
 def needed_units(sipo, ctx, wl):
-    """Voxel-angle pairs the solver's backprojector processes per launch and rays
-    its projector processes (columns with any band/gel voxel; active rays)."""
+    """Columns the solver's kernels process: (y, x) columns with a band or gel
+    voxel (backprojector) and (angle, bin) columns with an active ray (projector)."""
     lab = np.empty((wl.n, wl.n, wl.nz), np.uint8)
     act = np.empty((wl.n_angles, wl.n_det, wl.nz), np.uint8)
     sipo.sipo_get_array(ctx, 0, lab)
     sipo.sipo_get_array(ctx, 1, act)
-    need_cols = int(np.count_nonzero((lab != 0).any(axis=2)))
-    act_cols = int(np.count_nonzero(act.any(axis=2)))
-    return need_cols, act_cols
+    need = (lab != 0).any(axis=2)
+    act_col = act.any(axis=2)
+    return need, act_col
+
+
+def tap_counts(wl, need, act_col):
+    """Interpolation taps one launch of each fused kernel applies (per z value
+    times nz): the backprojector's in-range taps of the needed columns, and the
+    projector's non-zero taps into the active (angle, bin) columns."""
+    n, nd = wl.n, wl.n_det
+    c = np.arange(n) - (n - 1) / 2.0
+    Y, X = np.meshgrid(c, c, indexing="ij")
+    inside = np.ones((n, n), bool) if wl.vial_radius <= 0 else (X * X + Y * Y <= wl.vial_radius ** 2)
+    bp_mask = need & inside
+    xs_b, ys_b = X[bp_mask], Y[bp_mask]
+    xs_f, ys_f = X[inside], Y[inside]
+    off = (nd - 1) / 2.0
+    bp = fp = 0
+    for k, th in enumerate(wl.angles):
+        cth, sth = np.cos(th), np.sin(th)
+        u = xs_b * cth + ys_b * sth + off
+        i0 = np.floor(u)
+        bp += int(np.count_nonzero((i0 >= 0) & (i0 < nd)) + np.count_nonzero((i0 + 1 >= 0) & (i0 + 1 < nd)))
+        u = xs_f * cth + ys_f * sth + off
+        i0 = np.floor(u).astype(np.int64)
+        w = u - i0
+        hits = np.zeros(nd + 2, np.int64)
+        ok = (i0 >= 0) & (i0 < nd)
+        np.add.at(hits, i0[ok], 1)
+        ok1 = (i0 + 1 >= 0) & (i0 + 1 < nd) & (w > 0)
+        np.add.at(hits, i0[ok1] + 1, 1)
+        fp += int(hits[:nd][act_col[k]].sum())
+    return bp * wl.nz, fp * wl.nz
 
 
 def run_gpu(args, dist, rank, world, device):
@@ -245,19 +275,25 @@ def run_gpu(args, dist, rank, world, device):
     phases = sipo.sipo_profile(ctx, args.profile_iters)
     normal = sum(v for k, v in phases.items() if k != "check_step")
     per_iter_ms = (normal * (args.check_every - 1) + phases["check_step"]) / args.check_every
-    # roofline of the dominant kernel
-    need_cols, act_cols = needed_units(sipo, ctx, wl)
+    # roofline of the dominant kernel (work counted in taps: one FMA each)
+    need, act_col = needed_units(sipo, ctx, wl)
+    need_cols, act_cols = int(need.sum()), int(act_col.sum())
+    bp_taps, fp_taps = tap_counts(wl, need, act_col)
     bp_ms = phases["backproject"]
     fp_ms = phases["project_primal"]
-    dom, dom_ms = ("backproject+dual", bp_ms) if bp_ms >= fp_ms else ("project+primal", fp_ms)
-    pairs_bp = need_cols * wl.nz * wl.n_angles           # voxel-angle pairs
-    flop_bp = 4.0 * pairs_bp                               # 2 taps x FMA
-    # projector: every active column gathers ~2 taps per voxel it crosses
-    flop = flop_bp if dom.startswith("back") else 4.0 * pairs_bp
-    bytes_alg_bp = (wl.n_angles * wl.n_det * wl.nz * 4 + need_cols * wl.nz * (4 * 4 + 4 + 1 + 4 * 4))
+    if bp_ms >= fp_ms:
+        dom, dom_ms, taps = "k_backproject (fused dual update)", bp_ms, bp_taps
+    else:
+        dom, dom_ms, taps = "k_project (fused primal update)", fp_ms, fp_taps
+    # algorithmic HBM bytes: every input element once, every output once
+    el = 2 if args.storage == "bf16" else (8 if args.storage == "f64" else 4)
+    cw = 8 if args.storage == "f64" else 4
+    S = wl.n_angles * wl.n_det * wl.nz
+    bytes_bp = S * el + need_cols * wl.nz * (4 * el + 2 * cw + 1 + 2 * el + cw + el)
+    bytes_fp = wl.n * wl.n * wl.nz * el + act_cols * wl.nz * (cw + 2 * el + 2 * el)
     clk = clocks.summary()
     peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = flop / (dom_ms * 1e-3) / 1e12
+    achieved = 2.0 * taps / (dom_ms * 1e-3) / 1e12
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -266,12 +302,20 @@ def run_gpu(args, dist, rank, world, device):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops,
                 "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
-                "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
-                               f"{SM_MAX_MHZ:.0f} MHz",
-                "units_per_launch": pairs_bp, "flop_per_unit": 4,
+                "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x "
+                               f"{SM_MAX_MHZ:.0f} MHz (no measured FP32 peak exists)",
+                "units": "taps (one FMA = 2 FLOP per tap per z value)", "units_per_launch": taps,
                 "avg_launch_ms": dom_ms,
-                "hbm_gbs_algorithmic": bytes_alg_bp / (bp_ms * 1e-3) / 1e9,
-                "hbm_frac_of_measured": bytes_alg_bp / (bp_ms * 1e-3) / 1e9 / hbm}
+                "l1_roof_frac": (taps / (dom_ms * 1e-3)) / (SM_COUNT * 32 * SM_MAX_MHZ * 1e6),
+                "backproject": {"ms": bp_ms, "taps": bp_taps,
+                                "tflops": 2.0 * bp_taps / (bp_ms * 1e-3) / 1e12,
+                                "alg_bytes": bytes_bp, "gbs": bytes_bp / (bp_ms * 1e-3) / 1e9,
+                                "hbm_frac_of_measured": bytes_bp / (bp_ms * 1e-3) / 1e9 / hbm},
+                "project": {"ms": fp_ms, "taps": fp_taps,
+                            "tflops": 2.0 * fp_taps / (fp_ms * 1e-3) / 1e12,
+                            "alg_bytes": bytes_fp, "gbs": bytes_fp / (fp_ms * 1e-3) / 1e9,
+                            "hbm_frac_of_measured": bytes_fp / (fp_ms * 1e-3) / 1e9 / hbm},
+                "hbm_peak_gbs": hbm}
     # time to relative KKT 1e-4
     kkt_info = None
     if args.kkt_iters > 0:

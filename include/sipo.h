@@ -116,13 +116,15 @@ typedef struct sipo_case_params {
  * (SIPO_F32, SIPO_BF16 with FP32 arithmetic, or SIPO_F64); residuals, gap,
  * step sizes, restart logic and the u~/v~ scalars are FP64 in every mode.
  * tile_cfg: -1 lets the library choose tile shapes, otherwise an index into
- * its tile table (see sipo_tile_count). */
+ * its tile table (see sipo_tile_count).  primal_weight: initial primal weight
+ * omega of the preconditioned PDHG (<= 0: the library's default rule). */
 typedef struct sipo_tolerances {
   double kkt_tol;
   long long max_iter;
   int check_every;
   int storage;
   int tile_cfg;
+  double primal_weight;
 } sipo_tolerances;
 
 /* Result of sipo_solve.  kkt = max(rel_primal, rel_dual, rel_gap) of the
@@ -220,6 +222,16 @@ int sipo_tile_count(void);
 /* Total kernels this library has launched in this process (graph nodes count
  * once per graph launch). */
 long long sipo_kernel_launch_count(void);
+
+/* Convergence trace of the last solve: one entry per KKT check (at most
+ * 4096), 10 doubles each: iteration, relative KKT, relative primal
+ * residual, relative dual residual, relative gap, primal objective, primal
+ * weight, restarts so far, and the relative violations of the two Farkas
+ * candidates tested for primal infeasibility (dual difference since the last
+ * restart, dual part of T(z) - z; -1 when a candidate's dual objective is not
+ * positive).  Copies min(entries, max_entries) entries to host `out`
+ * and returns that count (>= 0), or a negative error code. */
+int sipo_get_trace(sipo_ctx *ctx, double *out, int max_entries);
 
 /* Replaces kkt_tol and max_iter for later solves (check_every, storage and
  * tile_cfg are fixed at creation; changing them is INVALID_ARG). */

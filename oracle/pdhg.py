@@ -29,10 +29,13 @@ The readings implemented here (and by the GPU solver) are published methods:
   36% of all iterations.  A restart moves z and z0 to T(z) and updates omega by
   log-smoothing (0.5) towards ||lam - lam0|| / ||x - x0|| (scaled norms).
 * Primal infeasibility (Secs. 2.7.1-2.7.2 treat an infeasible LP as a
-  diagnostic): at each check, the dual difference lam+ - lam0 since the last
-  restart is tested as a Farkas ray: its reduced costs G^T dlam must be
-  non-negative on every primal column, it must be non-negative, and its dual
-  objective must be positive; violations relative to the objective <= 1e-6.
+  diagnostic): at each check two candidate directions are tested as a Farkas
+  ray -- the dual difference lam+ - lam0 since the last restart, and the dual
+  part of the fixed-point residual T(z) - z, which tends to the infimal
+  displacement vector of PDHG (Applegate, Diaz, Lu & Lubin 2021).  A ray's
+  reduced costs G^T dlam must be non-negative on every primal column, the ray
+  non-negative, and its dual objective positive; the largest violation
+  (l_inf) relative to the objective <= 1e-6.
 """
 from __future__ import annotations
 
@@ -117,11 +120,11 @@ def _farkas(lp, pc, dq_g, dlam_up, dlam_lo):
         rv = 0.0
     if not obj > 0:
         return False
-    scale = 1.0 / obj
-    viol2 = np.sum(np.minimum(dq_g[lp.active], 0.0) ** 2)
-    viol2 += min(ru, 0.0) ** 2 + min(rv, 0.0) ** 2
-    viol2 += np.sum(np.minimum(dlam_up, 0.0) ** 2) + np.sum(np.minimum(dlam_lo, 0.0) ** 2)
-    return math.sqrt(viol2) * scale <= INFEAS_TOL
+    viol = max(np.max(np.maximum(-dq_g[lp.active], 0.0), initial=0.0),
+               -min(ru, 0.0), -min(rv, 0.0),
+               np.max(np.maximum(-dlam_up, 0.0), initial=0.0),
+               np.max(np.maximum(-dlam_lo, 0.0), initial=0.0))
+    return viol / obj <= INFEAS_TOL
 
 
 def solve(lp: LPData, ops: Operators, kkt_tol=1e-4, max_iter=10000,
@@ -187,7 +190,8 @@ def solve(lp: LPData, ops: Operators, kkt_tol=1e-4, max_iter=10000,
             if (info["rel_primal"] <= kkt_tol and info["rel_dual"] <= kkt_tol
                     and info["rel_gap"] <= kkt_tol):
                 status = OPTIMAL
-            elif k > 0 and _farkas(lp, pc, g_p - g0, lam_up_p - lam_up0, lam_lo_p - lam_lo0):
+            elif k > 0 and (_farkas(lp, pc, g_p - g0, lam_up_p - lam_up0, lam_lo_p - lam_lo0)
+                            or _farkas(lp, pc, g_p - g, lam_up_p - lam_up, lam_lo_p - lam_lo)):
                 status = PRIMAL_INFEASIBLE
             elif k == max_iter:
                 status = ITER_LIMIT

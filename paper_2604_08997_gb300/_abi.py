@@ -39,7 +39,7 @@ class sipo_case_params(Structure):
 
 class sipo_tolerances(Structure):
     _fields_ = [("kkt_tol", c_double), ("max_iter", c_longlong), ("check_every", c_int),
-                ("storage", c_int), ("tile_cfg", c_int)]
+                ("storage", c_int), ("tile_cfg", c_int), ("primal_weight", c_double)]
 
 
 class sipo_result(Structure):
@@ -82,6 +82,7 @@ SIGNATURES = {
     "sipo_tile_count": (c_int, []),
     "sipo_kernel_launch_count": (c_longlong, []),
     "sipo_set_tolerances": (c_int, [c_void_p, POINTER(sipo_tolerances)]),
+    "sipo_get_trace": (c_int, [c_void_p, POINTER(c_double), c_int]),
     "sipo_dose_metrics_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_longlong, c_double,
                                           c_double, POINTER(c_double), c_void_p]),
     "sipo_destroy": (c_int, [c_void_p]),
@@ -210,7 +211,8 @@ def sipo_create(geometry: dict, f_T, case: dict, tolerances: dict, stream=None) 
                          int(tolerances.get("max_iter", 10000)),
                          int(tolerances.get("check_every", 64)),
                          int(tolerances.get("storage", SIPO_F32)),
-                         int(tolerances.get("tile_cfg", -1)))
+                         int(tolerances.get("tile_cfg", -1)),
+                         float(tolerances.get("primal_weight", 0.0)))
     if isinstance(f_T, np.ndarray) and f_T.dtype != np.float32:
         raise TypeError("f_T must be float32")
     ptr, loc = _ptr(f_T)
@@ -319,8 +321,21 @@ def sipo_kernel_launch_count() -> int:
 def sipo_set_tolerances(ctx: Context, kkt_tol: float, max_iter: int, check_every: int = 64,
                         storage: int | None = None):
     tl = sipo_tolerances(float(kkt_tol), int(max_iter), int(check_every),
-                         int(ctx.storage if storage is None else storage), -1)
+                         int(ctx.storage if storage is None else storage), -1, 0.0)
     _check(load().sipo_set_tolerances(ctx.handle, ctypes.byref(tl)))
+
+
+TRACE_FIELDS = ("k", "kkt", "rel_primal", "rel_dual", "rel_gap", "pobj", "omega", "restarts",
+                "farkas_epoch", "farkas_residual")
+
+
+def sipo_get_trace(ctx: Context, max_entries: int = 4096) -> np.ndarray:
+    """Per-check convergence trace of the last solve, shape (n, 10) (TRACE_FIELDS)."""
+    buf = np.zeros((max_entries, len(TRACE_FIELDS)), np.float64)
+    n = load().sipo_get_trace(ctx.handle, buf.ctypes.data_as(POINTER(c_double)), int(max_entries))
+    if n < 0:
+        _check(n)
+    return buf[:n].copy()
 
 
 def sipo_dose_metrics_noalloc(dose, labels, f_T, f_crit: float, lower_scale: float,

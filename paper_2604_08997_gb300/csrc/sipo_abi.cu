@@ -68,6 +68,7 @@ struct SolverBase {
   virtual long long period() const = 0;
   virtual long long max_iter() const = 0;
   virtual void set_tolerances(const sipo_tolerances* t) = 0;
+  virtual int get_trace(double* out, int max_entries) = 0;
 };
 
 constexpr int kNumPhases = 7;
@@ -92,23 +93,28 @@ struct Solver final : SolverBase {
   int zl = 1;
   int P = 64;
   bool psf = false;
+  int bp_nv = 8;     // backprojector voxel columns per warp (tile table entry)
 
   // device memory
   std::vector<void*> allocs;
   C *cs = nullptr, *ex = nullptr, *ey = nullptr, *es = nullptr;
+  int2 *xspan = nullptr, *yspan = nullptr;
+  long long r2i = -1;
   C* taps[3] = {nullptr, nullptr, nullptr};
   C* dtaps[3] = {nullptr, nullptr, nullptr};
   float* fT = nullptr;
   uint8_t *lab = nullptr, *mask = nullptr, *act_col = nullptr, *need = nullptr;
   C *ft = nullptr, *row = nullptr, *col = nullptr;
   S *y = nullptr, *y0 = nullptr, *yp = nullptr, *ybar = nullptr;
-  C *gp = nullptr, *g0 = nullptr;
+  C *gp = nullptr, *g0 = nullptr, *gc = nullptr;
   S *lu = nullptr, *ll = nullptr, *lu0 = nullptr, *ll0 = nullptr, *lpu = nullptr, *lpl = nullptr;
   S *q = nullptr, *qp = nullptr, *kq = nullptr;
   C *d = nullptr, *d0 = nullptr, *dp = nullptr;
   C *braw = nullptr, *t1 = nullptr, *t2 = nullptr, *t3 = nullptr, *tvol = nullptr;
   Scal* st = nullptr;
   double* part = nullptr;
+  double* trace = nullptr;
+  static constexpr int kTraceCap = 4096;
   Scal* h_st = nullptr;  // pinned host mirror
 
   // host constants
@@ -173,6 +179,18 @@ struct Solver final : SolverBase {
   cudaStream_t strm() const override { return stream; }
   long long period() const override { return P; }
   long long max_iter() const override { return tol.max_iter; }
+  int get_trace(double* out, int max_entries) override {
+    ck(cudaMemcpyAsync(h_st, st, sizeof(Scal), cudaMemcpyDeviceToHost, stream), "read state");
+    ck(cudaStreamSynchronize(stream), "trace");
+    const int n = std::min(h_st->trace_n, std::max(0, max_entries));
+    if (n > 0) {
+      ck(cudaMemcpyAsync(out, trace, size_t(n) * kTraceFields * sizeof(double), cudaMemcpyDeviceToHost, stream),
+         "trace");
+      ck(cudaStreamSynchronize(stream), "trace");
+    }
+    return n;
+  }
+
   void set_tolerances(const sipo_tolerances* t) override {
     const int p = t->check_every > 0 ? t->check_every : 64;
     if (p != P || t->storage != tol.storage)
@@ -180,6 +198,7 @@ struct Solver final : SolverBase {
     if (!(t->kkt_tol >= 0) || t->max_iter < 0) fail(SIPO_ERR_INVALID_ARG, "bad tolerances");
     tol.kkt_tol = t->kkt_tol;
     tol.max_iter = t->max_iter;
+    if (t->primal_weight > 0) omega0 = t->primal_weight;
   }
 
   Geo<C> geo() const {
@@ -189,14 +208,16 @@ struct Solver final : SolverBase {
     g.cy = C((ny - 1) / 2.0);
     g.off = C((nd - 1) / 2.0);
     g.cs = cs; g.ex = ex; g.ey = ey; g.es = es;
-    g.r2q = vial_r > 0 ? 4.0 * (vial_r * vial_r) : 0.0;
     g.vial_r = vial_r;
+    g.r2i = r2i;
+    g.xspan = xspan;
+    g.yspan = yspan;
     return g;
   }
 
   Bufs<S, C> bufs() const {
     Bufs<S, C> b;
-    b.y = y; b.y0 = y0; b.yp = yp; b.ybar = ybar; b.col = col; b.gp = gp; b.g0 = g0;
+    b.y = y; b.y0 = y0; b.yp = yp; b.ybar = ybar; b.col = col; b.gp = gp; b.g0 = g0; b.gc = gc;
     b.lu = lu; b.ll = ll; b.lu0 = lu0; b.ll0 = ll0; b.lpu = lpu; b.lpl = lpl; b.q = q; b.qp = qp;
     b.d = d; b.d0 = d0; b.dp = dp; b.row = row; b.ft = ft_is_const ? nullptr : ft; b.lab = lab;
     b.ft_const = ft_const; b.up_ratio = C(up_ratio); b.has_u = has_u; b.has_v = has_v;
@@ -232,7 +253,36 @@ struct Solver final : SolverBase {
     }
   }
 
+  // Inside-vial index spans per row and per column, from the exact integer
+  // test (2ix - nx + 1)^2 + (2iy - ny + 1)^2 <= floor(4 R^2).
+  void build_spans() {
+    r2i = vial_r > 0 ? (long long)std::floor(4.0 * (vial_r * vial_r)) : -1;
+    std::vector<int2> hx(ny), hy(nx);
+    auto inside = [&](int ix, int iy) {
+      if (r2i < 0) return true;
+      const long long a = 2LL * ix - (nx - 1), b = 2LL * iy - (ny - 1);
+      return a * a + b * b <= r2i;
+    };
+    for (int iy = 0; iy < ny; ++iy) {
+      int lo = nx, hi = -1;
+      for (int ix = 0; ix < nx; ++ix)
+        if (inside(ix, iy)) { lo = std::min(lo, ix); hi = std::max(hi, ix); }
+      hx[iy] = make_int2(lo, hi);
+    }
+    for (int ix = 0; ix < nx; ++ix) {
+      int lo = ny, hi = -1;
+      for (int iy = 0; iy < ny; ++iy)
+        if (inside(ix, iy)) { lo = std::min(lo, iy); hi = std::max(hi, iy); }
+      hy[ix] = make_int2(lo, hi);
+    }
+    xspan = dalloc<int2>(ny);
+    yspan = dalloc<int2>(nx);
+    ck(cudaMemcpy(xspan, hx.data(), hx.size() * sizeof(int2), cudaMemcpyHostToDevice), "xspan");
+    ck(cudaMemcpy(yspan, hy.data(), hy.size() * sizeof(int2), cudaMemcpyHostToDevice), "yspan");
+  }
+
   void build_tables() {
+    build_spans();
     std::vector<C> h_cs(2 * size_t(na));
     for (int k = 0; k < na; ++k) {
       h_cs[2 * k] = C(std::cos(angles[k]));
@@ -409,7 +459,7 @@ struct Solver final : SolverBase {
     }
     // iterate storage
     y = dalloc<S>(SN); y0 = dalloc<S>(SN); yp = dalloc<S>(SN); ybar = dalloc<S>(SN);
-    gp = dalloc<C>(SN); g0 = dalloc<C>(SN); col = dalloc<C>(SN);
+    gp = dalloc<C>(SN); g0 = dalloc<C>(SN); gc = dalloc<C>(SN); col = dalloc<C>(SN);
     mask = dalloc<uint8_t>(SN);
     act_col = dalloc<uint8_t>(size_t(na) * nd);
     lu = dalloc<S>(V); ll = dalloc<S>(V); lu0 = dalloc<S>(V); ll0 = dalloc<S>(V);
@@ -417,6 +467,7 @@ struct Solver final : SolverBase {
     d = dalloc<C>(V); d0 = dalloc<C>(V); dp = dalloc<C>(V); row = dalloc<C>(V);
     st = dalloc<Scal>(1);
     part = dalloc<double>(size_t(kNumSlots) * kRedBlocks);
+    trace = dalloc<double>(size_t(kTraceCap) * kTraceFields);
     ensure_temps();
     if (psf) {
       kq = dalloc<S>(V);
@@ -474,7 +525,9 @@ struct Solver final : SolverBase {
                           (has_v && col_v > 0 ? c_v * c_v / col_v : 0.0);
     const double h_hat2 = sums[5] + sums[6];
     omega0 = (c_hat2 > 0 && h_hat2 > 0) ? std::sqrt(c_hat2 / h_hat2) : 1.0;
+    if (tol.primal_weight > 0) omega0 = tol.primal_weight;
     count(16);
+    choose_tiles();
   }
 
   // ------------------------------------------------------- iteration steps
@@ -484,7 +537,15 @@ struct Solver final : SolverBase {
   }
 
   void begin_solve() override {
-    zero(y, SN); zero(y0, SN); zero(yp, SN); zero(ybar, SN); zero(gp, SN); zero(g0, SN);
+    init_state();
+    build_graph();
+    launches = 0;
+    t_start = std::chrono::steady_clock::now();
+  }
+
+  // zero start of a solve (y = 0, lambda = 0, u~ = 0, v~ = 1, omega = omega0)
+  void init_state() {
+    zero(y, SN); zero(y0, SN); zero(yp, SN); zero(ybar, SN); zero(gp, SN); zero(g0, SN); zero(gc, SN);
     zero(lu, V); zero(ll, V); zero(lu0, V); zero(ll0, V); zero(lpu, V); zero(lpl, V);
     zero(q, V); zero(qp, V); zero(d, V); zero(d0, V); zero(dp, V);
     if (kq) zero(kq, V);
@@ -495,13 +556,44 @@ struct Solver final : SolverBase {
     h.max_iter = tol.max_iter;
     h.u = 0.0; h.v = 1.0; h.u0 = 0.0; h.v0 = 1.0; h.up = 0.0; h.vp = 1.0;
     h.omega = omega0;
+    h.trace = trace;
+    h.trace_cap = kTraceCap;
+    h.trace_n = 0;
     *h_st = h;
     ck(cudaMemcpyAsync(st, h_st, sizeof(Scal), cudaMemcpyHostToDevice, stream), "state");
     ck(cudaStreamSynchronize(stream), "begin solve");
     solved = false;
-    build_graph();
-    launches = 0;
-    t_start = std::chrono::steady_clock::now();
+  }
+
+  // Tile table: entry 0 = 8 voxel columns per backprojector warp, 1 = 4.
+  // tile_cfg -1 times a few un-captured iterations of each entry with CUDA
+  // events (backprojection phase) and keeps the fastest.
+  void choose_tiles() {
+    if (tol.tile_cfg == 0 || tol.tile_cfg == 1) {
+      bp_nv = tol.tile_cfg == 0 ? 8 : 4;
+      return;
+    }
+    if (tol.tile_cfg >= 0) fail(SIPO_ERR_INVALID_ARG, "tile_cfg must be -1, 0 or 1");
+    const int cand[2] = {8, 4};
+    float best = 1e30f;
+    int best_nv = 8;
+    cudaEvent_t ev[7];
+    for (auto& e : ev) ck(cudaEventCreate(&e), "event");
+    for (int nv : cand) {
+      bp_nv = nv;
+      init_state();
+      float tot = 0.0f;
+      for (int it = 0; it < 4; ++it) {
+        enqueue_normal(stream, ev);
+        ck(cudaStreamSynchronize(stream), "autotune");
+        float t = 0.0f;
+        ck(cudaEventElapsedTime(&t, ev[3], ev[6]), "elapsed");
+        if (it > 0) tot += t;  // first iteration is a warm-up
+      }
+      if (tot < best) { best = tot; best_nv = nv; }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    bp_nv = best_nv;
   }
 
   void enqueue_psf_q(const S* src, cudaStream_t s) { psf3<S, S>(src, kq, t1, t2, -1, s); }
@@ -523,14 +615,14 @@ struct Solver final : SolverBase {
     count(1);
     rec(3);
     if (psf) {
-      launch_backproject<S, S, C, kBpStore, C>(g, ybar, B, braw, need, vec, s);
+      launch_backproject<S, S, C, kBpStore, C>(g, ybar, B, braw, need, vec, s, bp_nv);
       count(1);
       rec(4);
       psf3<C, C>(braw, t3, t1, t2, -1, s);
       rec(5);
       dual_launch<false>(B, t3, nvv, s);
     } else {
-      launch_backproject<S, S, C, kBpDual, C>(g, ybar, B, (C*)nullptr, need, vec, s);
+      launch_backproject<S, S, C, kBpDual, C>(g, ybar, B, (C*)nullptr, need, vec, s, bp_nv);
       count(1);
       rec(4);
       rec(5);
@@ -557,13 +649,13 @@ struct Solver final : SolverBase {
     launch_project<S, S, C, kFpPrimalCheck, C>(g, psf ? kq : q, B, (C*)nullptr, act_col, vec, s);
     count(1);
     if (psf) {
-      launch_backproject<S, S, C, kBpStore, C>(g, ybar, B, braw, need, vec, s);
+      launch_backproject<S, S, C, kBpStore, C>(g, ybar, B, braw, need, vec, s, bp_nv);
       count(1);
       psf3<C, C>(braw, t3, t1, t2, -1, s);
       dual_launch<true>(B, t3, nvv, s);
       enqueue_psf_q(qp, s);
     } else {
-      launch_backproject<S, S, C, kBpDualCheck, C>(g, ybar, B, (C*)nullptr, need, vec, s);
+      launch_backproject<S, S, C, kBpDualCheck, C>(g, ybar, B, (C*)nullptr, need, vec, s, bp_nv);
       count(1);
     }
     launch_project<S, S, C, kFpResid, C>(g, psf ? kq : qp, B, (C*)nullptr, act_col, vec, s);
@@ -777,7 +869,7 @@ struct Solver final : SolverBase {
   }
 
   void profile(int iters, double* ms, int n) override {
-    begin_solve();
+    init_state();
     std::vector<cudaEvent_t> ev(7);
     for (auto& e : ev) ck(cudaEventCreate(&e), "event");
     std::vector<double> acc(kNumPhases, 0.0);
@@ -845,7 +937,7 @@ const char* sipo_phase_name(int i) {
   return (i >= 0 && i < sipo::kNumPhases) ? sipo::kPhaseNames[i] : "";
 }
 
-int sipo_tile_count(void) { return 1; }
+int sipo_tile_count(void) { return 2; }
 
 int sipo_create(const sipo_geometry* geo, const float* f_T, int f_T_location, const sipo_case_params* cp,
                 const sipo_tolerances* tol, void* stream, sipo_ctx** out) {
@@ -1013,6 +1105,13 @@ int sipo_profile(sipo_ctx* ctx, int iters, double* phase_ms, int n_phases) {
   if (!ctx || !phase_ms || iters < 0) sipo::fail(SIPO_ERR_INVALID_ARG, "bad argument");
   ctx->c.s->profile(iters, phase_ms, n_phases);
   return SIPO_OK;
+  SIPO_CATCH
+}
+
+int sipo_get_trace(sipo_ctx* ctx, double* out, int max_entries) {
+  SIPO_TRY
+  if (!ctx || (!out && max_entries > 0)) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
+  return ctx->c.s->get_trace(out, max_entries);
   SIPO_CATCH
 }
 

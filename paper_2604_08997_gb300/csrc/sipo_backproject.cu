@@ -7,17 +7,24 @@ namespace sipo {
 
 template <typename SI, typename S, typename C, int MODE, typename O>
 void launch_backproject(const Geo<C>& g, const SI* sino, const Bufs<S, C>& b, O* out,
-                        const uint8_t* need, bool vec, cudaStream_t stream) {
+                        const uint8_t* need, bool vec, cudaStream_t stream, int nv) {
   constexpr int ZLV = sizeof(SI) == 8 ? 4 : 8;
-  if (vec)
-    k_backproject<SI, S, C, ZLV, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, sino, b, out, need);
-  else
-    k_backproject<SI, S, C, 1, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, sino, b, out, need);
+  if (vec) {
+    if (nv == 4)
+      k_backproject<SI, S, C, ZLV, 4, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, sino, b, out, need);
+    else
+      k_backproject<SI, S, C, ZLV, 8, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, sino, b, out, need);
+  } else {
+    if (nv == 4)
+      k_backproject<SI, S, C, 1, 4, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, sino, b, out, need);
+    else
+      k_backproject<SI, S, C, 1, 8, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, sino, b, out, need);
+  }
 }
 
 #define SIPO_BP(SI, S, C, M, O) \
   template void launch_backproject<SI, S, C, M, O>(const Geo<C>&, const SI*, const Bufs<S, C>&, \
-                                                    O*, const uint8_t*, bool, cudaStream_t);
+                                                    O*, const uint8_t*, bool, cudaStream_t, int);
 #define SIPO_BP_SOLVER(S, C)       \
   SIPO_BP(S, S, C, kBpDual, C)     \
   SIPO_BP(S, S, C, kBpDualCheck, C) \

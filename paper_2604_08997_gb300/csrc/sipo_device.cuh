@@ -128,44 +128,84 @@ struct Geo {
   const C* ex;              // [na][nx] exp(mu x sin) or nullptr (no attenuation)
   const C* ey;              // [na][ny] exp(-mu y cos)
   const C* es;              // [na][nd] vial entry factor (0 off the vial) or nullptr
-  double r2q;               // 4 R^2 (R = vial radius); <= 0: no vial
   double vial_r;            // R
+  long long r2i;            // floor(4 R^2): integer vial threshold (-1: no vial)
+  const int2* xspan;        // [ny]: inside-vial ix range of row iy (lo > hi: empty)
+  const int2* yspan;        // [nx]: inside-vial iy range of column ix
 };
 
 // Voxel (ix, iy) inside the vial: x^2 + y^2 <= R^2 evaluated exactly in
 // integers, (2ix - nx + 1)^2 + (2iy - ny + 1)^2 <= 4 R^2.
 template <typename C>
 __device__ __forceinline__ bool in_vial(const Geo<C>& g, int ix, int iy) {
-  if (g.r2q <= 0.0) return true;
-  long long a = 2LL * ix - (g.nx - 1), b = 2LL * iy - (g.ny - 1);
-  return double(a * a + b * b) <= g.r2q;
+  if (g.r2i < 0) return true;
+  const long long a = 2LL * ix - (g.nx - 1), b = 2LL * iy - (g.ny - 1);
+  return a * a + b * b <= g.r2i;
 }
 
 __device__ __forceinline__ float fl_(float x) { return floorf(x); }
 __device__ __forceinline__ double fl_(double x) { return floor(x); }
 
+// floor(u) as a value and as an int.  Single precision avoids the conversion
+// unit: adding 1.5*2^23 with round-down lands u + M in [2^23, 2^24), where the
+// float spacing is 1, so the sum is exactly M + floor(u) for |u| < 2^22; the
+// difference of bit patterns is floor(u) and t - M recovers it as a float.
+// The result equals floorf(u) bit for bit.
+__device__ __forceinline__ void floor_split(float u, float& fl, int& i) {
+  const float t = __fadd_rd(u, 12582912.0f);
+  i = __float_as_int(t) - 0x4B400000;
+  fl = t - 12582912.0f;
+}
+__device__ __forceinline__ void floor_split(double u, double& fl, int& i) {
+  fl = floor(u);
+  i = int(fl);
+}
+
+
 // --------------------------------------------------------------- reductions
 // Deterministic block reduction of N doubles per thread: warp shuffles, then
 // one pass over the warps in fixed order; thread 0 writes the block partials
 // to part[slot * kRedBlocks + blockIdx.x].
-template <int N>
+// Slots whose bit is set in MAXMASK are reduced with max instead of sum.
+template <int N, unsigned MAXMASK = 0u>
 __device__ __forceinline__ void block_reduce_store(double (&v)[N], double* part, int slot0) {
   __shared__ double red[kWarps][N > 0 ? N : 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     double x = v[i];
+    const bool mx = (MAXMASK >> i) & 1u;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_down_sync(0xffffffffu, x, o);
+      x = mx ? fmax(x, y) : x + y;
+    }
     if (lane == 0) red[warp][i] = x;
   }
   __syncthreads();
   if (threadIdx.x < N) {
-    double s = 0.0;
+    const bool mx = (MAXMASK >> threadIdx.x) & 1u;
+    double s = red[0][threadIdx.x];
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) s += red[w][threadIdx.x];
+    for (int w = 1; w < kWarps; ++w) s = mx ? fmax(s, red[w][threadIdx.x]) : s + red[w][threadIdx.x];
     part[(slot0 + threadIdx.x) * kRedBlocks + blockIdx.x] = s;
   }
+}
+
+// Maximum of one slot over all kRedBlocks partials (non-negative values).
+__device__ __forceinline__ double block_max_slot(const double* part, int slot) {
+  __shared__ double tmp[kThreads];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) s = fmax(s, part[slot * kRedBlocks + i]);
+  tmp[threadIdx.x] = s;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) tmp[threadIdx.x] = fmax(tmp[threadIdx.x], tmp[threadIdx.x + st]);
+    __syncthreads();
+  }
+  double r = tmp[0];
+  __syncthreads();
+  return r;
 }
 
 // Sum of one slot over all kRedBlocks partials, by one block, fixed order.

@@ -275,7 +275,10 @@ __global__ void __launch_bounds__(kThreads) k_scalar_step(Scal* st, const double
 __global__ void __launch_bounds__(kThreads) k_scalar_check(Scal* st, const double* part) {
   if (st->done) return;
   double s[kNumSlots];
-  for (int i = kSlRp2; i < kNumSlots; ++i) s[i] = block_sum_slot(part, i);
+  for (int i = kSlRp2; i < kNumSlots; ++i) {
+    const bool mx = i == kSlFkNeg || i == kSlFrNeg || i == kSlFkG || i == kSlFrG;
+    s[i] = mx ? block_max_slot(part, i) : block_sum_slot(part, i);
+  }
   if (threadIdx.x != 0) return;
   const double up = st->up, vp = st->vp, u = st->u, v = st->v, u0 = st->u0, v0 = st->v0;
   double om = st->omega;
@@ -308,21 +311,33 @@ __global__ void __launch_bounds__(kThreads) k_scalar_check(Scal* st, const doubl
   st->rel_gap = rel_gap; st->pobj = pobj; st->dobj = dobj;
   st->kkt = fmax(rel_p, fmax(rel_d, rel_gap));
   st->sband_p = SbP; st->sgel_p = SgP;
+  // Farkas candidates (primal infeasibility, Secs. 2.7.1-2.7.2): the dual
+  // difference since the last restart, and the dual part of the fixed-point
+  // residual T(z) - z (which tends to the infimal displacement of PDHG).
+  auto farkas = [&](double L, double band, double gel, double up, double g2, double neg) {
+    double obj = L, ru = 0.0, rv = 0.0;
+    if (st->has_u) ru = -band;
+    else obj -= st->band_rhs * band;
+    if (st->has_v) { rv = -gel; obj += fmax(rv, 0.0); }
+    else obj -= up;
+    if (!(obj > 0.0)) return -1.0;
+    // l_inf violation of the ray's conditions relative to its dual objective
+    const double viol = fmax(fmax(g2, neg), fmax(-fmin(ru, 0.0), -fmin(rv, 0.0)));
+    return viol / obj;
+  };
+  const double fe = farkas(s[kSlFkL], s[kSlFkBand], s[kSlFkGel], s[kSlFkUp], s[kSlFkG], s[kSlFkNeg]);
+  const double fr = farkas(s[kSlFrL], s[kSlFrBand], s[kSlFrGel], s[kSlFrUp], s[kSlFrG], s[kSlFrNeg]);
+  if (st->trace && st->trace_n < st->trace_cap) {
+    double* e = st->trace + (size_t)st->trace_n * kTraceFields;
+    e[0] = double(st->k); e[1] = st->kkt; e[2] = rel_p; e[3] = rel_d; e[4] = rel_gap;
+    e[5] = pobj; e[6] = om; e[7] = double(st->restarts); e[8] = fe; e[9] = fr;
+    st->trace_n += 1;
+  }
   int status = -1;
   if (rel_p <= st->kkt_tol && rel_d <= st->kkt_tol && rel_gap <= st->kkt_tol) {
     status = 0;
-  } else if (st->k > 0) {
-    // Farkas ray from the dual difference since the last restart
-    double obj = s[kSlFkL], ru = 0.0, rv = 0.0;
-    if (st->has_u) ru = -s[kSlFkBand];
-    else obj -= st->band_rhs * s[kSlFkBand];
-    if (st->has_v) { rv = -s[kSlFkGel]; obj += fmax(rv, 0.0); }
-    else obj -= s[kSlFkUp];
-    if (obj > 0.0) {
-      const double viol2 = s[kSlFkG] + fmin(ru, 0.0) * fmin(ru, 0.0) +
-                           fmin(rv, 0.0) * fmin(rv, 0.0) + s[kSlFkNeg];
-      if (sqrt(viol2) / obj <= kInfeasTol) status = 1;
-    }
+  } else if (st->k > 0 && ((fe >= 0.0 && fe <= kInfeasTol) || (fr >= 0.0 && fr <= kInfeasTol))) {
+    status = 1;
   }
   if (status < 0 && st->k >= st->max_iter) status = 3;
   if (status >= 0) {
@@ -463,7 +478,7 @@ __global__ void __launch_bounds__(kThreads) k_dual(Bufs<S, C> b, const C* __rest
                                                    long long nvec) {
   if (b.st->done) return;
   const StepScalars<C> sc = read_scalars<C>(b.st);
-  constexpr int NR = CHECK ? 13 : 2;
+  constexpr int NR = CHECK ? kCheckSlots : 2;
   double red[NR] = {};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nvec;
        i += (long long)gridDim.x * blockDim.x) {
@@ -472,7 +487,7 @@ __global__ void __launch_bounds__(kThreads) k_dual(Bufs<S, C> b, const C* __rest
     load_z<C, C, ZL>(dbar + base, db);
     dual_update<S, C, ZL, CHECK>(b, sc, base, db, red);
   }
-  block_reduce_store<NR>(red, b.part, CHECK ? kSlRp2 : kSlSBand);
+  block_reduce_store<NR, CHECK ? kCheckMaxMask : 0u>(red, b.part, CHECK ? kSlRp2 : kSlSBand);
 }
 
 // --------------------------------------------------------- post-solve

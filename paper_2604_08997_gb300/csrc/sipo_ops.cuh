@@ -23,9 +23,26 @@ namespace sipo {
 enum FpMode : int { kFpStore = 0, kFpPrimal = 1, kFpPrimalCheck = 2, kFpResid = 3 };
 enum BpMode : int { kBpStore = 0, kBpDual = 1, kBpDualCheck = 2 };
 
-constexpr int kBpTile = 8;  // backprojector voxel tile: 8 x 8 columns, one row per warp
 
 // --------------------------------------------------------------- projector
+// Smallest integer >= x without the conversion unit (via floor_split of -x).
+__device__ __forceinline__ int ceil_int(float x) {
+  float f;
+  int i;
+  floor_split(-x, f, i);
+  return -i;
+}
+__device__ __forceinline__ int ceil_int(double x) { return int(ceil(x)); }
+
+// Candidate window: the voxels whose detector coordinate on the walked row is
+// within 1 of bin j lie strictly inside (xc - h, xc + h), h = 1/|cos| <= sqrt 2
+// (exact arithmetic).  With the FP32 rounding of u and of xc (< 1e-4) the
+// widened window (xc - h - 1e-3, xc + h + 1e-3) is narrower than 3, so the
+// three integers from ceil(xc - h - 1e-3) contain every voxel with a non-zero
+// weight; each candidate's weight is then computed exactly as the
+// backprojector computes it (same u, same floor), so P stays the transpose.
+constexpr float kCandEps = 1e-3f;
+
 // SI: element type read from `vol`; O: element type written by kFpStore.
 template <typename SI, typename S, typename C, int ZL, int MODE, typename O>
 __global__ void __launch_bounds__(kThreads)
@@ -33,7 +50,7 @@ k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __r
           const uint8_t* __restrict__ act_col) {
   if (MODE != kFpStore && b.st->done) return;
   constexpr int ZC = 32 * ZL;
-  constexpr int NR = MODE == kFpPrimalCheck ? 2 : (MODE == kFpResid ? 3 : 0);
+  constexpr int NR = MODE == kFpPrimalCheck ? 2 : (MODE == kFpResid ? 4 : 0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nzc = (g.nz + ZC - 1) / ZC;
   const int njb = (g.nd + kWarps - 1) / kWarps;
@@ -55,86 +72,100 @@ k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __r
     C acc[ZL];
 #pragma unroll
     for (int i = 0; i < ZL; ++i) acc[i] = C(0);
-    if (esj != C(0)) {
+    if (esj != C(0) && z0 < g.nz) {
       const C c = g.cs[2 * k], s = g.cs[2 * k + 1];
-      const C sj = C(j) - g.off;
+      const C jf = C(j), jm = C(j - 1);
+      const C sj = jf - g.off;
       C H = C(0);
-      if (g.r2q > 0.0) {
+      if (g.r2i >= 0) {
         C a = fabs(sj) - C(1.5);
         a = a > C(0) ? a : C(0);
         const C R = C(g.vial_r);
         H = R * R - a * a;
         H = (H > C(0) ? sqrt(H) : C(0)) + C(1.5);
       }
+      const SI* vz = vol + z0;
       if (fabs(c) >= fabs(s)) {
-        // walk rows; on row iy the bin is reached from x near (j - inner)/c
+        // walk rows iy; on each row the bin is reached from x near (j - inner) / cos
         int lo = 0, hi = g.ny - 1;
-        if (g.r2q > 0.0) {
+        if (g.r2i >= 0) {
           const C yc = sj * s, hy = fabs(c) * H + C(1);
-          lo = max(0, int(fl_(yc - hy + g.cy)));
-          hi = min(g.ny - 1, int(ceil(yc + hy + g.cy)));
+          lo = max(0, -ceil_int(-(yc - hy + g.cy)));
+          hi = min(g.ny - 1, ceil_int(yc + hy + g.cy));
         }
-        const C inv_c = C(1) / c, h = C(1) / fabs(c);
-        for (int iy = lo; iy <= hi; ++iy) {
-          const C yf = C(iy) - g.cy;
+        const C inv_c = C(1) / c, h = C(1) / fabs(c) + C(kCandEps);
+        C yf = C(lo) - g.cy;
+        for (int iy = lo; iy <= hi; ++iy, yf += C(1)) {
+          const int2 sp = g.xspan[iy];
+          if (sp.x > sp.y) continue;
           const C inner = geo_inner(yf, s, g.off);
-          const C eyv = g.ex ? g.ey[(size_t)k * g.ny + iy] : C(1);
-          const C ixc = (C(j) - inner) * inv_c + g.cx;
-          const int ixa = int(fl_(ixc - h)) - 1;
+          const C ixc = (jf - inner) * inv_c + g.cx;
+          const int ix0 = ceil_int(ixc - h);
+          const C xf0 = C(ix0) - g.cx;
+          C wt[3];
 #pragma unroll
-          for (int m = 0; m < 5; ++m) {
-            const int ix = ixa + m;
-            if (ix < 0 || ix >= g.nx) continue;
-            const C xf = C(ix) - g.cx;
-            const C u = geo_outer(xf, c, inner);
-            const C flo = fl_(u);
-            const int i0 = int(flo);
+          for (int m = 0; m < 3; ++m) {
+            const C u = geo_outer(xf0 + C(m), c, inner);
+            C flo;
+            int i0;
+            floor_split(u, flo, i0);
             const C wv = u - flo;
-            C wt = (i0 == j) ? (C(1) - wv) : ((i0 + 1 == j) ? wv : C(0));
-            if (wt == C(0)) continue;
-            if (!in_vial(g, ix, iy)) continue;
-            if (g.ex) wt = wt * (g.ex[(size_t)k * g.nx + ix] * eyv);
-            if (z0 < g.nz) {
-              C v[ZL];
-              load_z<SI, C, ZL>(vol + ((size_t)iy * g.nx + ix) * g.nz + z0, v);
+            const int ix = ix0 + m;
+            const bool ok = ix >= sp.x && ix <= sp.y;
+            wt[m] = ok ? ((flo == jf) ? (C(1) - wv) : ((flo == jm) ? wv : C(0))) : C(0);
+          }
+          const C eyv = g.ex ? g.ey[(size_t)k * g.ny + iy] : C(1);
+          const SI* vrow = vz + ((size_t)iy * g.nx) * g.nz;
 #pragma unroll
-              for (int i = 0; i < ZL; ++i) acc[i] = fma(wt, v[i], acc[i]);
-            }
+          for (int m = 0; m < 3; ++m) {
+            if (wt[m] == C(0)) continue;
+            const int ix = ix0 + m;
+            const C w = g.ex ? wt[m] * (g.ex[(size_t)k * g.nx + ix] * eyv) : wt[m];
+            C v[ZL];
+            load_z<SI, C, ZL>(vrow + (size_t)ix * g.nz, v);
+#pragma unroll
+            for (int i = 0; i < ZL; ++i) acc[i] = fma(w, v[i], acc[i]);
           }
         }
       } else {
-        // walk columns; on column ix the bin is reached from y near (j - off - x c)/s
+        // walk columns ix; on each column the bin is reached from y near (j - off - x cos) / sin
         int lo = 0, hi = g.nx - 1;
-        if (g.r2q > 0.0) {
+        if (g.r2i >= 0) {
           const C xc = sj * c, hx = fabs(s) * H + C(1);
-          lo = max(0, int(fl_(xc - hx + g.cx)));
-          hi = min(g.nx - 1, int(ceil(xc + hx + g.cx)));
+          lo = max(0, -ceil_int(-(xc - hx + g.cx)));
+          hi = min(g.nx - 1, ceil_int(xc + hx + g.cx));
         }
-        const C inv_s = C(1) / s, h = C(1) / fabs(s);
-        for (int ix = lo; ix <= hi; ++ix) {
-          const C xf = C(ix) - g.cx;
-          const C exv = g.ex ? g.ex[(size_t)k * g.nx + ix] : C(1);
-          const C iyc = (C(j) - g.off - xf * c) * inv_s + g.cy;
-          const int iya = int(fl_(iyc - h)) - 1;
+        const C inv_s = C(1) / s, h = C(1) / fabs(s) + C(kCandEps);
+        C xf = C(lo) - g.cx;
+        for (int ix = lo; ix <= hi; ++ix, xf += C(1)) {
+          const int2 sp = g.yspan[ix];
+          if (sp.x > sp.y) continue;
+          const C iyc = (jf - g.off - xf * c) * inv_s + g.cy;
+          const int iy0 = ceil_int(iyc - h);
+          const C yf0 = C(iy0) - g.cy;
+          C wt[3];
 #pragma unroll
-          for (int m = 0; m < 5; ++m) {
-            const int iy = iya + m;
-            if (iy < 0 || iy >= g.ny) continue;
-            const C yf = C(iy) - g.cy;
-            const C u = geo_outer(xf, c, geo_inner(yf, s, g.off));
-            const C flo = fl_(u);
-            const int i0 = int(flo);
+          for (int m = 0; m < 3; ++m) {
+            const C u = geo_outer(xf, c, geo_inner(yf0 + C(m), s, g.off));
+            C flo;
+            int i0;
+            floor_split(u, flo, i0);
             const C wv = u - flo;
-            C wt = (i0 == j) ? (C(1) - wv) : ((i0 + 1 == j) ? wv : C(0));
-            if (wt == C(0)) continue;
-            if (!in_vial(g, ix, iy)) continue;
-            if (g.ex) wt = wt * (exv * g.ey[(size_t)k * g.ny + iy]);
-            if (z0 < g.nz) {
-              C v[ZL];
-              load_z<SI, C, ZL>(vol + ((size_t)iy * g.nx + ix) * g.nz + z0, v);
+            const int iy = iy0 + m;
+            const bool ok = iy >= sp.x && iy <= sp.y;
+            wt[m] = ok ? ((flo == jf) ? (C(1) - wv) : ((flo == jm) ? wv : C(0))) : C(0);
+          }
+          const C exv = g.ex ? g.ex[(size_t)k * g.nx + ix] : C(1);
+          const SI* vcol = vz + (size_t)ix * g.nz;
 #pragma unroll
-              for (int i = 0; i < ZL; ++i) acc[i] = fma(wt, v[i], acc[i]);
-            }
+          for (int m = 0; m < 3; ++m) {
+            if (wt[m] == C(0)) continue;
+            const int iy = iy0 + m;
+            const C w = g.ex ? wt[m] * (exv * g.ey[(size_t)k * g.ny + iy]) : wt[m];
+            C v[ZL];
+            load_z<SI, C, ZL>(vcol + (size_t)iy * g.nx * g.nz, v);
+#pragma unroll
+            for (int i = 0; i < ZL; ++i) acc[i] = fma(w, v[i], acc[i]);
           }
         }
       }
@@ -154,20 +185,76 @@ k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __r
     }
   }
   if constexpr (MODE == kFpPrimalCheck) block_reduce_store<2>(red, b.part, kSlFpX);
-  if constexpr (MODE == kFpResid) block_reduce_store<3>(red, b.part, kSlRd2);
+  if constexpr (MODE == kFpResid) block_reduce_store<4, kResidMaxMask>(red, b.part, kSlRd2);
 }
 
 // ----------------------------------------------------------- backprojector
-// need: per (iy, ix) column flag (nullptr: every column); columns without it
-// are skipped (and left unwritten in kBpStore mode unless need is nullptr).
-template <typename SI, typename S, typename C, int ZL, int MODE, typename O>
-__global__ void __launch_bounds__(kThreads)
+// One angle for the NV voxels of a warp's row segment.  Voxels are visited in
+// increasing detector coordinate (left to right when cos >= 0, right to left
+// otherwise); u then never decreases and floor(u) advances by 0 or 1 from one
+// voxel to the next (|cos| <= 1), so a two-row window (rows cur and cur + 1,
+// ZL values per lane each) slides along the detector and each sinogram row is
+// loaded once per angle instead of once per voxel.  Rows off the detector are
+// zero.  The taps are the same weights as before; only loads are shared.
+template <typename SI, typename C, int ZL>
+__device__ __forceinline__ void bp_load_row(const Geo<C>& g, const SI* srow, int r, C (&t)[ZL]) {
+  if (unsigned(r) < unsigned(g.nd)) {
+    load_z<SI, C, ZL>(srow + (size_t)r * g.nz, t);
+  } else {
+#pragma unroll
+    for (int i = 0; i < ZL; ++i) t[i] = C(0);
+  }
+}
+
+template <typename SI, typename C, int ZL, int NV, bool FWD>
+__device__ __forceinline__ void bp_angle(const Geo<C>& g, const SI* srow, const C* exk, const C* esk,
+                                         C eyv, C xf0, C c, C inner, unsigned mask, C (&acc)[NV][ZL]) {
+  int cur = -2147483647;
+  C tA[ZL], tB[ZL];
+#pragma unroll
+  for (int i = 0; i < ZL; ++i) { tA[i] = C(0); tB[i] = C(0); }
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    const int v = FWD ? q : NV - 1 - q;
+    if (!((mask >> v) & 1u)) continue;
+    const C u = geo_outer(xf0 + C(v), c, inner);
+    C flo;
+    int i0;
+    floor_split(u, flo, i0);
+    const C wv = u - flo;
+    const C e = exk ? exk[v] * eyv : C(1);
+    C w0 = (C(1) - wv) * e, w1 = wv * e;
+    if (esk) {
+      w0 = unsigned(i0) < unsigned(g.nd) ? w0 * esk[i0] : C(0);
+      w1 = unsigned(i0 + 1) < unsigned(g.nd) ? w1 * esk[i0 + 1] : C(0);
+    }
+    if (i0 != cur) {
+      if (i0 == cur + 1) {
+#pragma unroll
+        for (int i = 0; i < ZL; ++i) tA[i] = tB[i];
+      } else {
+        bp_load_row<SI, C, ZL>(g, srow, i0, tA);
+      }
+      bp_load_row<SI, C, ZL>(g, srow, i0 + 1, tB);
+      cur = i0;
+    }
+#pragma unroll
+    for (int i = 0; i < ZL; ++i) acc[v][i] = fma(w1, tB[i], fma(w0, tA[i], acc[v][i]));
+  }
+}
+
+
+// Tile: NV voxel columns along x per warp, one row per warp (8 rows per
+// block), ZL z values per lane.  need: per (iy, ix) column flag (nullptr:
+// every column); columns without it are skipped (and left unwritten in
+// kBpStore mode unless need is nullptr).
+template <typename SI, typename S, typename C, int ZL, int NV, int MODE, typename O>
+__global__ void __launch_bounds__(kThreads, 2)
 k_backproject(const Geo<C> g, const SI* __restrict__ sino, const Bufs<S, C> b, O* __restrict__ out,
               const uint8_t* __restrict__ need) {
   if (MODE != kBpStore && b.st->done) return;
   constexpr int ZC = 32 * ZL;
-  constexpr int NV = kBpTile;
-  constexpr int NR = MODE == kBpDualCheck ? 13 : (MODE == kBpDual ? 2 : 0);
+  constexpr int NR = MODE == kBpDualCheck ? kCheckSlots : (MODE == kBpDual ? 2 : 0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ntx = (g.nx + NV - 1) / NV, nty = (g.ny + kWarps - 1) / kWarps;
   const int nzc = (g.nz + ZC - 1) / ZC;
@@ -184,11 +271,12 @@ k_backproject(const Geo<C> g, const SI* __restrict__ sino, const Bufs<S, C> b, O
     const int iy = ty * kWarps + warp;
     const int z0 = tz * ZC + lane * ZL;
     if (iy >= g.ny) continue;
+    const int2 sp = g.xspan[iy];
     unsigned mask = 0;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const int ix = tx * NV + v;
-      if (ix < g.nx && in_vial(g, ix, iy) && (need == nullptr || need[(size_t)iy * g.nx + ix]))
+      if (ix < g.nx && ix >= sp.x && ix <= sp.y && (need == nullptr || need[(size_t)iy * g.nx + ix]))
         mask |= 1u << v;
     }
     C acc[NV][ZL];
@@ -198,41 +286,19 @@ k_backproject(const Geo<C> g, const SI* __restrict__ sino, const Bufs<S, C> b, O
       for (int i = 0; i < ZL; ++i) acc[v][i] = C(0);
     if (mask != 0u && z0 < g.nz) {
       const C yf = C(iy) - g.cy;
+      const C xf0 = C(tx * NV) - g.cx;
+      const SI* sz = sino + z0;
       for (int k = 0; k < g.na; ++k) {
         const C c = g.cs[2 * k], s = g.cs[2 * k + 1];
         const C inner = geo_inner(yf, s, g.off);
         const C eyv = g.ex ? g.ey[(size_t)k * g.ny + iy] : C(1);
-        const SI* srow = sino + (size_t)k * g.nd * g.nz + z0;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          if (!((mask >> v) & 1u)) continue;
-          const int ix = tx * NV + v;
-          const C xf = C(ix) - g.cx;
-          const C u = geo_outer(xf, c, inner);
-          const C flo = fl_(u);
-          const int i0 = int(flo);
-          const C wv = u - flo;
-          const C e = g.ex ? g.ex[(size_t)k * g.nx + ix] * eyv : C(1);
-          C w0 = (C(1) - wv) * e, w1 = wv * e;
-          const bool ok0 = unsigned(i0) < unsigned(g.nd);
-          const bool ok1 = unsigned(i0 + 1) < unsigned(g.nd);
-          if (g.es) {
-            w0 = ok0 ? w0 * g.es[(size_t)k * g.nd + i0] : C(0);
-            w1 = ok1 ? w1 * g.es[(size_t)k * g.nd + i0 + 1] : C(0);
-          }
-          if (ok0) {
-            C tv[ZL];
-            load_z<SI, C, ZL>(srow + (size_t)i0 * g.nz, tv);
-#pragma unroll
-            for (int i = 0; i < ZL; ++i) acc[v][i] = fma(w0, tv[i], acc[v][i]);
-          }
-          if (ok1) {
-            C tv[ZL];
-            load_z<SI, C, ZL>(srow + (size_t)(i0 + 1) * g.nz, tv);
-#pragma unroll
-            for (int i = 0; i < ZL; ++i) acc[v][i] = fma(w1, tv[i], acc[v][i]);
-          }
-        }
+        const SI* srow = sz + (size_t)k * g.nd * g.nz;
+        const C* exk = g.ex ? g.ex + (size_t)k * g.nx + tx * NV : nullptr;
+        const C* esk = g.es ? g.es + (size_t)k * g.nd : nullptr;
+        if (c >= C(0))
+          bp_angle<SI, C, ZL, NV, true>(g, srow, exk, esk, eyv, xf0, c, inner, mask, acc);
+        else
+          bp_angle<SI, C, ZL, NV, false>(g, srow, exk, esk, eyv, xf0, c, inner, mask, acc);
       }
     }
     if (z0 >= g.nz) continue;
@@ -249,7 +315,7 @@ k_backproject(const Geo<C> g, const SI* __restrict__ sino, const Bufs<S, C> b, O
     }
   }
   if constexpr (MODE == kBpDual) block_reduce_store<2>(red, b.part, kSlSBand);
-  if constexpr (MODE == kBpDualCheck) block_reduce_store<13>(red, b.part, kSlRp2);
+  if constexpr (MODE == kBpDualCheck) block_reduce_store<kCheckSlots, kCheckMaxMask>(red, b.part, kSlRp2);
 }
 
 // ------------------------------------------------------- separable PSF pass

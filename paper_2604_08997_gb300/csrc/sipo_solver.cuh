@@ -38,14 +38,20 @@ enum Slot : int {
   kSlFkBand,      // Farkas: sum_band dlam_up
   kSlFkGel,       // Farkas: sum_gel f~ dlam_up
   kSlFkUp,        // Farkas: sum_gel f~_U dlam_up
-  kSlFkNeg,       // Farkas: ||min(dlam, 0)||^2
+  kSlFkNeg,       // Farkas: max(-dlam, 0) (max-reduced)
+  kSlFrL,         // same five for the fixed-point residual direction dlam = lam+ - lam
+  kSlFrBand,
+  kSlFrGel,
+  kSlFrUp,
+  kSlFrNeg,
   // projector, check step
   kSlFpX,         // ||y - y+||^2_col
   kSlOmX,         // ||y+ - y0||^2_col
   // projector on q+ (dual residual of T(z))
   kSlRd2,         // ||min(g+, 0)||^2 on active rays
   kSlRd2s,        // preconditioned
-  kSlFkG,         // Farkas: ||min(g+ - g0, 0)||^2 on active rays
+  kSlFkG,         // Farkas: max(-(g+ - g0), 0) on active rays (max-reduced)
+  kSlFrG,         // Farkas: max(-(g+ - g), 0) on active rays (residual direction, max-reduced)
   kNumSlots
 };
 
@@ -63,7 +69,20 @@ struct Scal {
   int r0_set, done, status, restart, restarts, pad;
   // KKT data of the last check
   double kkt, rel_p, rel_d, rel_gap, rp, rd, pobj, dobj, gap, sband_p, sgel_p;
+  // per-check trace: kTraceFields doubles per entry, up to trace_cap entries
+  double* trace;
+  int trace_cap, trace_n;
 };
+
+// k, kkt, rel_primal, rel_dual, rel_gap, pobj, omega, restarts, and the
+// relative violations of the two Farkas candidates (epoch difference, residual
+// direction; -1 when the candidate's dual objective is not positive)
+constexpr int kTraceFields = 10;
+constexpr int kCheckSlots = kSlFpX - kSlRp2;  // backprojector check-step slots
+// max-reduced slots among them (Farkas negativity, l_inf) and among the
+// projector residual slots (kSlRd2 .. kSlFrG)
+constexpr unsigned kCheckMaxMask = (1u << (kSlFkNeg - kSlRp2)) | (1u << (kSlFrNeg - kSlRp2));
+constexpr unsigned kResidMaxMask = (1u << (kSlFkG - kSlRd2)) | (1u << (kSlFrG - kSlRd2));
 
 // Device arrays of one solve.  S: storage type of iterates, C: compute type.
 template <typename S, typename C>
@@ -72,6 +91,7 @@ struct Bufs {
   S *y, *y0, *yp, *ybar;
   const C* col;         // Pock-Chambolle column abs-sum of each ray (0: masked)
   C *gp, *g0;           // A q+ at the last check / at the last restart
+  C* gc;                // A q of the current iterate at the last check
   // volume-sized
   S *lu, *ll, *lu0, *ll0, *lpu, *lpl, *q, *qp;
   C *d, *d0, *dp;       // A^T y (current, anchor, T point) on band and gel
@@ -113,7 +133,7 @@ __device__ __forceinline__ C rnd(C x) {  // value after a round trip through S
 // One z-vector of voxels.  CHECK = false: Halpern step fused (writes the next
 // iterate and the dual sums of Eqs. 48-49).  CHECK = true: writes T(z) and
 // accumulates its residuals, objective pieces and restart distances.
-// Reduction accumulators: red[0..1] normal, red[0..12] check (slots 2..14).
+// Reduction accumulators: red[0..1] normal, red[0..kCheckSlots) check.
 template <typename S, typename C, int ZL, bool CHECK>
 __device__ __forceinline__ void dual_update(const Bufs<S, C>& b, const StepScalars<C>& sc,
                                             size_t base, const C (&dbar)[ZL],
@@ -206,7 +226,7 @@ __device__ __forceinline__ void dual_update(const Bufs<S, C>& b, const StepScala
       const double dlu = double(lup) - double(lu0[i]);
       red[6] += double(rup) * (double(lu[i]) - double(lup)) * (double(lu[i]) - double(lup));
       red[7] += double(rup) * dlu * dlu;
-      red[12] += dlu < 0.0 ? dlu * dlu : 0.0;
+      red[12] = fmax(red[12], -dlu);
       if (band) {
         red[4] += double(lup);
         red[9] += dlu;
@@ -223,8 +243,16 @@ __device__ __forceinline__ void dual_update(const Bufs<S, C>& b, const StepScala
         red[8] += double(f) * dll;
         red[10] += double(f) * dlu;
         red[11] += double(f) * double(b.up_ratio) * dlu;
-        red[12] += dll < 0.0 ? dll * dll : 0.0;
+        red[12] = fmax(red[12], -dll);
+        const double rl = double(llp) - double(ll[i]);
+        red[13] += double(f) * rl;
+        red[15] += double(f) * (double(lup) - double(lu[i]));
+        red[16] += double(f) * double(b.up_ratio) * (double(lup) - double(lu[i]));
+        red[17] = fmax(red[17], -rl);
       }
+      const double ru = double(lup) - double(lu[i]);
+      if (band) red[14] += ru;
+      red[17] = fmax(red[17], -ru);
     }
   }
   if constexpr (!CHECK) {
@@ -266,30 +294,36 @@ __device__ __forceinline__ void primal_update(const Bufs<S, C>& b, const StepSca
     } else {
       yo[i] = yp;
       const double dx = double(y[i]) - double(yp), dz = double(yp) - double(y0[i]);
+      (void)dz;
       red[0] += double(col[i]) * dx * dx;
       red[1] += double(col[i]) * dz * dz;
     }
   }
   store_z<S, C, ZL>(b.ybar + base, yb);
-  if constexpr (!CHECK) store_z<S, C, ZL>(b.y + base, yo);
-  else store_z<S, C, ZL>(b.yp + base, yo);
+  if constexpr (!CHECK) {
+    store_z<S, C, ZL>(b.y + base, yo);
+  } else {
+    store_z<S, C, ZL>(b.yp + base, yo);
+    store_z<C, C, ZL>(b.gc + base, g);
+  }
 }
 
-// Dual residual of T(z) on active rays from g+ = A q+ (red[0..2]).
+// Dual residual of T(z) on active rays from g+ = A q+ (red[0..3]).
 template <typename S, typename C, int ZL>
 __device__ __forceinline__ void resid_update(const Bufs<S, C>& b, size_t base, const C (&g)[ZL],
                                              double* red) {
-  C col[ZL], g0[ZL];
+  C col[ZL], g0[ZL], gc[ZL];
   load_z<C, C, ZL>(b.col + base, col);
   load_z<C, C, ZL>(b.g0 + base, g0);
+  load_z<C, C, ZL>(b.gc + base, gc);
 #pragma unroll
   for (int i = 0; i < ZL; ++i) {
     if (col[i] > C(0)) {
       const double m = g[i] < C(0) ? double(g[i]) : 0.0;
       red[0] += m * m;
       red[1] += m * m / double(col[i]);
-      const double f = double(g[i]) - double(g0[i]);
-      red[2] += f < 0.0 ? f * f : 0.0;
+      red[2] = fmax(red[2], double(g0[i]) - double(g[i]));
+      red[3] = fmax(red[3], double(gc[i]) - double(g[i]));
     }
   }
   store_z<C, C, ZL>(b.gp + base, g);

@@ -48,7 +48,7 @@ def test_invalid_arguments_fail_before_device_work(lib):
     g.nx, g.ny, g.nz, g.n_angles, g.n_det = 0, 8, 1, 4, 9
     g.angles = ang.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     cp = _abi.sipo_case_params(0, 1.0, 1.0, 0.05, 0.05, 0.8, 2)
-    tl = _abi.sipo_tolerances(1e-4, 100, 64, 0, -1)
+    tl = _abi.sipo_tolerances(1e-4, 100, 64, 0, -1, 0.0)
     tgt = np.ones(64, np.float32)
     out = ctypes.c_void_p()
     rc = lib.sipo_create(ctypes.byref(g), ctypes.c_void_p(tgt.ctypes.data), 0, ctypes.byref(cp),
