@@ -316,18 +316,32 @@ def run_gpu(args, dist, rank, world, device):
                             "alg_bytes": bytes_fp, "gbs": bytes_fp / (fp_ms * 1e-3) / 1e9,
                             "hbm_frac_of_measured": bytes_fp / (fp_ms * 1e-3) / 1e9 / hbm},
                 "hbm_peak_gbs": hbm}
-    # time to relative KKT 1e-4
+    # time to relative KKT 1e-4: the requested instance, and the strictest
+    # inhibition ratio of the sweep grid above it that converges (the requested
+    # Case-2 instance may be infeasible, in which case its status is reported)
     kkt_info = None
     if args.kkt_iters > 0:
-        sipo.sipo_set_tolerances(ctx, 1e-4, args.kkt_iters, args.check_every)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rk = sipo.sipo_solve(ctx)
-        torch.cuda.synchronize()
-        tk = time.perf_counter() - t0
-        kkt_info = {"seconds": tk, "iters": rk["iters"], "status": rk["status_name"],
-                    "kkt": rk["kkt"], "objective": rk["pobj"], "restarts": rk["restarts"],
-                    "dtvr_f": rk["dtvr_f"], "psr_f": rk["psr_f"]}
+        kkt_info = {}
+        runs = [("requested", cp)]
+        if wl.case == 2 and args.feasible_ratio > 0:
+            runs.append(("feasible_ratio_%.2f" % args.feasible_ratio,
+                         dict(cp, inhibit_ratio=args.feasible_ratio)))
+        for label, cpk in runs:
+            ctx_k = ctx if cpk is cp else sipo.sipo_create(geo, tgt, cpk, tol)
+            sipo.sipo_set_tolerances(ctx_k, 1e-4, args.kkt_iters, args.check_every)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rk = sipo.sipo_solve(ctx_k)
+            torch.cuda.synchronize()
+            tk = time.perf_counter() - t0
+            kkt_info[label] = {"inhibit_ratio": cpk.get("inhibit_ratio"), "seconds": tk,
+                               "iters": rk["iters"], "status": rk["status_name"], "kkt": rk["kkt"],
+                               "rel_primal": rk["rel_primal"], "rel_dual": rk["rel_dual"],
+                               "rel_gap": rk["rel_gap"], "objective": rk["pobj"],
+                               "restarts": rk["restarts"], "dtvr_f": rk["dtvr_f"], "psr_f": rk["psr_f"],
+                               "alpha": rk["alpha"]}
+            if ctx_k is not ctx:
+                sipo.sipo_destroy(ctx_k)
     # end to end through the C ABI from pinned host memory
     tgt_h = torch.from_numpy(wl.target).pin_memory()
     y_h = torch.empty((wl.n_angles, wl.n_det, wl.nz), dtype=torch.float32).pin_memory()
@@ -351,6 +365,7 @@ def run_gpu(args, dist, rank, world, device):
            "roofline": roofline, "clocks": clk, "time_to_kkt_1e-4": kkt_info,
            "phases_ms": phases, "model_iter_ms": per_iter_ms,
            "solver": {"status": res["status_name"], "kkt": res["kkt"], "restarts": res["restarts"],
+                      "bp_tile_cfg": res["tile_cfg"],
                       "check_every": args.check_every, "need_columns": need_cols,
                       "active_columns": act_cols}}
     sipo.sipo_destroy(ctx)
@@ -367,7 +382,8 @@ def main(argv=None):
     p.add_argument("--storage", default="f32", choices=["f32", "bf16", "f64"])
     p.add_argument("--check-every", type=int, default=64)
     p.add_argument("--profile-iters", type=int, default=8)
-    p.add_argument("--kkt-iters", type=int, default=6000)
+    p.add_argument("--kkt-iters", type=int, default=2048)
+    p.add_argument("--feasible-ratio", type=float, default=0.85)
     p.add_argument("--cpu-seconds", type=float, default=20.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     args = p.parse_args(argv)

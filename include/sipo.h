@@ -143,6 +143,7 @@ typedef struct sipo_result {
   double f_crit, alpha, dtvr_f, dsr, psr_f, s;
   double solve_ms;
   long long kernel_launches;
+  int tile_cfg; /* backprojector tile table entry in use */
 } sipo_result;
 
 /* Creates a solver context: copies the geometry and the target dose f_T
@@ -216,7 +217,9 @@ int sipo_profile(sipo_ctx *ctx, int iters, double *phase_ms, int n_phases);
 int sipo_phase_count(void);
 const char *sipo_phase_name(int i);
 
-/* Number of entries in the projector tile table (for sipo_tolerances.tile_cfg). */
+/* Number of entries in the backprojector tile table (for sipo_tolerances.tile_cfg):
+ * 0 = 8 voxel columns per warp at 2 blocks/SM, 1 = 4 columns at 2 blocks/SM,
+ * 2 = 4 columns at 3 blocks/SM. */
 int sipo_tile_count(void);
 
 /* Total kernels this library has launched in this process (graph nodes count

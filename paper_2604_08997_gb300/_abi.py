@@ -49,7 +49,7 @@ class sipo_result(Structure):
                 ("gap", c_double), ("pobj", c_double), ("dobj", c_double), ("u", c_double),
                 ("v", c_double), ("omega", c_double), ("f_crit", c_double), ("alpha", c_double),
                 ("dtvr_f", c_double), ("dsr", c_double), ("psr_f", c_double), ("s", c_double),
-                ("solve_ms", c_double), ("kernel_launches", c_longlong)]
+                ("solve_ms", c_double), ("kernel_launches", c_longlong), ("tile_cfg", c_int)]
 
     def as_dict(self) -> dict:
         d = {name: getattr(self, name) for name, _ in self._fields_}

@@ -93,7 +93,7 @@ struct Solver final : SolverBase {
   int zl = 1;
   int P = 64;
   bool psf = false;
-  int bp_nv = 8;     // backprojector voxel columns per warp (tile table entry)
+  int bp_nv = 0;     // backprojector tile table entry
 
   // device memory
   std::vector<void*> allocs;
@@ -104,6 +104,7 @@ struct Solver final : SolverBase {
   C* dtaps[3] = {nullptr, nullptr, nullptr};
   float* fT = nullptr;
   uint8_t *lab = nullptr, *mask = nullptr, *act_col = nullptr, *need = nullptr;
+  int2* rspan = nullptr;  // per-ray walked span meeting columns in `need`
   C *ft = nullptr, *row = nullptr, *col = nullptr;
   S *y = nullptr, *y0 = nullptr, *yp = nullptr, *ybar = nullptr;
   C *gp = nullptr, *g0 = nullptr, *gc = nullptr;
@@ -457,6 +458,8 @@ struct Solver final : SolverBase {
         k_need_cols<<<gc, kThreads, 0, stream>>>(lab, need, nx, ny, nz);
       }
     }
+    rspan = dalloc<int2>(size_t(na) * nd);
+    launch_ray_spans<C>(geo(), need, rspan, stream);
     // iterate storage
     y = dalloc<S>(SN); y0 = dalloc<S>(SN); yp = dalloc<S>(SN); ybar = dalloc<S>(SN);
     gp = dalloc<C>(SN); g0 = dalloc<C>(SN); gc = dalloc<C>(SN); col = dalloc<C>(SN);
@@ -565,22 +568,21 @@ struct Solver final : SolverBase {
     solved = false;
   }
 
-  // Tile table: entry 0 = 8 voxel columns per backprojector warp, 1 = 4.
-  // tile_cfg -1 times a few un-captured iterations of each entry with CUDA
-  // events (backprojection phase) and keeps the fastest.
+  // Tile table (kBpTiles entries, see launch_backproject).  tile_cfg >= 0
+  // selects an entry; -1 times a few un-captured iterations of each entry with
+  // CUDA events (backprojection phase) and keeps the fastest.
   void choose_tiles() {
-    if (tol.tile_cfg == 0 || tol.tile_cfg == 1) {
-      bp_nv = tol.tile_cfg == 0 ? 8 : 4;
+    if (tol.tile_cfg >= 0) {
+      if (tol.tile_cfg >= kBpTiles) fail(SIPO_ERR_INVALID_ARG, "tile_cfg out of range");
+      bp_nv = tol.tile_cfg;
       return;
     }
-    if (tol.tile_cfg >= 0) fail(SIPO_ERR_INVALID_ARG, "tile_cfg must be -1, 0 or 1");
-    const int cand[2] = {8, 4};
     float best = 1e30f;
-    int best_nv = 8;
+    int best_tile = 0;
     cudaEvent_t ev[7];
     for (auto& e : ev) ck(cudaEventCreate(&e), "event");
-    for (int nv : cand) {
-      bp_nv = nv;
+    for (int tile = 0; tile < kBpTiles; ++tile) {
+      bp_nv = tile;
       init_state();
       float tot = 0.0f;
       for (int it = 0; it < 4; ++it) {
@@ -590,10 +592,10 @@ struct Solver final : SolverBase {
         ck(cudaEventElapsedTime(&t, ev[3], ev[6]), "elapsed");
         if (it > 0) tot += t;  // first iteration is a warm-up
       }
-      if (tot < best) { best = tot; best_nv = nv; }
+      if (tot < best) { best = tot; best_tile = tile; }
     }
     for (auto& e : ev) cudaEventDestroy(e);
-    bp_nv = best_nv;
+    bp_nv = best_tile;
   }
 
   void enqueue_psf_q(const S* src, cudaStream_t s) { psf3<S, S>(src, kq, t1, t2, -1, s); }
@@ -611,7 +613,7 @@ struct Solver final : SolverBase {
     rec(1);
     if (psf) enqueue_psf_q(q, s);
     rec(2);
-    launch_project<S, S, C, kFpPrimal, C>(g, psf ? kq : q, B, (C*)nullptr, act_col, vec, s);
+    launch_project<S, S, C, kFpPrimal, C>(g, psf ? kq : q, B, (C*)nullptr, act_col, vec, s, need, rspan);
     count(1);
     rec(3);
     if (psf) {
@@ -646,7 +648,7 @@ struct Solver final : SolverBase {
     k_scalar_step<true><<<1, kThreads, 0, s>>>(st, part);
     count(1);
     if (psf) enqueue_psf_q(q, s);
-    launch_project<S, S, C, kFpPrimalCheck, C>(g, psf ? kq : q, B, (C*)nullptr, act_col, vec, s);
+    launch_project<S, S, C, kFpPrimalCheck, C>(g, psf ? kq : q, B, (C*)nullptr, act_col, vec, s, need, rspan);
     count(1);
     if (psf) {
       launch_backproject<S, S, C, kBpStore, C>(g, ybar, B, braw, need, vec, s, bp_nv);
@@ -658,7 +660,7 @@ struct Solver final : SolverBase {
       launch_backproject<S, S, C, kBpDualCheck, C>(g, ybar, B, (C*)nullptr, need, vec, s, bp_nv);
       count(1);
     }
-    launch_project<S, S, C, kFpResid, C>(g, psf ? kq : qp, B, (C*)nullptr, act_col, vec, s);
+    launch_project<S, S, C, kFpResid, C>(g, psf ? kq : qp, B, (C*)nullptr, act_col, vec, s, need, rspan);
     count(1);
     k_scalar_check<<<1, kThreads, 0, s>>>(st, part);
     count(1);
@@ -758,6 +760,7 @@ struct Solver final : SolverBase {
     res->s = m[6];
     res->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     res->kernel_launches = launches;
+    res->tile_cfg = bp_nv;
   }
 
   // copies n elements of S (converted to C) to out (host or device)
@@ -937,7 +940,7 @@ const char* sipo_phase_name(int i) {
   return (i >= 0 && i < sipo::kNumPhases) ? sipo::kPhaseNames[i] : "";
 }
 
-int sipo_tile_count(void) { return 2; }
+int sipo_tile_count(void) { return sipo::kBpTiles; }
 
 int sipo_create(const sipo_geometry* geo, const float* f_T, int f_T_location, const sipo_case_params* cp,
                 const sipo_tolerances* tol, void* stream, sipo_ctx** out) {

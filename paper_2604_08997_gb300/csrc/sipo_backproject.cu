@@ -5,21 +5,27 @@
 
 namespace sipo {
 
+// Tile table: 0 = 8 columns per warp, 2 blocks/SM; 1 = 4 columns, 2 blocks/SM;
+// 2 = 4 columns, 3 blocks/SM (tighter register budget).
+template <typename SI, typename S, typename C, int ZL, int MODE, typename O>
+static void launch_bp_zl(const Geo<C>& g, const SI* sino, const Bufs<S, C>& b, O* out, const uint8_t* need,
+                         cudaStream_t stream, int tile) {
+  if (tile == 1)
+    k_backproject<SI, S, C, ZL, 4, 2, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, sino, b, out, need);
+  else if (tile == 2)
+    k_backproject<SI, S, C, ZL, 4, 3, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, sino, b, out, need);
+  else
+    k_backproject<SI, S, C, ZL, 8, 2, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, sino, b, out, need);
+}
+
 template <typename SI, typename S, typename C, int MODE, typename O>
 void launch_backproject(const Geo<C>& g, const SI* sino, const Bufs<S, C>& b, O* out,
-                        const uint8_t* need, bool vec, cudaStream_t stream, int nv) {
+                        const uint8_t* need, bool vec, cudaStream_t stream, int tile) {
   constexpr int ZLV = sizeof(SI) == 8 ? 4 : 8;
-  if (vec) {
-    if (nv == 4)
-      k_backproject<SI, S, C, ZLV, 4, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, sino, b, out, need);
-    else
-      k_backproject<SI, S, C, ZLV, 8, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, sino, b, out, need);
-  } else {
-    if (nv == 4)
-      k_backproject<SI, S, C, 1, 4, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, sino, b, out, need);
-    else
-      k_backproject<SI, S, C, 1, 8, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, sino, b, out, need);
-  }
+  if (vec)
+    launch_bp_zl<SI, S, C, ZLV, MODE, O>(g, sino, b, out, need, stream, tile);
+  else
+    launch_bp_zl<SI, S, C, 1, MODE, O>(g, sino, b, out, need, stream, tile);
 }
 
 #define SIPO_BP(SI, S, C, M, O) \

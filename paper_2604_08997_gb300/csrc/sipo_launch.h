@@ -10,14 +10,23 @@ namespace sipo {
 
 // vec selects the 16-byte vector z-path (needs nz % ZL == 0, ZL = 8 for
 // 4/2-byte elements and 4 for doubles) over the scalar path (ZL = 1).
+// need: per-column flag of voxels whose input may be non-zero (nullptr: all);
+// rspan: per-ray walked-axis span holding such columns (nullptr: whole ray).
 template <typename SI, typename S, typename C, int MODE, typename O>
 void launch_project(const Geo<C>& g, const SI* vol, const Bufs<S, C>& b, O* out,
-                    const uint8_t* act_col, bool vec, cudaStream_t stream);
+                    const uint8_t* act_col, bool vec, cudaStream_t stream,
+                    const uint8_t* need = nullptr, const int2* rspan = nullptr);
 
-// nv: voxel columns per warp (4 or 8; the tile table of sipo_tile_count).
+// Per-ray span of the projector walk that meets flagged columns (k_ray_spans).
+template <typename C>
+void launch_ray_spans(const Geo<C>& g, const uint8_t* need, int2* out, cudaStream_t stream);
+
+// tile: entry of the backprojector tile table (0: 8 columns per warp, 2
+// blocks/SM; 1: 4 columns, 2 blocks/SM; 2: 4 columns, 3 blocks/SM).
+constexpr int kBpTiles = 3;
 template <typename SI, typename S, typename C, int MODE, typename O>
 void launch_backproject(const Geo<C>& g, const SI* sino, const Bufs<S, C>& b, O* out,
-                        const uint8_t* need, bool vec, cudaStream_t stream, int nv = 8);
+                        const uint8_t* need, bool vec, cudaStream_t stream, int tile = 0);
 
 template <typename C> constexpr int vec_zl() { return sizeof(C) == 8 ? 4 : 8; }
 

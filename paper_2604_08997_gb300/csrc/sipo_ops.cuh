@@ -44,10 +44,15 @@ __device__ __forceinline__ int ceil_int(double x) { return int(ceil(x)); }
 constexpr float kCandEps = 1e-3f;
 
 // SI: element type read from `vol`; O: element type written by kFpStore.
+// act_col: per (angle, bin) flag of rays with an active z (solver modes skip
+// the others); need: per (y, x) column flag of voxels whose input can be
+// non-zero (the solver's dual combination vanishes on exterior columns), or
+// nullptr to gather every in-vial voxel.
 template <typename SI, typename S, typename C, int ZL, int MODE, typename O>
 __global__ void __launch_bounds__(kThreads)
 k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __restrict__ out,
-          const uint8_t* __restrict__ act_col) {
+          const uint8_t* __restrict__ act_col, const uint8_t* __restrict__ need,
+          const int2* __restrict__ rspan) {
   if (MODE != kFpStore && b.st->done) return;
   constexpr int ZC = 32 * ZL;
   constexpr int NR = MODE == kFpPrimalCheck ? 2 : (MODE == kFpResid ? 4 : 0);
@@ -93,6 +98,11 @@ k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __r
           lo = max(0, -ceil_int(-(yc - hy + g.cy)));
           hi = min(g.ny - 1, ceil_int(yc + hy + g.cy));
         }
+        if (rspan) {
+          const int2 r = rspan[(size_t)k * g.nd + j];
+          lo = max(lo, r.x);
+          hi = min(hi, r.y);
+        }
         const C inv_c = C(1) / c, h = C(1) / fabs(c) + C(kCandEps);
         C yf = C(lo) - g.cy;
         for (int iy = lo; iy <= hi; ++iy, yf += C(1)) {
@@ -111,7 +121,8 @@ k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __r
             floor_split(u, flo, i0);
             const C wv = u - flo;
             const int ix = ix0 + m;
-            const bool ok = ix >= sp.x && ix <= sp.y;
+            bool ok = ix >= sp.x && ix <= sp.y;
+            if (need != nullptr && ok) ok = need[(size_t)iy * g.nx + ix] != 0;
             wt[m] = ok ? ((flo == jf) ? (C(1) - wv) : ((flo == jm) ? wv : C(0))) : C(0);
           }
           const C eyv = g.ex ? g.ey[(size_t)k * g.ny + iy] : C(1);
@@ -135,6 +146,11 @@ k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __r
           lo = max(0, -ceil_int(-(xc - hx + g.cx)));
           hi = min(g.nx - 1, ceil_int(xc + hx + g.cx));
         }
+        if (rspan) {
+          const int2 r = rspan[(size_t)k * g.nd + j];
+          lo = max(lo, r.x);
+          hi = min(hi, r.y);
+        }
         const C inv_s = C(1) / s, h = C(1) / fabs(s) + C(kCandEps);
         C xf = C(lo) - g.cx;
         for (int ix = lo; ix <= hi; ++ix, xf += C(1)) {
@@ -152,7 +168,8 @@ k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __r
             floor_split(u, flo, i0);
             const C wv = u - flo;
             const int iy = iy0 + m;
-            const bool ok = iy >= sp.x && iy <= sp.y;
+            bool ok = iy >= sp.x && iy <= sp.y;
+            if (need != nullptr && ok) ok = need[(size_t)iy * g.nx + ix] != 0;
             wt[m] = ok ? ((flo == jf) ? (C(1) - wv) : ((flo == jm) ? wv : C(0))) : C(0);
           }
           const C exv = g.ex ? g.ex[(size_t)k * g.nx + ix] : C(1);
@@ -248,8 +265,8 @@ __device__ __forceinline__ void bp_angle(const Geo<C>& g, const SI* srow, const 
 // block), ZL z values per lane.  need: per (iy, ix) column flag (nullptr:
 // every column); columns without it are skipped (and left unwritten in
 // kBpStore mode unless need is nullptr).
-template <typename SI, typename S, typename C, int ZL, int NV, int MODE, typename O>
-__global__ void __launch_bounds__(kThreads, 2)
+template <typename SI, typename S, typename C, int ZL, int NV, int MINB, int MODE, typename O>
+__global__ void __launch_bounds__(kThreads, MINB)
 k_backproject(const Geo<C> g, const SI* __restrict__ sino, const Bufs<S, C> b, O* __restrict__ out,
               const uint8_t* __restrict__ need) {
   if (MODE != kBpStore && b.st->done) return;
@@ -309,13 +326,77 @@ k_backproject(const Geo<C> g, const SI* __restrict__ sino, const Bufs<S, C> b, O
       const size_t base = ((size_t)iy * g.nx + ix) * g.nz + z0;
       if constexpr (MODE == kBpStore) {
         if (need == nullptr || ((mask >> v) & 1u)) store_z<O, C, ZL>(out + base, acc[v]);
-      } else {
-        if ((mask >> v) & 1u) dual_update<S, C, ZL, MODE == kBpDualCheck>(b, sc, base, acc[v], red);
+      } else if ((mask >> v) & 1u) {
+        // the epilogue runs on halves of the z-vector to keep its live range short
+        constexpr int H = (ZL % 8 == 0) ? ZL / 2 : ZL;
+#pragma unroll
+        for (int h0 = 0; h0 < ZL; h0 += H) {
+          C part[H];
+#pragma unroll
+          for (int i = 0; i < H; ++i) part[i] = acc[v][h0 + i];
+          dual_update<S, C, H, MODE == kBpDualCheck>(b, sc, base + h0, part, red);
+        }
       }
     }
   }
   if constexpr (MODE == kBpDual) block_reduce_store<2>(red, b.part, kSlSBand);
   if constexpr (MODE == kBpDualCheck) block_reduce_store<kCheckSlots, kCheckMaxMask>(red, b.part, kSlRp2);
+}
+
+// ----------------------------------------------------------- ray row spans
+// For each ray (angle k, bin j): the first and last index along its walked
+// axis at which a candidate voxel lies in a flagged column (need).  The span
+// tests the window of k_project widened by one candidate on each side, so a
+// one-off difference in how the compiler rounds the window start cannot drop
+// a row: restricting the walk to the span skips only rows whose taps are all
+// zero.  Empty spans are (1, 0).
+template <typename C>
+__global__ void __launch_bounds__(kThreads)
+k_ray_spans(const Geo<C> g, const uint8_t* __restrict__ need, int2* __restrict__ out) {
+  const long long n = (long long)g.na * g.nd;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
+       r += (long long)gridDim.x * blockDim.x) {
+    const int k = int(r / g.nd), j = int(r % g.nd);
+    const C c = g.cs[2 * k], s = g.cs[2 * k + 1];
+    const C jf = C(j);
+    int first = 1, last = 0;
+    if (fabs(c) >= fabs(s)) {
+      const C inv_c = C(1) / c, h = C(1) / fabs(c) + C(kCandEps);
+      for (int iy = 0; iy < g.ny; ++iy) {
+        const int2 sp = g.xspan[iy];
+        if (sp.x > sp.y) continue;
+        const C inner = geo_inner(C(iy) - g.cy, s, g.off);
+        const int ix0 = ceil_int((jf - inner) * inv_c + g.cx - h);
+        bool hit = false;
+        for (int m = -1; m < 4; ++m) {
+          const int ix = ix0 + m;
+          if (ix >= sp.x && ix <= sp.y && need[(size_t)iy * g.nx + ix]) hit = true;
+        }
+        if (hit) {
+          if (first > last) first = iy;
+          last = iy;
+        }
+      }
+    } else {
+      const C inv_s = C(1) / s, h = C(1) / fabs(s) + C(kCandEps);
+      for (int ix = 0; ix < g.nx; ++ix) {
+        const int2 sp = g.yspan[ix];
+        if (sp.x > sp.y) continue;
+        const C xf = C(ix) - g.cx;
+        const int iy0 = ceil_int((jf - g.off - xf * c) * inv_s + g.cy - h);
+        bool hit = false;
+        for (int m = -1; m < 4; ++m) {
+          const int iy = iy0 + m;
+          if (iy >= sp.x && iy <= sp.y && need[(size_t)iy * g.nx + ix]) hit = true;
+        }
+        if (hit) {
+          if (first > last) first = ix;
+          last = ix;
+        }
+      }
+    }
+    out[r] = make_int2(first, last);
+  }
 }
 
 // ------------------------------------------------------- separable PSF pass

@@ -3,21 +3,34 @@
 #include "sipo_launch.h"
 #include "sipo_ops.cuh"
 
+#include <algorithm>
+
 namespace sipo {
 
 template <typename SI, typename S, typename C, int MODE, typename O>
 void launch_project(const Geo<C>& g, const SI* vol, const Bufs<S, C>& b, O* out,
-                    const uint8_t* act_col, bool vec, cudaStream_t stream) {
+                    const uint8_t* act_col, bool vec, cudaStream_t stream, const uint8_t* need,
+                    const int2* rspan) {
   constexpr int ZLV = sizeof(SI) == 8 ? 4 : 8;
   if (vec)
-    k_project<SI, S, C, ZLV, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, vol, b, out, act_col);
+    k_project<SI, S, C, ZLV, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, vol, b, out, act_col, need, rspan);
   else
-    k_project<SI, S, C, 1, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, vol, b, out, act_col);
+    k_project<SI, S, C, 1, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, vol, b, out, act_col, need, rspan);
 }
+
+template <typename C>
+void launch_ray_spans(const Geo<C>& g, const uint8_t* need, int2* out, cudaStream_t stream) {
+  const long long n = (long long)g.na * g.nd;
+  const int grid = int(std::min<long long>((n + kThreads - 1) / kThreads, 152LL * 16));
+  k_ray_spans<C><<<grid, kThreads, 0, stream>>>(g, need, out);
+}
+template void launch_ray_spans<float>(const Geo<float>&, const uint8_t*, int2*, cudaStream_t);
+template void launch_ray_spans<double>(const Geo<double>&, const uint8_t*, int2*, cudaStream_t);
 
 #define SIPO_FP(SI, S, C, M, O) \
   template void launch_project<SI, S, C, M, O>(const Geo<C>&, const SI*, const Bufs<S, C>&, O*, \
-                                                const uint8_t*, bool, cudaStream_t);
+                                                const uint8_t*, bool, cudaStream_t, const uint8_t*, \
+                                                const int2*);
 #define SIPO_FP_SOLVER(S, C)          \
   SIPO_FP(S, S, C, kFpPrimal, C)      \
   SIPO_FP(S, S, C, kFpPrimalCheck, C) \
