@@ -105,6 +105,7 @@ struct Solver final : SolverBase {
   float* fT = nullptr;
   uint8_t *lab = nullptr, *mask = nullptr, *act_col = nullptr, *need = nullptr;
   int2* rspan = nullptr;  // per-ray walked span meeting columns in `need`
+  NeedBits nbits{};      // `need` packed as bits for the projector
   C *ft = nullptr, *row = nullptr, *col = nullptr;
   S *y = nullptr, *y0 = nullptr, *yp = nullptr, *ybar = nullptr;
   C *gp = nullptr, *g0 = nullptr, *gc = nullptr;
@@ -460,6 +461,16 @@ struct Solver final : SolverBase {
     }
     rspan = dalloc<int2>(size_t(na) * nd);
     launch_ray_spans<C>(geo(), need, rspan, stream);
+    {
+      const int wr = (nx + 2 * kNbPad + 31) / 32 + 1, wc = (ny + 2 * kNbPad + 31) / 32 + 1;
+      uint32_t* br = dalloc<uint32_t>(size_t(ny) * wr);
+      uint32_t* bc = dalloc<uint32_t>(size_t(nx) * wc);
+      launch_need_bits(need, br, bc, nx, ny, wr, wc, stream);
+      nbits.rows = br;
+      nbits.cols = bc;
+      nbits.wr = wr;
+      nbits.wc = wc;
+    }
     // iterate storage
     y = dalloc<S>(SN); y0 = dalloc<S>(SN); yp = dalloc<S>(SN); ybar = dalloc<S>(SN);
     gp = dalloc<C>(SN); g0 = dalloc<C>(SN); gc = dalloc<C>(SN); col = dalloc<C>(SN);
@@ -613,7 +624,7 @@ struct Solver final : SolverBase {
     rec(1);
     if (psf) enqueue_psf_q(q, s);
     rec(2);
-    launch_project<S, S, C, kFpPrimal, C>(g, psf ? kq : q, B, (C*)nullptr, act_col, vec, s, need, rspan);
+    launch_project<S, S, C, kFpPrimal, C>(g, psf ? kq : q, B, (C*)nullptr, act_col, vec, s, nbits, rspan);
     count(1);
     rec(3);
     if (psf) {
@@ -648,7 +659,7 @@ struct Solver final : SolverBase {
     k_scalar_step<true><<<1, kThreads, 0, s>>>(st, part);
     count(1);
     if (psf) enqueue_psf_q(q, s);
-    launch_project<S, S, C, kFpPrimalCheck, C>(g, psf ? kq : q, B, (C*)nullptr, act_col, vec, s, need, rspan);
+    launch_project<S, S, C, kFpPrimalCheck, C>(g, psf ? kq : q, B, (C*)nullptr, act_col, vec, s, nbits, rspan);
     count(1);
     if (psf) {
       launch_backproject<S, S, C, kBpStore, C>(g, ybar, B, braw, need, vec, s, bp_nv);
@@ -660,7 +671,7 @@ struct Solver final : SolverBase {
       launch_backproject<S, S, C, kBpDualCheck, C>(g, ybar, B, (C*)nullptr, need, vec, s, bp_nv);
       count(1);
     }
-    launch_project<S, S, C, kFpResid, C>(g, psf ? kq : qp, B, (C*)nullptr, act_col, vec, s, need, rspan);
+    launch_project<S, S, C, kFpResid, C>(g, psf ? kq : qp, B, (C*)nullptr, act_col, vec, s, nbits, rspan);
     count(1);
     k_scalar_check<<<1, kThreads, 0, s>>>(st, part);
     count(1);

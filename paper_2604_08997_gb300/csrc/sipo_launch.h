@@ -5,17 +5,23 @@
 #include <cuda_runtime.h>
 
 #include "sipo_solver.cuh"
+#include "sipo_ops.cuh"
 
 namespace sipo {
 
 // vec selects the 16-byte vector z-path (needs nz % ZL == 0, ZL = 8 for
 // 4/2-byte elements and 4 for doubles) over the scalar path (ZL = 1).
-// need: per-column flag of voxels whose input may be non-zero (nullptr: all);
-// rspan: per-ray walked-axis span holding such columns (nullptr: whole ray).
+// nb: packed per-column flags of voxels whose input may be non-zero (rows ==
+// nullptr: every in-vial voxel); rspan: per-ray walked-axis span holding such
+// columns (nullptr: whole ray).
 template <typename SI, typename S, typename C, int MODE, typename O>
 void launch_project(const Geo<C>& g, const SI* vol, const Bufs<S, C>& b, O* out,
                     const uint8_t* act_col, bool vec, cudaStream_t stream,
-                    const uint8_t* need = nullptr, const int2* rspan = nullptr);
+                    const NeedBits& nb = NeedBits{}, const int2* rspan = nullptr);
+
+// Packs need[y][x] into the row-major and column-major bit arrays of NeedBits.
+void launch_need_bits(const uint8_t* need, uint32_t* rows, uint32_t* cols, int nx, int ny, int wr, int wc,
+                      cudaStream_t stream);
 
 // Per-ray span of the projector walk that meets flagged columns (k_ray_spans).
 template <typename C>

@@ -24,6 +24,26 @@ enum FpMode : int { kFpStore = 0, kFpPrimal = 1, kFpPrimalCheck = 2, kFpResid = 
 enum BpMode : int { kBpStore = 0, kBpDual = 1, kBpDualCheck = 2 };
 
 
+// Column flags packed as bits for the projector's candidate test.  rows: for
+// each y, bit (x + kNbPad) of word array [y][words] says whether column (y, x)
+// may hold a non-zero input; cols: the same indexed [x][words] by y.  The pad
+// of kNbPad zero bits on both ends lets the three-candidate window be read
+// without bounds checks (the walk is clipped to spans within the grid).
+constexpr int kNbPad = 32;
+struct NeedBits {
+  const uint32_t* rows;  // nullptr: use the vial spans instead
+  const uint32_t* cols;
+  int wr, wc;            // words per row / per column
+  __device__ __forceinline__ unsigned window(const uint32_t* base, int line, int start) const {
+    const int w = base == rows ? wr : wc;
+    int b = start + kNbPad;
+    b = b < 0 ? 0 : (b > 32 * w - 35 ? 32 * w - 35 : b);
+    const uint32_t* p = base + (size_t)line * w + (b >> 5);
+    const unsigned long long pair = (unsigned long long)__ldg(p) | ((unsigned long long)__ldg(p + 1) << 32);
+    return unsigned(pair >> (b & 31)) & 7u;
+  }
+};
+
 // --------------------------------------------------------------- projector
 // Smallest integer >= x without the conversion unit (via floor_split of -x).
 __device__ __forceinline__ int ceil_int(float x) {
@@ -51,8 +71,8 @@ constexpr float kCandEps = 1e-3f;
 template <typename SI, typename S, typename C, int ZL, int MODE, typename O>
 __global__ void __launch_bounds__(kThreads)
 k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __restrict__ out,
-          const uint8_t* __restrict__ act_col, const uint8_t* __restrict__ need,
-          const int2* __restrict__ rspan) {
+          const uint8_t* __restrict__ act_col, const NeedBits nb, const int2* __restrict__ rspan) {
+  const bool use_bits = nb.rows != nullptr;
   if (MODE != kFpStore && b.st->done) return;
   constexpr int ZC = 32 * ZL;
   constexpr int NR = MODE == kFpPrimalCheck ? 2 : (MODE == kFpResid ? 4 : 0);
@@ -106,11 +126,19 @@ k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __r
         const C inv_c = C(1) / c, h = C(1) / fabs(c) + C(kCandEps);
         C yf = C(lo) - g.cy;
         for (int iy = lo; iy <= hi; ++iy, yf += C(1)) {
-          const int2 sp = g.xspan[iy];
-          if (sp.x > sp.y) continue;
           const C inner = geo_inner(yf, s, g.off);
           const C ixc = (jf - inner) * inv_c + g.cx;
           const int ix0 = ceil_int(ixc - h);
+          unsigned okm;
+          if (use_bits) {
+            okm = nb.window(nb.rows, iy, ix0);
+          } else {
+            const int2 sp = g.xspan[iy];
+            okm = 0u;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) okm |= unsigned(ix0 + m >= sp.x && ix0 + m <= sp.y) << m;
+          }
+          if (okm == 0u) continue;
           const C xf0 = C(ix0) - g.cx;
           C wt[3];
 #pragma unroll
@@ -120,10 +148,8 @@ k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __r
             int i0;
             floor_split(u, flo, i0);
             const C wv = u - flo;
-            const int ix = ix0 + m;
-            bool ok = ix >= sp.x && ix <= sp.y;
-            if (need != nullptr && ok) ok = need[(size_t)iy * g.nx + ix] != 0;
-            wt[m] = ok ? ((flo == jf) ? (C(1) - wv) : ((flo == jm) ? wv : C(0))) : C(0);
+            const C t = (flo == jf) ? (C(1) - wv) : ((flo == jm) ? wv : C(0));
+            wt[m] = ((okm >> m) & 1u) ? t : C(0);
           }
           const C eyv = g.ex ? g.ey[(size_t)k * g.ny + iy] : C(1);
           const SI* vrow = vz + ((size_t)iy * g.nx) * g.nz;
@@ -154,10 +180,18 @@ k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __r
         const C inv_s = C(1) / s, h = C(1) / fabs(s) + C(kCandEps);
         C xf = C(lo) - g.cx;
         for (int ix = lo; ix <= hi; ++ix, xf += C(1)) {
-          const int2 sp = g.yspan[ix];
-          if (sp.x > sp.y) continue;
           const C iyc = (jf - g.off - xf * c) * inv_s + g.cy;
           const int iy0 = ceil_int(iyc - h);
+          unsigned okm;
+          if (use_bits) {
+            okm = nb.window(nb.cols, ix, iy0);
+          } else {
+            const int2 sp = g.yspan[ix];
+            okm = 0u;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) okm |= unsigned(iy0 + m >= sp.x && iy0 + m <= sp.y) << m;
+          }
+          if (okm == 0u) continue;
           const C yf0 = C(iy0) - g.cy;
           C wt[3];
 #pragma unroll
@@ -167,10 +201,8 @@ k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __r
             int i0;
             floor_split(u, flo, i0);
             const C wv = u - flo;
-            const int iy = iy0 + m;
-            bool ok = iy >= sp.x && iy <= sp.y;
-            if (need != nullptr && ok) ok = need[(size_t)iy * g.nx + ix] != 0;
-            wt[m] = ok ? ((flo == jf) ? (C(1) - wv) : ((flo == jm) ? wv : C(0))) : C(0);
+            const C t = (flo == jf) ? (C(1) - wv) : ((flo == jm) ? wv : C(0));
+            wt[m] = ((okm >> m) & 1u) ? t : C(0);
           }
           const C exv = g.ex ? g.ex[(size_t)k * g.nx + ix] : C(1);
           const SI* vcol = vz + (size_t)ix * g.nz;

@@ -7,15 +7,45 @@
 
 namespace sipo {
 
+// bits[line][word] from flags need[y][x]; by_rows selects line = y (bits over
+// x) or line = x (bits over y).
+__global__ void k_need_bits(const uint8_t* __restrict__ need, uint32_t* __restrict__ bits, int nx, int ny,
+                            int words, int by_rows) {
+  const int lines = by_rows ? ny : nx, len = by_rows ? nx : ny;
+  const long long n = (long long)lines * words;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int line = int(i / words), w = int(i % words);
+    uint32_t v = 0;
+    for (int bt = 0; bt < 32; ++bt) {
+      const int pos = w * 32 + bt - kNbPad;
+      if (pos >= 0 && pos < len) {
+        const int x = by_rows ? pos : line, y = by_rows ? line : pos;
+        if (need[(size_t)y * nx + x]) v |= 1u << bt;
+      }
+    }
+    bits[i] = v;
+  }
+}
+
+
 template <typename SI, typename S, typename C, int MODE, typename O>
 void launch_project(const Geo<C>& g, const SI* vol, const Bufs<S, C>& b, O* out,
-                    const uint8_t* act_col, bool vec, cudaStream_t stream, const uint8_t* need,
+                    const uint8_t* act_col, bool vec, cudaStream_t stream, const NeedBits& nb,
                     const int2* rspan) {
   constexpr int ZLV = sizeof(SI) == 8 ? 4 : 8;
   if (vec)
-    k_project<SI, S, C, ZLV, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, vol, b, out, act_col, need, rspan);
+    k_project<SI, S, C, ZLV, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, vol, b, out, act_col, nb, rspan);
   else
-    k_project<SI, S, C, 1, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, vol, b, out, act_col, need, rspan);
+    k_project<SI, S, C, 1, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, vol, b, out, act_col, nb, rspan);
+}
+
+void launch_need_bits(const uint8_t* need, uint32_t* rows, uint32_t* cols, int nx, int ny, int wr, int wc,
+                      cudaStream_t stream) {
+  const int gr = int(std::min<long long>(((long long)ny * wr + kThreads - 1) / kThreads, 152LL * 16));
+  const int gc = int(std::min<long long>(((long long)nx * wc + kThreads - 1) / kThreads, 152LL * 16));
+  k_need_bits<<<gr, kThreads, 0, stream>>>(need, rows, nx, ny, wr, 1);
+  k_need_bits<<<gc, kThreads, 0, stream>>>(need, cols, nx, ny, wc, 0);
 }
 
 template <typename C>
@@ -29,7 +59,7 @@ template void launch_ray_spans<double>(const Geo<double>&, const uint8_t*, int2*
 
 #define SIPO_FP(SI, S, C, M, O) \
   template void launch_project<SI, S, C, M, O>(const Geo<C>&, const SI*, const Bufs<S, C>&, O*, \
-                                                const uint8_t*, bool, cudaStream_t, const uint8_t*, \
+                                                const uint8_t*, bool, cudaStream_t, const NeedBits&, \
                                                 const int2*);
 #define SIPO_FP_SOLVER(S, C)          \
   SIPO_FP(S, S, C, kFpPrimal, C)      \
