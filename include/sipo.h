@@ -167,10 +167,15 @@ int sipo_create(const sipo_geometry *geo, const float *f_T, int f_T_location,
  * INVALID_ARG, CUDA, TIMEOUT. */
 int sipo_solve(sipo_ctx *ctx, void *y_out, int y_location, sipo_result *res);
 
-/* Solves n independent contexts as one batch: their iterations are issued
- * together in one captured CUDA graph per check period so that small LPs of
- * a parameter sweep share the device.  y_outs may be NULL or an array of n
- * nullable pointers (same rules as sipo_solve).  results: n entries. */
+/* Solves n independent contexts as one batch (a parameter sweep): one CUDA
+ * graph holds one check period of every context as parallel branches (each on
+ * its context's stream), so small LPs share the device and the host waits
+ * once per period.  Contexts that finish keep their branch but exit at once.
+ * In a batch the iteration limit of each context is rounded up to a whole
+ * number of its check periods.  Each context must appear once; contexts
+ * created on the same stream run one after another.  y_outs may be NULL or an
+ * array of n nullable pointers (same rules as sipo_solve).  results: n
+ * entries. */
 int sipo_solve_batched(sipo_ctx **ctxs, int n, void **y_outs, int y_location,
                        sipo_result *results);
 

@@ -13,7 +13,10 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
+#include <tuple>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -69,7 +72,23 @@ struct SolverBase {
   virtual long long max_iter() const = 0;
   virtual void set_tolerances(const sipo_tolerances* t) = 0;
   virtual int get_trace(double* out, int max_entries) = 0;
+  // batched solves: zero start without a graph, one check period enqueued on
+  // `s` (check step + period - 1 fused steps) followed by a copy of the state
+  // to the pinned host mirror, and that mirror
+  virtual void init_for_batch() = 0;
+  virtual void enqueue_period(cudaStream_t s) = 0;
+  virtual const Scal& host_state() const = 0;
 };
+
+// Autotuned backprojector tile per problem shape (process-wide cache).
+struct TileKey {
+  int nx, ny, nz, na, nd, storage, psf;
+  bool operator<(const TileKey& o) const {
+    return std::tie(nx, ny, nz, na, nd, storage, psf) < std::tie(o.nx, o.ny, o.nz, o.na, o.nd, o.storage, o.psf);
+  }
+};
+std::mutex g_tile_mutex;
+std::map<TileKey, int> g_tile_cache;
 
 constexpr int kNumPhases = 7;
 const char* kPhaseNames[kNumPhases] = {"scalar_step", "psf_q",       "project_primal", "backproject",
@@ -192,6 +211,20 @@ struct Solver final : SolverBase {
     }
     return n;
   }
+
+  void init_for_batch() override {
+    init_state();
+    launches = 0;
+    t_start = std::chrono::steady_clock::now();
+  }
+
+  void enqueue_period(cudaStream_t s) override {
+    enqueue_check(s);
+    for (int i = 1; i < P; ++i) enqueue_normal(s);
+    ck(cudaMemcpyAsync(h_st, st, sizeof(Scal), cudaMemcpyDeviceToHost, s), "state copy");
+  }
+
+  const Scal& host_state() const override { return *h_st; }
 
   void set_tolerances(const sipo_tolerances* t) override {
     const int p = t->check_every > 0 ? t->check_every : 64;
@@ -588,6 +621,15 @@ struct Solver final : SolverBase {
       bp_nv = tol.tile_cfg;
       return;
     }
+    const TileKey key{nx, ny, nz, na, nd, tol.storage, psf ? 1 : 0};
+    {
+      std::lock_guard<std::mutex> lock(g_tile_mutex);
+      auto it = g_tile_cache.find(key);
+      if (it != g_tile_cache.end()) {
+        bp_nv = it->second;
+        return;
+      }
+    }
     float best = 1e30f;
     int best_tile = 0;
     cudaEvent_t ev[7];
@@ -607,6 +649,8 @@ struct Solver final : SolverBase {
     }
     for (auto& e : ev) cudaEventDestroy(e);
     bp_nv = best_tile;
+    std::lock_guard<std::mutex> lock(g_tile_mutex);
+    g_tile_cache[key] = best_tile;
   }
 
   void enqueue_psf_q(const S* src, cudaStream_t s) { psf3<S, S>(src, kq, t1, t2, -1, s); }
@@ -1019,33 +1063,61 @@ int sipo_solve(sipo_ctx* ctx, void* y_out, int y_location, sipo_result* res) {
 int sipo_solve_batched(sipo_ctx** ctxs, int n, void** y_outs, int y_location, sipo_result* results) {
   SIPO_TRY
   if (!ctxs || n < 0 || (n > 0 && !results)) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
+  if (n == 0) return SIPO_OK;
   std::vector<sipo::SolverBase*> s(n);
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i]) sipo::fail(SIPO_ERR_INVALID_ARG, "null context");
     s[i] = ctxs[i]->c.s.get();
-    s[i]->begin_solve();
+    for (int j = 0; j < i; ++j)
+      if (s[j] == s[i]) sipo::fail(SIPO_ERR_INVALID_ARG, "a context appears twice in the batch");
   }
-  std::vector<long long> k(n, 0);
-  std::vector<char> active(n, 1);
-  int left = n;
-  while (left > 0) {
+  for (auto* x : s) x->init_for_batch();
+  // One graph per check period of the whole batch: every context's period is
+  // a branch forked from, and joined back into, a master stream.
+  cudaStream_t master = nullptr;
+  sipo::ck(cudaStreamCreateWithFlags(&master, cudaStreamNonBlocking), "stream");
+  std::vector<cudaEvent_t> ev(n + 1, nullptr);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  auto cleanup = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto e : ev)
+      if (e) cudaEventDestroy(e);
+    if (master) cudaStreamDestroy(master);
+  };
+  try {
+    for (auto& e : ev) sipo::ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    sipo::ck(cudaStreamBeginCapture(master, cudaStreamCaptureModeThreadLocal), "begin capture");
+    sipo::ck(cudaEventRecord(ev[n], master), "fork");
     for (int i = 0; i < n; ++i) {
-      if (!active[i]) continue;
-      const long long m = std::min(s[i]->period(), s[i]->max_iter() - k[i]);
-      if (m <= 0) continue;
-      s[i]->launch_block(m);
-      k[i] += m;
-      s[i]->request_done();
+      cudaStream_t si = s[i]->strm();
+      sipo::ck(cudaStreamWaitEvent(si, ev[n], 0), "fork wait");
+      s[i]->enqueue_period(si);
+      sipo::ck(cudaEventRecord(ev[i], si), "join");
+      sipo::ck(cudaStreamWaitEvent(master, ev[i], 0), "join wait");
     }
-    for (int i = 0; i < n; ++i) {
-      if (!active[i]) continue;
-      const bool done = s[i]->done_flag();
-      if (done || k[i] >= s[i]->max_iter()) {
-        active[i] = 0;
-        --left;
-      }
+    sipo::ck(cudaStreamEndCapture(master, &graph), "end capture");
+    sipo::ck(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
+    size_t nodes = 0;
+    sipo::ck(cudaGraphGetNodes(graph, nullptr, &nodes), "graph nodes");
+    // iteration limits round up to whole check periods; a context whose limit
+    // is reached stops at the check that opens its next period
+    long long max_periods = 0;
+    for (auto* x : s) max_periods = std::max(max_periods, (x->max_iter() + x->period() - 1) / x->period() + 1);
+    for (long long p = 0; p < max_periods; ++p) {
+      sipo::ck(cudaGraphLaunch(exec, master), "graph launch");
+      sipo::g_launches += (long long)nodes;
+      sipo::ck(cudaStreamSynchronize(master), "batch period");
+      bool all = true;
+      for (auto* x : s) all = all && x->host_state().done != 0;
+      if (all) break;
     }
+  } catch (...) {
+    cleanup();
+    throw;
   }
+  cleanup();
   for (int i = 0; i < n; ++i) s[i]->finish_solve(y_outs ? y_outs[i] : nullptr, y_location, &results[i]);
   return SIPO_OK;
   SIPO_CATCH

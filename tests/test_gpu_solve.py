@@ -152,3 +152,21 @@ def test_csg_case2_fp32_certificate_and_bf16(sipo):
     r16 = sipo.sipo_solve(ctx16)
     assert r16["status"] in (sipo.SIPO_OPTIMAL, sipo.SIPO_ITER_LIMIT)
     assert abs(r16["pobj"] - ref["obj"]) <= 2e-2 * abs(ref["obj"])
+
+
+def test_batched_solve_matches_individual_solves(sipo):
+    """One graph per period for the whole batch gives the same iterates as solving
+    each context alone (same kernels, deterministic reductions)."""
+    specs = TINY + [(2, dict(inhibit_ratio=0.3))]
+    single, ctxs = [], []
+    for case, extra in specs:
+        lp, ops, geo, tgt, cp = _tiny(case, extra)
+        tol = dict(storage=sipo.SIPO_F64, kkt_tol=1e-9, max_iter=64 * 400)
+        single.append(sipo.sipo_solve(sipo.sipo_create(geo, tgt, cp, tol)))
+        ctxs.append(sipo.sipo_create(geo, tgt, cp, tol))
+    batched = sipo.sipo_solve_batched(ctxs)
+    for a, b in zip(single, batched):
+        assert a["status"] == b["status"]
+        assert a["iters"] == b["iters"]
+        assert a["pobj"] == b["pobj"] and a["kkt"] == b["kkt"]
+    assert batched[-1]["status"] == sipo.SIPO_PRIMAL_INFEASIBLE
