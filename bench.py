@@ -216,14 +216,16 @@ def needed_units(sipo, ctx, wl):
 def tap_counts(wl, need, act_col):
     """Interpolation taps one launch of each fused kernel applies (per z value
     times nz): the backprojector's in-range taps of the needed columns, and the
-    projector's non-zero taps into the active (angle, bin) columns."""
+    projector's non-zero taps from the needed columns into the active (angle,
+    bin) columns.  Both kernels skip columns outside `need` (the input of the
+    projector, the dual combination, is zero there), so neither count includes
+    them."""
     n, nd = wl.n, wl.n_det
     c = np.arange(n) - (n - 1) / 2.0
     Y, X = np.meshgrid(c, c, indexing="ij")
     inside = np.ones((n, n), bool) if wl.vial_radius <= 0 else (X * X + Y * Y <= wl.vial_radius ** 2)
     bp_mask = need & inside
     xs_b, ys_b = X[bp_mask], Y[bp_mask]
-    xs_f, ys_f = X[inside], Y[inside]
     off = (nd - 1) / 2.0
     bp = fp = 0
     for k, th in enumerate(wl.angles):
@@ -231,8 +233,7 @@ def tap_counts(wl, need, act_col):
         u = xs_b * cth + ys_b * sth + off
         i0 = np.floor(u)
         bp += int(np.count_nonzero((i0 >= 0) & (i0 < nd)) + np.count_nonzero((i0 + 1 >= 0) & (i0 + 1 < nd)))
-        u = xs_f * cth + ys_f * sth + off
-        i0 = np.floor(u).astype(np.int64)
+        i0 = i0.astype(np.int64)
         w = u - i0
         hits = np.zeros(nd + 2, np.int64)
         ok = (i0 >= 0) & (i0 < nd)

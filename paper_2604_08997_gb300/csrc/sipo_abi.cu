@@ -108,8 +108,8 @@ struct Solver final : SolverBase {
   sipo_tolerances tol;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  bool vec = false;
-  int zl = 1;
+  int zl = 1;  // z values per lane of the operator kernels (z_lanes)
+  int ze = 1;  // z values per thread of the element-wise kernels (G or 1)
   int P = 64;
   bool psf = false;
   int bp_nv = 0;     // backprojector tile table entry
@@ -176,9 +176,8 @@ struct Solver final : SolverBase {
     cp = *c;
     tol = *t;
     P = tol.check_every > 0 ? tol.check_every : 64;
-    constexpr int ZLV = vec_zl<C>();
-    vec = (nz % ZLV) == 0;
-    zl = vec ? ZLV : 1;
+    zl = z_lanes<C>(nz);
+    ze = zl > 1 ? z_group<C>() : 1;
     if (s) {
       stream = s;
     } else {
@@ -531,7 +530,7 @@ struct Solver final : SolverBase {
       k_convert<float, C><<<gv, kThreads, 0, stream>>>(fT, t1, (long long)V);
       src = t1;
     }
-    launch_project<C, C, C, kFpStore, C>(g, src, Bufs<C, C>{}, gp, nullptr, vec, stream);
+    launch_project<C, C, C, kFpStore, C>(g, src, Bufs<C, C>{}, gp, nullptr, zl, stream);
     const int gs = grid_for((long long)SN);
     k_mask<C><<<gs, kThreads, 0, stream>>>(gp, mask, g0, (long long)SN);
     k_act_cols<<<grid_for((long long)na * nd), kThreads, 0, stream>>>(mask, act_col, (long long)na * nd, nz);
@@ -540,17 +539,17 @@ struct Solver final : SolverBase {
     if (psf) {
       psf3<C, C>(t1, t2, t3, braw, -1, stream);
       ck(cudaMemsetAsync(braw, 0, V * sizeof(C), stream), "memset");
-      launch_project<C, C, C, kFpStore, C>(g, t2, Bufs<C, C>{}, col, nullptr, vec, stream);
+      launch_project<C, C, C, kFpStore, C>(g, t2, Bufs<C, C>{}, col, nullptr, zl, stream);
     } else {
-      launch_project<C, C, C, kFpStore, C>(g, t1, Bufs<C, C>{}, col, nullptr, vec, stream);
+      launch_project<C, C, C, kFpStore, C>(g, t1, Bufs<C, C>{}, col, nullptr, zl, stream);
     }
     k_apply_mask<C><<<gs, kThreads, 0, stream>>>(col, mask, (long long)SN);
     // row abs-sums of A^T over active rays: A^T 1_act = K P^T 1_act
     if (psf) {
-      launch_backproject<C, C, C, kBpStore, C>(g, g0, Bufs<C, C>{}, t1, nullptr, vec, stream);
+      launch_backproject<C, C, C, kBpStore, C>(g, g0, Bufs<C, C>{}, t1, nullptr, zl, stream);
       psf3<C, C>(t1, row, t2, t3, -1, stream);
     } else {
-      launch_backproject<C, C, C, kBpStore, C>(g, g0, Bufs<C, C>{}, row, nullptr, vec, stream);
+      launch_backproject<C, C, C, kBpStore, C>(g, g0, Bufs<C, C>{}, row, nullptr, zl, stream);
     }
     (void)B;
     // setup sums
@@ -658,7 +657,7 @@ struct Solver final : SolverBase {
   void enqueue_normal(cudaStream_t s, cudaEvent_t* ev = nullptr) {
     const Geo<C> g = geo();
     const Bufs<S, C> B = bufs();
-    const long long nvv = (long long)(V / zl);
+    const long long nvv = (long long)(V / ze);
     auto rec = [&](int i) {
       if (ev) ck(cudaEventRecord(ev[i], s), "event");
     };
@@ -668,18 +667,18 @@ struct Solver final : SolverBase {
     rec(1);
     if (psf) enqueue_psf_q(q, s);
     rec(2);
-    launch_project<S, S, C, kFpPrimal, C>(g, psf ? kq : q, B, (C*)nullptr, act_col, vec, s, nbits, rspan);
+    launch_project<S, S, C, kFpPrimal, C>(g, psf ? kq : q, B, (C*)nullptr, act_col, zl, s, nbits, rspan);
     count(1);
     rec(3);
     if (psf) {
-      launch_backproject<S, S, C, kBpStore, C>(g, ybar, B, braw, need, vec, s, bp_nv);
+      launch_backproject<S, S, C, kBpStore, C>(g, ybar, B, braw, need, zl, s, bp_nv);
       count(1);
       rec(4);
       psf3<C, C>(braw, t3, t1, t2, -1, s);
       rec(5);
       dual_launch<false>(B, t3, nvv, s);
     } else {
-      launch_backproject<S, S, C, kBpDual, C>(g, ybar, B, (C*)nullptr, need, vec, s, bp_nv);
+      launch_backproject<S, S, C, kBpDual, C>(g, ybar, B, (C*)nullptr, need, zl, s, bp_nv);
       count(1);
       rec(4);
       rec(5);
@@ -689,8 +688,8 @@ struct Solver final : SolverBase {
 
   template <bool CHECK>
   void dual_launch(const Bufs<S, C>& B, const C* dbar, long long nvv, cudaStream_t s) {
-    if (vec)
-      k_dual<S, C, vec_zl<C>(), CHECK><<<kRedBlocks, kThreads, 0, s>>>(B, dbar, nvv);
+    if (ze > 1)
+      k_dual<S, C, z_group<C>(), CHECK><<<kRedBlocks, kThreads, 0, s>>>(B, dbar, nvv);
     else
       k_dual<S, C, 1, CHECK><<<kRedBlocks, kThreads, 0, s>>>(B, dbar, nvv);
     count(1);
@@ -699,29 +698,29 @@ struct Solver final : SolverBase {
   void enqueue_check(cudaStream_t s) {
     const Geo<C> g = geo();
     const Bufs<S, C> B = bufs();
-    const long long nvv = (long long)(V / zl), nvs = (long long)(SN / zl);
+    const long long nvv = (long long)(V / ze), nvs = (long long)(SN / ze);
     k_scalar_step<true><<<1, kThreads, 0, s>>>(st, part);
     count(1);
     if (psf) enqueue_psf_q(q, s);
-    launch_project<S, S, C, kFpPrimalCheck, C>(g, psf ? kq : q, B, (C*)nullptr, act_col, vec, s, nbits, rspan);
+    launch_project<S, S, C, kFpPrimalCheck, C>(g, psf ? kq : q, B, (C*)nullptr, act_col, zl, s, nbits, rspan);
     count(1);
     if (psf) {
-      launch_backproject<S, S, C, kBpStore, C>(g, ybar, B, braw, need, vec, s, bp_nv);
+      launch_backproject<S, S, C, kBpStore, C>(g, ybar, B, braw, need, zl, s, bp_nv);
       count(1);
       psf3<C, C>(braw, t3, t1, t2, -1, s);
       dual_launch<true>(B, t3, nvv, s);
       enqueue_psf_q(qp, s);
     } else {
-      launch_backproject<S, S, C, kBpDualCheck, C>(g, ybar, B, (C*)nullptr, need, vec, s, bp_nv);
+      launch_backproject<S, S, C, kBpDualCheck, C>(g, ybar, B, (C*)nullptr, need, zl, s, bp_nv);
       count(1);
     }
-    launch_project<S, S, C, kFpResid, C>(g, psf ? kq : qp, B, (C*)nullptr, act_col, vec, s, nbits, rspan);
+    launch_project<S, S, C, kFpResid, C>(g, psf ? kq : qp, B, (C*)nullptr, act_col, zl, s, nbits, rspan);
     count(1);
     k_scalar_check<<<1, kThreads, 0, s>>>(st, part);
     count(1);
-    if (vec) {
-      k_blend_sino<S, C, vec_zl<C>()><<<grid_for(nvs), kThreads, 0, s>>>(B, nvs);
-      k_blend_vol<S, C, vec_zl<C>()><<<kRedBlocks, kThreads, 0, s>>>(B, nvv);
+    if (ze > 1) {
+      k_blend_sino<S, C, z_group<C>()><<<grid_for(nvs), kThreads, 0, s>>>(B, nvs);
+      k_blend_vol<S, C, z_group<C>()><<<kRedBlocks, kThreads, 0, s>>>(B, nvv);
     } else {
       k_blend_sino<S, C, 1><<<grid_for(nvs), kThreads, 0, s>>>(B, nvs);
       k_blend_vol<S, C, 1><<<kRedBlocks, kThreads, 0, s>>>(B, nvv);
@@ -842,7 +841,7 @@ struct Solver final : SolverBase {
       psf3<C, C>(src, t3, t1, t2, -1, s);
       src = t3;
     }
-    launch_project<C, C, C, kFpStore, C>(g, src, Bufs<C, C>{}, static_cast<C*>(sino), nullptr, vec, s);
+    launch_project<C, C, C, kFpStore, C>(g, src, Bufs<C, C>{}, static_cast<C*>(sino), nullptr, zl, s);
     count(1);
     ck(cudaGetLastError(), "project");
   }
@@ -851,11 +850,11 @@ struct Solver final : SolverBase {
     const Geo<C> g = geo();
     if (psf) {
       ensure_temps();
-      launch_backproject<C, C, C, kBpStore, C>(g, static_cast<const C*>(sino), Bufs<C, C>{}, t3, nullptr, vec, s);
+      launch_backproject<C, C, C, kBpStore, C>(g, static_cast<const C*>(sino), Bufs<C, C>{}, t3, nullptr, zl, s);
       psf3<C, C>(t3, static_cast<C*>(vol), t1, t2, -1, s);
     } else {
       launch_backproject<C, C, C, kBpStore, C>(g, static_cast<const C*>(sino), Bufs<C, C>{},
-                                               static_cast<C*>(vol), nullptr, vec, s);
+                                               static_cast<C*>(vol), nullptr, zl, s);
     }
     count(1);
     ck(cudaGetLastError(), "backproject");
@@ -878,7 +877,7 @@ struct Solver final : SolverBase {
     double* pg = dalloc_part();
     // b = P_mu^T sino, recomputed (not stored by the forward pass)
     launch_backproject<C, C, C, kBpStore, C>(geo(), static_cast<const C*>(sino), Bufs<C, C>{}, tvol, nullptr,
-                                             vec, s);
+                                             zl, s);
     count(1);
     for (int a = 0; a < 3; ++a) {
       grad[a] = 0.0;

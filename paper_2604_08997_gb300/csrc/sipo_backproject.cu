@@ -20,17 +20,19 @@ static void launch_bp_zl(const Geo<C>& g, const SI* sino, const Bufs<S, C>& b, O
 
 template <typename SI, typename S, typename C, int MODE, typename O>
 void launch_backproject(const Geo<C>& g, const SI* sino, const Bufs<S, C>& b, O* out,
-                        const uint8_t* need, bool vec, cudaStream_t stream, int tile) {
-  constexpr int ZLV = sizeof(SI) == 8 ? 4 : 8;
-  if (vec)
-    launch_bp_zl<SI, S, C, ZLV, MODE, O>(g, sino, b, out, need, stream, tile);
+                        const uint8_t* need, int zl, cudaStream_t stream, int tile) {
+  constexpr int G = z_group<C>();
+  if (zl == 2 * G)
+    launch_bp_zl<SI, S, C, 2 * G, MODE, O>(g, sino, b, out, need, stream, tile);
+  else if (zl == G)
+    launch_bp_zl<SI, S, C, G, MODE, O>(g, sino, b, out, need, stream, tile);
   else
     launch_bp_zl<SI, S, C, 1, MODE, O>(g, sino, b, out, need, stream, tile);
 }
 
 #define SIPO_BP(SI, S, C, M, O) \
   template void launch_backproject<SI, S, C, M, O>(const Geo<C>&, const SI*, const Bufs<S, C>&, \
-                                                    O*, const uint8_t*, bool, cudaStream_t, int);
+                                                    O*, const uint8_t*, int, cudaStream_t, int);
 #define SIPO_BP_SOLVER(S, C)       \
   SIPO_BP(S, S, C, kBpDual, C)     \
   SIPO_BP(S, S, C, kBpDualCheck, C) \

@@ -1,11 +1,11 @@
 // sipo_device.cuh -- device-side building blocks of the SiPO solver (sm_103a).
 //
 // Layouts (z = rotation axis, fastest): volume [ny][nx][nz], sinogram
-// [n_angles][n_det][nz].  Every kernel maps the 32 lanes of a warp onto
-// consecutive z and gives each lane ZL consecutive z values, so all geometry
-// (detector coordinate, interpolation weight, attenuation factor) is
-// warp-uniform and every sinogram / volume access is a coalesced 16-byte
-// vector load per lane.
+// [n_angles][n_det][nz].  Every operator kernel maps the 32 lanes of a warp
+// onto one z column segment of 32 * ZL values (ZL per lane, in 16-byte groups
+// interleaved across the lanes), so all geometry (detector coordinate,
+// interpolation weight, attenuation factor) is warp-uniform and every
+// sinogram / volume access is a fully coalesced vector load.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -41,66 +41,111 @@ template <typename S> struct Compute { using type = float; };
 template <> struct Compute<double> { using type = double; };
 
 // ------------------------------------------------- z-vector loads and stores
-// ZL consecutive elements starting at p.  When the vector is 16-byte sized it
-// is moved with 128-bit accesses (the host guarantees the alignment by only
-// choosing such ZL when nz is a multiple of the vector width).
-template <typename S, typename C, int ZL>
-__device__ __forceinline__ void load_z(const S* __restrict__ p, C (&v)[ZL]) {
-  constexpr int kBytes = int(sizeof(S)) * ZL;
-  if constexpr (kBytes % 16 == 0) {
-    const uint4* q = reinterpret_cast<const uint4*>(p);
+// A z-vector of ZL elements per lane is NG = ZL / G groups of G consecutive
+// elements, G = the number of compute elements in 16 bytes (4 floats, 2
+// doubles; 1 on the scalar path).  Group q of lane l sits at
+// p + q * 32 * G, where p = tile start + l * G: one access of the warp to a
+// group covers 32 * G consecutive elements, so each request uses every byte of
+// its sectors (16 bytes a lane for 4-byte data, 8 for bf16, 4 for labels).
+// The host picks ZL = G or 2G only when nz is a multiple of G (and of 64 G for
+// 2G), which keeps every group access aligned and inside its z column.
+template <typename C, int ZL>
+struct ZLayout {
+  static constexpr int kVec = 16 / int(sizeof(C));
+  static constexpr int G = ZL < kVec ? ZL : kVec;
+  static constexpr int NG = ZL / G;
+  static constexpr int kStride = 32 * G;  // elements between a lane's groups
+  static_assert(ZL % G == 0, "ZL must be a multiple of the group size");
+};
+
+// One group: G elements of storage type S at p.
+template <typename S, typename C, int G>
+__device__ __forceinline__ void load_group(const S* __restrict__ p, C* v) {
+  constexpr int kBytes = int(sizeof(S)) * G;
+  if constexpr (kBytes == 16) {
+    const uint4 r = __ldg(reinterpret_cast<const uint4*>(p));
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+    if constexpr (sizeof(S) == 4) {
 #pragma unroll
-    for (int i = 0; i < kBytes / 16; ++i) {
-      uint4 r = __ldg(q + i);
-      uint32_t w[4] = {r.x, r.y, r.z, r.w};
-      if constexpr (sizeof(S) == 4) {
+      for (int j = 0; j < 4; ++j) v[j] = __uint_as_float(w[j]);
+    } else if constexpr (sizeof(S) == 8) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) v[i * 4 + j] = __uint_as_float(w[j]);
-      } else if constexpr (sizeof(S) == 2) {
+      for (int j = 0; j < 2; ++j) v[j] = __hiloint2double(int(w[2 * j + 1]), int(w[2 * j]));
+    } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          v[i * 8 + 2 * j] = __uint_as_float(w[j] << 16);
-          v[i * 8 + 2 * j + 1] = __uint_as_float(w[j] & 0xffff0000u);
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-          v[i * 2 + j] = __hiloint2double(int(w[2 * j + 1]), int(w[2 * j]));
+      for (int j = 0; j < 4; ++j) {
+        v[2 * j] = __uint_as_float(w[j] << 16);
+        v[2 * j + 1] = __uint_as_float(w[j] & 0xffff0000u);
       }
     }
+  } else if constexpr (kBytes == 8 && sizeof(S) == 2) {
+    const uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
+    v[0] = __uint_as_float(r.x << 16);
+    v[1] = __uint_as_float(r.x & 0xffff0000u);
+    v[2] = __uint_as_float(r.y << 16);
+    v[3] = __uint_as_float(r.y & 0xffff0000u);
   } else {
 #pragma unroll
-    for (int i = 0; i < ZL; ++i) v[i] = to_c(p[i]);
+    for (int i = 0; i < G; ++i) v[i] = to_c(p[i]);
   }
+}
+
+template <typename S, typename C, int G>
+__device__ __forceinline__ void store_group(S* __restrict__ p, const C* v) {
+  constexpr int kBytes = int(sizeof(S)) * G;
+  if constexpr (kBytes == 16 && sizeof(S) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (kBytes == 16 && sizeof(S) == 8) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  } else if constexpr (sizeof(S) == 2 && (G == 4 || G == 8)) {
+    uint32_t w[G / 2];
+#pragma unroll
+    for (int j = 0; j < G / 2; ++j) {
+      __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+      w[j] = *reinterpret_cast<uint32_t*>(&h);
+    }
+    if constexpr (G == 4) *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+    else *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < G; ++i) p[i] = from_c<S>(v[i]);
+  }
+}
+
+// The lane's z-vector whose first group starts at p (layout above).
+template <typename S, typename C, int ZL>
+__device__ __forceinline__ void load_z(const S* __restrict__ p, C (&v)[ZL]) {
+  using L = ZLayout<C, ZL>;
+#pragma unroll
+  for (int q = 0; q < L::NG; ++q) load_group<S, C, L::G>(p + q * L::kStride, v + q * L::G);
 }
 
 template <typename S, typename C, int ZL>
 __device__ __forceinline__ void store_z(S* __restrict__ p, const C (&v)[ZL]) {
-  constexpr int kBytes = int(sizeof(S)) * ZL;
-  if constexpr (kBytes % 16 == 0 && sizeof(S) == 4) {
-    float4* q = reinterpret_cast<float4*>(p);
+  using L = ZLayout<C, ZL>;
 #pragma unroll
-    for (int i = 0; i < ZL / 4; ++i)
-      q[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-  } else if constexpr (kBytes % 16 == 0 && sizeof(S) == 8) {
-    double2* q = reinterpret_cast<double2*>(p);
+  for (int q = 0; q < L::NG; ++q) store_group<S, C, L::G>(p + q * L::kStride, v + q * L::G);
+}
+
+// Labels (one byte each) of the lane's z-vector, same layout.
+template <typename C, int ZL>
+__device__ __forceinline__ void load_labels(const uint8_t* __restrict__ p, uint8_t (&lab)[ZL]) {
+  using L = ZLayout<C, ZL>;
 #pragma unroll
-    for (int i = 0; i < ZL / 2; ++i) q[i] = make_double2(v[2 * i], v[2 * i + 1]);
-  } else if constexpr (kBytes % 16 == 0 && sizeof(S) == 2) {
-    uint4* q = reinterpret_cast<uint4*>(p);
+  for (int q = 0; q < L::NG; ++q) {
+    const uint8_t* pq = p + q * L::kStride;
+    if constexpr (L::G == 4) {
+      const uint32_t r = __ldg(reinterpret_cast<const uint32_t*>(pq));
 #pragma unroll
-    for (int i = 0; i < ZL / 8; ++i) {
-      uint32_t w[4];
+      for (int j = 0; j < 4; ++j) lab[q * 4 + j] = (r >> (8 * j)) & 0xff;
+    } else if constexpr (L::G == 2) {
+      const uint32_t r = __ldg(reinterpret_cast<const unsigned short*>(pq));
+      lab[q * 2] = r & 0xff;
+      lab[q * 2 + 1] = (r >> 8) & 0xff;
+    } else {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        __nv_bfloat162 h = __floats2bfloat162_rn(v[8 * i + 2 * j], v[8 * i + 2 * j + 1]);
-        w[j] = *reinterpret_cast<uint32_t*>(&h);
-      }
-      q[i] = make_uint4(w[0], w[1], w[2], w[3]);
+      for (int j = 0; j < L::G; ++j) lab[q * L::G + j] = pq[j];
     }
-  } else {
-#pragma unroll
-    for (int i = 0; i < ZL; ++i) p[i] = from_c<S>(v[i]);
   }
 }
 

@@ -9,14 +9,14 @@
 
 namespace sipo {
 
-// vec selects the 16-byte vector z-path (needs nz % ZL == 0, ZL = 8 for
-// 4/2-byte elements and 4 for doubles) over the scalar path (ZL = 1).
+// zl: z values per lane (z_lanes<C>(nz) picks it): 2G or G, G = 16 bytes of
+// compute elements, for the vector paths, 1 for the scalar path.
 // nb: packed per-column flags of voxels whose input may be non-zero (rows ==
 // nullptr: every in-vial voxel); rspan: per-ray walked-axis span holding such
 // columns (nullptr: whole ray).
 template <typename SI, typename S, typename C, int MODE, typename O>
 void launch_project(const Geo<C>& g, const SI* vol, const Bufs<S, C>& b, O* out,
-                    const uint8_t* act_col, bool vec, cudaStream_t stream,
+                    const uint8_t* act_col, int zl, cudaStream_t stream,
                     const NeedBits& nb = NeedBits{}, const int2* rspan = nullptr);
 
 // Packs need[y][x] into the row-major and column-major bit arrays of NeedBits.
@@ -32,8 +32,17 @@ void launch_ray_spans(const Geo<C>& g, const uint8_t* need, int2* out, cudaStrea
 constexpr int kBpTiles = 3;
 template <typename SI, typename S, typename C, int MODE, typename O>
 void launch_backproject(const Geo<C>& g, const SI* sino, const Bufs<S, C>& b, O* out,
-                        const uint8_t* need, bool vec, cudaStream_t stream, int tile = 0);
+                        const uint8_t* need, int zl, cudaStream_t stream, int tile = 0);
 
-template <typename C> constexpr int vec_zl() { return sizeof(C) == 8 ? 4 : 8; }
+// Group size G of the z layout (elements of C in 16 bytes).
+template <typename C> constexpr int z_group() { return 16 / int(sizeof(C)); }
+
+// z values per lane for a z extent nz: two groups when a warp's 64 G values
+// tile nz exactly, one group when nz is a multiple of G (the last warp of a
+// column may then be partly idle, lane by lane), else the scalar path.
+template <typename C> inline int z_lanes(int nz) {
+  constexpr int G = z_group<C>();
+  return nz % (64 * G) == 0 ? 2 * G : (nz % G == 0 ? G : 1);
+}
 
 }  // namespace sipo

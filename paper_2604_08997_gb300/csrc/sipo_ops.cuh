@@ -8,9 +8,10 @@
 //
 // Projection (P, the exact transpose): gather form.  For each ray (angle, bin)
 // the kernel walks the dominant axis of the ray direction and, on each row or
-// column, evaluates the <= 5 voxels whose interpolation reaches the bin with
-// the very same arithmetic as the backprojector, so the weights agree bit for
-// bit.  No atomics; each output is written once.
+// column, evaluates the three candidate voxels whose interpolation can reach
+// the bin, with weights equal bit for bit to the backprojector's.  The lanes
+// evaluate 32 lines at once and the warp then streams the compacted taps.  No
+// atomics; each output is written once.
 //
 // Both kernels run a grid-stride loop over tiles on a fixed grid of
 // kRedBlocks blocks so that fused reductions have a fixed number of partials.
@@ -23,6 +24,62 @@ namespace sipo {
 enum FpMode : int { kFpStore = 0, kFpPrimal = 1, kFpPrimalCheck = 2, kFpResid = 3 };
 enum BpMode : int { kBpStore = 0, kBpDual = 1, kBpDualCheck = 2 };
 
+
+// --------------------------------------------------------------- projector
+// Smallest integer >= x without the conversion unit (via floor_split of -x),
+// as an int and as a float.
+__device__ __forceinline__ void ceil_split(float x, float& cf, int& ci) {
+  float f;
+  int i;
+  floor_split(-x, f, i);
+  cf = -f;
+  ci = -i;
+}
+__device__ __forceinline__ void ceil_split(double x, double& cf, int& ci) {
+  cf = ceil(x);
+  ci = int(cf);
+}
+__device__ __forceinline__ int ceil_int(float x) {
+  float f;
+  int i;
+  ceil_split(x, f, i);
+  return i;
+}
+__device__ __forceinline__ int ceil_int(double x) { return int(ceil(x)); }
+
+// Candidate window: the voxels whose detector coordinate on the walked row is
+// within 1 of bin j lie strictly inside (xc - h, xc + h), h = 1/|cos| <= sqrt 2
+// (exact arithmetic).  With the FP32 rounding of u and of xc (< 1e-4) the
+// widened window (xc - h - 1e-3, xc + h + 1e-3) is narrower than 3, so the
+// three integers from ceil(xc - h - 1e-3) contain every voxel with a non-zero
+// weight; each candidate's weight is then the backprojector's weight of the
+// same u, so P stays the transpose.
+constexpr float kCandEps = 1e-3f;
+
+// Weight of the voxel with detector coordinate u in bin j (jm = j - 1).  The
+// backprojector gives bin floor(u) the weight 1 - (u - floor u) and bin
+// floor(u) + 1 the weight u - floor u.
+//   FAST = false: that rule, literally.
+//   FAST = true (j >= 2): max(0, 1 - |u - j|), the same float bit for bit.
+// For |u - j| < 1 and j >= 2, u lies in [j/2, 2j], so u - j is exact
+// (Sterbenz).  If u >= j, floor u = j and both forms round 1 - (u - j).  If
+// u < j, floor u = j - 1 and the exact value of 1 - (j - u) is u - (j - 1),
+// which the backprojector computes exactly, so it is representable and the
+// rounding of 1 - (j - u) returns it.  If |u - j| >= 1 the rounded |u - j| is
+// >= 1 too and the weight is 0, as it is in the backprojector.
+template <bool FAST, typename C>
+__device__ __forceinline__ C tap_weight(C u, C jf, C jm) {
+  if constexpr (FAST) {
+    const C t = C(1) - fabs(u - jf);
+    return t > C(0) ? t : C(0);
+  } else {
+    C flo;
+    int i0;
+    floor_split(u, flo, i0);
+    const C wv = u - flo;
+    return (flo == jf) ? (C(1) - wv) : ((flo == jm) ? wv : C(0));
+  }
+}
 
 // Column flags packed as bits for the projector's candidate test.  rows: for
 // each y, bit (x + kNbPad) of word array [y][words] says whether column (y, x)
@@ -44,30 +101,134 @@ struct NeedBits {
   }
 };
 
-// --------------------------------------------------------------- projector
-// Smallest integer >= x without the conversion unit (via floor_split of -x).
-__device__ __forceinline__ int ceil_int(float x) {
-  float f;
-  int i;
-  floor_split(-x, f, i);
-  return -i;
-}
-__device__ __forceinline__ int ceil_int(double x) { return int(ceil(x)); }
+// One ray (angle k, bin j) of the projector, walked along y when
+// |cos| >= |sin| (ROWS: on row iy the bin is reached from x near
+// (j - inner) / cos) and along x otherwise (on column ix from y near
+// (j - off - x cos) / sin); three candidates per line from the window start.
+//
+// The warp handles the ray's lines 32 at a time: lane l evaluates line
+// r0 + l (window, flags, weights), the non-zero taps of the 32 lines are
+// compacted in line order into the warp's tap list in shared memory (column
+// index and weight), and the whole warp then streams that list, four taps per
+// step, each tap a coalesced load of the warp's z segment of one voxel column
+// and ZL fused multiply-adds.  Taps are applied in the order of the serial
+// walk (line by line, candidates in increasing order), so the sums do not
+// depend on how lines are split over lanes.
+constexpr int kTapList = 96;  // 32 lines x 3 candidates
 
-// Candidate window: the voxels whose detector coordinate on the walked row is
-// within 1 of bin j lie strictly inside (xc - h, xc + h), h = 1/|cos| <= sqrt 2
-// (exact arithmetic).  With the FP32 rounding of u and of xc (< 1e-4) the
-// widened window (xc - h - 1e-3, xc + h + 1e-3) is narrower than 3, so the
-// three integers from ceil(xc - h - 1e-3) contain every voxel with a non-zero
-// weight; each candidate's weight is then computed exactly as the
-// backprojector computes it (same u, same floor), so P stays the transpose.
-constexpr float kCandEps = 1e-3f;
+template <typename C>
+struct TapList {
+  int col[kTapList];
+  C w[kTapList];
+};
+
+template <bool ROWS, bool FAST, typename C>
+__device__ __forceinline__ int fp_line_taps(const Geo<C>& g, const NeedBits& nb, bool use_bits, int k, C jf,
+                                            C c, C s, C inv_a, C h, int line, int (&col)[3], C (&wt)[3]) {
+  const C jm = jf - C(1);
+  C cf;
+  int i0;
+  C inner = C(0), xf = C(0);
+  if constexpr (ROWS) {
+    inner = geo_inner(C(line) - g.cy, s, g.off);
+    ceil_split((jf - inner) * inv_a + g.cx - h, cf, i0);
+  } else {
+    xf = C(line) - g.cx;
+    ceil_split((jf - g.off - xf * c) * inv_a + g.cy - h, cf, i0);
+  }
+  unsigned okm;
+  if (use_bits) {
+    okm = nb.window(ROWS ? nb.rows : nb.cols, line, i0);
+  } else {
+    const int2 sp = ROWS ? g.xspan[line] : g.yspan[line];
+    okm = 0u;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) okm |= unsigned(i0 + m >= sp.x && i0 + m <= sp.y) << m;
+  }
+  int nt = 0;
+  if (okm == 0u) return 0;
+  const C f0 = ROWS ? cf - g.cx : cf - g.cy;
+  C eline = C(1);
+  if (g.ex) eline = ROWS ? g.ey[(size_t)k * g.ny + line] : g.ex[(size_t)k * g.nx + line];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const C u = ROWS ? geo_outer(f0 + C(m), c, inner) : geo_outer(xf, c, geo_inner(f0 + C(m), s, g.off));
+    C t = tap_weight<FAST>(u, jf, jm);
+    t = ((okm >> m) & 1u) ? t : C(0);
+    const int ix = ROWS ? i0 + m : line, iy = ROWS ? line : i0 + m;
+    if (g.ex && t != C(0))
+      t = ROWS ? t * (g.ex[(size_t)k * g.nx + ix] * eline) : t * (eline * g.ey[(size_t)k * g.ny + iy]);
+    col[m] = iy * g.nx + ix;
+    wt[m] = t;
+    nt += t != C(0);
+  }
+  return nt;
+}
+
+template <bool ROWS, bool FAST, typename SI, typename C, int ZL>
+__device__ __forceinline__ void fp_walk(const Geo<C>& g, const SI* vz, const NeedBits& nb, bool use_bits, int k,
+                                        C jf, C c, C s, int lo, int hi, TapList<C>& tl, C (&acc)[ZL]) {
+  const int lane = threadIdx.x & 31;
+  const C a = ROWS ? c : s;
+  const C inv_a = C(1) / a, h = C(1) / fabs(a) + C(kCandEps);
+  for (int r0 = lo; r0 <= hi; r0 += 32) {
+    int col[3] = {0, 0, 0};
+    C wt[3] = {C(0), C(0), C(0)};
+    int nt = 0;
+    if (r0 + lane <= hi)
+      nt = fp_line_taps<ROWS, FAST, C>(g, nb, use_bits, k, jf, c, s, inv_a, h, r0 + lane, col, wt);
+    // exclusive prefix of the tap counts over the lanes = list positions
+    int incl = nt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) continue;
+    int pos = incl - nt;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      if (wt[m] != C(0)) {
+        tl.col[pos] = col[m];
+        tl.w[pos] = wt[m];
+        ++pos;
+      }
+    }
+    __syncwarp();
+    int t = 0;
+    for (; t + 4 <= total; t += 4) {
+      C v[4][ZL];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) load_z<SI, C, ZL>(vz + (size_t)tl.col[t + u] * g.nz, v[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const C w = tl.w[t + u];
+#pragma unroll
+        for (int i = 0; i < ZL; ++i) acc[i] = fma(w, v[u][i], acc[i]);
+      }
+    }
+    for (; t < total; ++t) {
+      C v[ZL];
+      load_z<SI, C, ZL>(vz + (size_t)tl.col[t] * g.nz, v);
+      const C w = tl.w[t];
+#pragma unroll
+      for (int i = 0; i < ZL; ++i) acc[i] = fma(w, v[i], acc[i]);
+    }
+    __syncwarp();
+  }
+}
 
 // SI: element type read from `vol`; O: element type written by kFpStore.
 // act_col: per (angle, bin) flag of rays with an active z (solver modes skip
-// the others); need: per (y, x) column flag of voxels whose input can be
-// non-zero (the solver's dual combination vanishes on exterior columns), or
-// nullptr to gather every in-vial voxel.
+// the others); nb: packed per-column flags of voxels whose input can be
+// non-zero (the solver's dual combination vanishes on the other columns), or
+// rows == nullptr to gather every in-vial voxel; rspan: per-ray walked span
+// meeting such columns (nullptr: the whole ray).
+//
+// Tiles (angle, 8 consecutive bins, z segment) are numbered with the angle
+// fastest, so the grid-stride loop gives every block a mix of central bins
+// (long rays) and outer bins (short rays) and the blocks finish together.
 template <typename SI, typename S, typename C, int ZL, int MODE, typename O>
 __global__ void __launch_bounds__(kThreads)
 k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __restrict__ out,
@@ -83,23 +244,27 @@ k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __r
   double red[NR > 0 ? NR : 1] = {};
   StepScalars<C> sc{};
   if (MODE == kFpPrimal || MODE == kFpPrimalCheck) sc = read_scalars<C>(b.st);
+  __shared__ __align__(16) TapList<C> taps[kWarps];
 
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int tz = int(t % nzc);
-    const long long t1 = t / nzc;
-    const int jb = int(t1 % njb);
-    const int k = int(t1 / njb);
+    const int k = int(t % g.na);
+    const long long t1 = t / g.na;
+    const int tz = int(t1 % nzc);
+    const int jb = int(t1 / nzc);
     const int j = jb * kWarps + warp;
-    const int z0 = tz * ZC + lane * ZL;
+    const int z0 = tz * ZC + lane * ZLayout<C, ZL>::G;
     if (j >= g.nd) continue;
     if (MODE != kFpStore && act_col != nullptr && !act_col[(size_t)k * g.nd + j]) continue;
     const C esj = g.es ? g.es[(size_t)k * g.nd + j] : C(1);
     C acc[ZL];
 #pragma unroll
     for (int i = 0; i < ZL; ++i) acc[i] = C(0);
-    if (esj != C(0) && z0 < g.nz) {
+    // The whole warp walks the ray (the walk uses warp shuffles); a lane past
+    // the end of a ragged z column reads the column's first group instead and
+    // never stores its result.
+    if (esj != C(0)) {
       const C c = g.cs[2 * k], s = g.cs[2 * k + 1];
-      const C jf = C(j), jm = C(j - 1);
+      const C jf = C(j);
       const C sj = jf - g.off;
       C H = C(0);
       if (g.r2i >= 0) {
@@ -109,114 +274,28 @@ k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __r
         H = R * R - a * a;
         H = (H > C(0) ? sqrt(H) : C(0)) + C(1.5);
       }
-      const SI* vz = vol + z0;
-      if (fabs(c) >= fabs(s)) {
-        // walk rows iy; on each row the bin is reached from x near (j - inner) / cos
-        int lo = 0, hi = g.ny - 1;
-        if (g.r2i >= 0) {
-          const C yc = sj * s, hy = fabs(c) * H + C(1);
-          lo = max(0, -ceil_int(-(yc - hy + g.cy)));
-          hi = min(g.ny - 1, ceil_int(yc + hy + g.cy));
-        }
-        if (rspan) {
-          const int2 r = rspan[(size_t)k * g.nd + j];
-          lo = max(lo, r.x);
-          hi = min(hi, r.y);
-        }
-        const C inv_c = C(1) / c, h = C(1) / fabs(c) + C(kCandEps);
-        C yf = C(lo) - g.cy;
-        for (int iy = lo; iy <= hi; ++iy, yf += C(1)) {
-          const C inner = geo_inner(yf, s, g.off);
-          const C ixc = (jf - inner) * inv_c + g.cx;
-          const int ix0 = ceil_int(ixc - h);
-          unsigned okm;
-          if (use_bits) {
-            okm = nb.window(nb.rows, iy, ix0);
-          } else {
-            const int2 sp = g.xspan[iy];
-            okm = 0u;
-#pragma unroll
-            for (int m = 0; m < 3; ++m) okm |= unsigned(ix0 + m >= sp.x && ix0 + m <= sp.y) << m;
-          }
-          if (okm == 0u) continue;
-          const C xf0 = C(ix0) - g.cx;
-          C wt[3];
-#pragma unroll
-          for (int m = 0; m < 3; ++m) {
-            const C u = geo_outer(xf0 + C(m), c, inner);
-            C flo;
-            int i0;
-            floor_split(u, flo, i0);
-            const C wv = u - flo;
-            const C t = (flo == jf) ? (C(1) - wv) : ((flo == jm) ? wv : C(0));
-            wt[m] = ((okm >> m) & 1u) ? t : C(0);
-          }
-          const C eyv = g.ex ? g.ey[(size_t)k * g.ny + iy] : C(1);
-          const SI* vrow = vz + ((size_t)iy * g.nx) * g.nz;
-#pragma unroll
-          for (int m = 0; m < 3; ++m) {
-            if (wt[m] == C(0)) continue;
-            const int ix = ix0 + m;
-            const C w = g.ex ? wt[m] * (g.ex[(size_t)k * g.nx + ix] * eyv) : wt[m];
-            C v[ZL];
-            load_z<SI, C, ZL>(vrow + (size_t)ix * g.nz, v);
-#pragma unroll
-            for (int i = 0; i < ZL; ++i) acc[i] = fma(w, v[i], acc[i]);
-          }
-        }
+      const SI* vz = vol + (z0 < g.nz ? z0 : 0);
+      const bool rows = fabs(c) >= fabs(s);
+      int lo = 0, hi = (rows ? g.ny : g.nx) - 1;
+      if (g.r2i >= 0) {
+        // walked-axis extent of the ray's chord through the vial (+1 margin)
+        const C mid = rows ? sj * s + g.cy : sj * c + g.cx;
+        const C half = (rows ? fabs(c) : fabs(s)) * H + C(1);
+        lo = max(0, -ceil_int(-(mid - half)));
+        hi = min(hi, ceil_int(mid + half));
+      }
+      if (rspan) {
+        const int2 r = rspan[(size_t)k * g.nd + j];
+        lo = max(lo, r.x);
+        hi = min(hi, r.y);
+      }
+      TapList<C>& tl = taps[warp];
+      if (rows) {
+        if (j >= 2) fp_walk<true, true, SI, C, ZL>(g, vz, nb, use_bits, k, jf, c, s, lo, hi, tl, acc);
+        else fp_walk<true, false, SI, C, ZL>(g, vz, nb, use_bits, k, jf, c, s, lo, hi, tl, acc);
       } else {
-        // walk columns ix; on each column the bin is reached from y near (j - off - x cos) / sin
-        int lo = 0, hi = g.nx - 1;
-        if (g.r2i >= 0) {
-          const C xc = sj * c, hx = fabs(s) * H + C(1);
-          lo = max(0, -ceil_int(-(xc - hx + g.cx)));
-          hi = min(g.nx - 1, ceil_int(xc + hx + g.cx));
-        }
-        if (rspan) {
-          const int2 r = rspan[(size_t)k * g.nd + j];
-          lo = max(lo, r.x);
-          hi = min(hi, r.y);
-        }
-        const C inv_s = C(1) / s, h = C(1) / fabs(s) + C(kCandEps);
-        C xf = C(lo) - g.cx;
-        for (int ix = lo; ix <= hi; ++ix, xf += C(1)) {
-          const C iyc = (jf - g.off - xf * c) * inv_s + g.cy;
-          const int iy0 = ceil_int(iyc - h);
-          unsigned okm;
-          if (use_bits) {
-            okm = nb.window(nb.cols, ix, iy0);
-          } else {
-            const int2 sp = g.yspan[ix];
-            okm = 0u;
-#pragma unroll
-            for (int m = 0; m < 3; ++m) okm |= unsigned(iy0 + m >= sp.x && iy0 + m <= sp.y) << m;
-          }
-          if (okm == 0u) continue;
-          const C yf0 = C(iy0) - g.cy;
-          C wt[3];
-#pragma unroll
-          for (int m = 0; m < 3; ++m) {
-            const C u = geo_outer(xf, c, geo_inner(yf0 + C(m), s, g.off));
-            C flo;
-            int i0;
-            floor_split(u, flo, i0);
-            const C wv = u - flo;
-            const C t = (flo == jf) ? (C(1) - wv) : ((flo == jm) ? wv : C(0));
-            wt[m] = ((okm >> m) & 1u) ? t : C(0);
-          }
-          const C exv = g.ex ? g.ex[(size_t)k * g.nx + ix] : C(1);
-          const SI* vcol = vz + (size_t)ix * g.nz;
-#pragma unroll
-          for (int m = 0; m < 3; ++m) {
-            if (wt[m] == C(0)) continue;
-            const int iy = iy0 + m;
-            const C w = g.ex ? wt[m] * (exv * g.ey[(size_t)k * g.ny + iy]) : wt[m];
-            C v[ZL];
-            load_z<SI, C, ZL>(vcol + (size_t)iy * g.nx * g.nz, v);
-#pragma unroll
-            for (int i = 0; i < ZL; ++i) acc[i] = fma(w, v[i], acc[i]);
-          }
-        }
+        if (j >= 2) fp_walk<false, true, SI, C, ZL>(g, vz, nb, use_bits, k, jf, c, s, lo, hi, tl, acc);
+        else fp_walk<false, false, SI, C, ZL>(g, vz, nb, use_bits, k, jf, c, s, lo, hi, tl, acc);
       }
 #pragma unroll
       for (int i = 0; i < ZL; ++i) acc[i] *= esj;
@@ -318,7 +397,7 @@ k_backproject(const Geo<C> g, const SI* __restrict__ sino, const Bufs<S, C> b, O
     const int tx = int(t1 % ntx);
     const int ty = int(t1 / ntx);
     const int iy = ty * kWarps + warp;
-    const int z0 = tz * ZC + lane * ZL;
+    const int z0 = tz * ZC + lane * ZLayout<C, ZL>::G;
     if (iy >= g.ny) continue;
     const int2 sp = g.xspan[iy];
     unsigned mask = 0;
@@ -359,14 +438,14 @@ k_backproject(const Geo<C> g, const SI* __restrict__ sino, const Bufs<S, C> b, O
       if constexpr (MODE == kBpStore) {
         if (need == nullptr || ((mask >> v) & 1u)) store_z<O, C, ZL>(out + base, acc[v]);
       } else if ((mask >> v) & 1u) {
-        // the epilogue runs on halves of the z-vector to keep its live range short
-        constexpr int H = (ZL % 8 == 0) ? ZL / 2 : ZL;
+        // the epilogue runs group by group to keep its live range short
+        using L = ZLayout<C, ZL>;
 #pragma unroll
-        for (int h0 = 0; h0 < ZL; h0 += H) {
-          C part[H];
+        for (int q = 0; q < L::NG; ++q) {
+          C part[L::G];
 #pragma unroll
-          for (int i = 0; i < H; ++i) part[i] = acc[v][h0 + i];
-          dual_update<S, C, H, MODE == kBpDualCheck>(b, sc, base + h0, part, red);
+          for (int i = 0; i < L::G; ++i) part[i] = acc[v][q * L::G + i];
+          dual_update<S, C, L::G, MODE == kBpDualCheck>(b, sc, base + q * L::kStride, part, red);
         }
       }
     }

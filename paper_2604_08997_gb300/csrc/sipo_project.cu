@@ -31,11 +31,13 @@ __global__ void k_need_bits(const uint8_t* __restrict__ need, uint32_t* __restri
 
 template <typename SI, typename S, typename C, int MODE, typename O>
 void launch_project(const Geo<C>& g, const SI* vol, const Bufs<S, C>& b, O* out,
-                    const uint8_t* act_col, bool vec, cudaStream_t stream, const NeedBits& nb,
+                    const uint8_t* act_col, int zl, cudaStream_t stream, const NeedBits& nb,
                     const int2* rspan) {
-  constexpr int ZLV = sizeof(SI) == 8 ? 4 : 8;
-  if (vec)
-    k_project<SI, S, C, ZLV, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, vol, b, out, act_col, nb, rspan);
+  constexpr int G = z_group<C>();
+  if (zl == 2 * G)
+    k_project<SI, S, C, 2 * G, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, vol, b, out, act_col, nb, rspan);
+  else if (zl == G)
+    k_project<SI, S, C, G, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, vol, b, out, act_col, nb, rspan);
   else
     k_project<SI, S, C, 1, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, vol, b, out, act_col, nb, rspan);
 }
@@ -59,7 +61,7 @@ template void launch_ray_spans<double>(const Geo<double>&, const uint8_t*, int2*
 
 #define SIPO_FP(SI, S, C, M, O) \
   template void launch_project<SI, S, C, M, O>(const Geo<C>&, const SI*, const Bufs<S, C>&, O*, \
-                                                const uint8_t*, bool, cudaStream_t, const NeedBits&, \
+                                                const uint8_t*, int, cudaStream_t, const NeedBits&, \
                                                 const int2*);
 #define SIPO_FP_SOLVER(S, C)          \
   SIPO_FP(S, S, C, kFpPrimal, C)      \

@@ -139,28 +139,7 @@ __device__ __forceinline__ void dual_update(const Bufs<S, C>& b, const StepScala
                                             size_t base, const C (&dbar)[ZL],
                                             double* red) {
   uint8_t lab[ZL];
-  if constexpr (ZL % 8 == 0) {
-    const uint2* p = reinterpret_cast<const uint2*>(b.lab + base);
-#pragma unroll
-    for (int i = 0; i < ZL / 8; ++i) {
-      uint2 r = __ldg(p + i);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) lab[8 * i + j] = (r.x >> (8 * j)) & 0xff;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) lab[8 * i + 4 + j] = (r.y >> (8 * j)) & 0xff;
-    }
-  } else if constexpr (ZL % 4 == 0) {
-    const uint32_t* p = reinterpret_cast<const uint32_t*>(b.lab + base);
-#pragma unroll
-    for (int i = 0; i < ZL / 4; ++i) {
-      uint32_t r = __ldg(p + i);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) lab[4 * i + j] = (r >> (8 * j)) & 0xff;
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < ZL; ++i) lab[i] = b.lab[base + i];
-  }
+  load_labels<C, ZL>(b.lab + base, lab);
   bool any = false;
 #pragma unroll
   for (int i = 0; i < ZL; ++i) any |= (lab[i] != kExt);

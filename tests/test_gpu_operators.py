@@ -39,6 +39,10 @@ CASES = [
     (24, 24, 16, 19, 35, 11.0, 0.03, (0.0, 0.0, 0.0)),
     (21, 26, 24, 31, 37, 10.5, 0.02, (1.0, 0.7, 1.3)),
     (33, 33, 1, 45, 47, 0.0, 0.0, (0.0, 0.0, 0.0)),
+    # deep z: two 16-byte groups per lane (FP32 at nz % 256 == 0, FP64 at nz % 128 == 0)
+    (11, 9, 256, 7, 15, 4.0, 0.05, (0.0, 0.0, 0.0)),
+    # one group per lane with a partly idle last warp (132 = 128 + 4)
+    (10, 12, 132, 9, 17, 0.0, 0.0, (0.0, 0.0, 0.0)),
 ]
 
 

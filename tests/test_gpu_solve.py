@@ -91,6 +91,40 @@ def test_fp64_iterates_track_the_oracle(sipo, case, extra):
         assert abs(a - b) <= 1e-7 * max(abs(b), 1e-3), (key, a, b)
 
 
+def _layered_target(n, nz):
+    """Per-slice disc targets that change along z, so a mix-up of z values
+    between lanes or 16-byte groups changes the result."""
+    t = np.empty((n, n, nz), np.float32)
+    for z in range(nz):
+        t[:, :, z] = discs_2d(n, n_discs=1, r_range=(1.5, 3.0), container_radius=4.0, seed=z % 7)[:, :, 0]
+    return t
+
+
+@pytest.mark.parametrize("storage,nz,iters,rtol,atol", [("f64", 128, 320, 1e-7, 1e-10),
+                                                        ("f32", 256, 64, 1e-4, 1e-5)])
+def test_deep_z_solve_tracks_the_oracle(sipo, storage, nz, iters, rtol, atol):
+    """The fused solver kernels with two 16-byte groups per lane (FP64 at
+    nz = 128, FP32 at nz = 256) against the FP64 oracle PDHG.  FP32 iterates
+    differ from FP64 ones by rounding (~1e-7 relative per step), so the FP32
+    case runs one check period and allows 1e-4 relative plus 1e-5 absolute on
+    the (already normalised) residuals."""
+    n, na, nd = 10, 8, 15
+    tgt = _layered_target(n, nz)
+    ang = uniform_angles(na)
+    cp = dict(kase=2, inhibit_ratio=0.6, band_width=2)
+    lp, ops = build_lp(Geometry(n, n, nz, ang, nd), tgt, CaseParams(case=2, inhibit_ratio=0.6, band_width=2))
+    ref = pdhg.solve(lp, ops, kkt_tol=0.0, max_iter=iters)
+    st = sipo.SIPO_F64 if storage == "f64" else sipo.SIPO_F32
+    ctx = sipo.sipo_create(dict(nx=n, ny=n, nz=nz, angles=ang, n_det=nd), tgt, cp,
+                           dict(storage=st, kkt_tol=0.0, max_iter=iters))
+    res = sipo.sipo_solve(ctx)
+    assert res["iters"] == iters
+    assert res["restarts"] == ref["restarts"]
+    for key in ("pobj", "dobj", "rel_primal", "rel_dual"):
+        a, b = res[key], ref["info"][key]
+        assert abs(a - b) <= rtol * abs(b) + atol, (key, a, b)
+
+
 def test_disc64_case1_fp64_to_1e6(sipo):
     """The 64x64 / 96-angle / 91-bin single-slice workload, Case 1, to KKT 1e-6."""
     wl = workload("disc64")
