@@ -317,13 +317,63 @@ k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __r
 }
 
 // ----------------------------------------------------------- backprojector
-// One angle for the NV voxels of a warp's row segment.  Voxels are visited in
-// increasing detector coordinate (left to right when cos >= 0, right to left
-// otherwise); u then never decreases and floor(u) advances by 0 or 1 from one
-// voxel to the next (|cos| <= 1), so a two-row window (rows cur and cur + 1,
-// ZL values per lane each) slides along the detector and each sinogram row is
-// loaded once per angle instead of once per voxel.  Rows off the detector are
-// zero.  The taps are the same weights as before; only loads are shared.
+// Per-angle interpolation data of a warp's NV voxels, computed by the lanes
+// for kBpChunk angles at once (lane l: angle k0 + l): for voxel v, the first
+// tap i0 = floor(u) and the weights w0 (bin i0) and w1 (bin i0 + 1),
+// attenuation and vial factors included.  Voxels without their flag keep
+// their i0 (so the detector window below still moves monotonically) and get
+// zero weights; their sums are never stored.
+template <typename C> struct alignas(2 * sizeof(C) >= 16 ? 8 : 16) BpEnt {
+  C w0, w1;
+  int i0, pad;
+};
+template <typename C> constexpr int bp_chunk() { return sizeof(C) == 8 ? 16 : 32; }
+
+template <typename C, int NV>
+struct BpTable {
+  BpEnt<C> e[NV][bp_chunk<C>()];
+};
+
+template <typename C, int NV>
+__device__ __forceinline__ void bp_fill(const Geo<C>& g, int k, C yf, C xf0, int iy, int tx0, unsigned mask,
+                                        BpTable<C, NV>& tb, int slot) {
+  const C c = g.cs[2 * k], s = g.cs[2 * k + 1];
+  const C inner = geo_inner(yf, s, g.off);
+  const C eyv = g.ex ? g.ey[(size_t)k * g.ny + iy] : C(1);
+  const C* esk = g.es ? g.es + (size_t)k * g.nd : nullptr;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const C u = geo_outer(xf0 + C(v), c, inner);
+    C flo;
+    int i0;
+    floor_split(u, flo, i0);
+    C w0 = C(0), w1 = C(0);
+    if ((mask >> v) & 1u) {
+      const C wv = u - flo;
+      const C e = g.ex ? g.ex[(size_t)k * g.nx + tx0 + v] * eyv : C(1);
+      w0 = (C(1) - wv) * e;
+      w1 = wv * e;
+      if (esk) {
+        w0 = unsigned(i0) < unsigned(g.nd) ? w0 * esk[i0] : C(0);
+        w1 = unsigned(i0 + 1) < unsigned(g.nd) ? w1 * esk[i0 + 1] : C(0);
+      }
+    }
+    BpEnt<C> en;
+    en.w0 = w0;
+    en.w1 = w1;
+    en.i0 = i0;
+    en.pad = 0;
+    tb.e[v][slot] = en;
+  }
+}
+
+// One angle (table column kk) for the NV voxels of a warp's row segment.
+// Voxels are visited in increasing detector coordinate (left to right when
+// cos >= 0, right to left otherwise); u then never decreases and floor(u)
+// advances by 0 or 1 from one voxel to the next (|cos| <= 1), so a two-row
+// window (rows cur and cur + 1, ZL values per lane each) slides along the
+// detector and each sinogram row is loaded once per angle instead of once per
+// voxel.  Rows off the detector are zero.
 template <typename SI, typename C, int ZL>
 __device__ __forceinline__ void bp_load_row(const Geo<C>& g, const SI* srow, int r, C (&t)[ZL]) {
   if (unsigned(r) < unsigned(g.nd)) {
@@ -335,39 +385,29 @@ __device__ __forceinline__ void bp_load_row(const Geo<C>& g, const SI* srow, int
 }
 
 template <typename SI, typename C, int ZL, int NV, bool FWD>
-__device__ __forceinline__ void bp_angle(const Geo<C>& g, const SI* srow, const C* exk, const C* esk,
-                                         C eyv, C xf0, C c, C inner, unsigned mask, C (&acc)[NV][ZL]) {
+__device__ __forceinline__ void bp_angle(const Geo<C>& g, const SI* srow, const BpTable<C, NV>& tb, int kk,
+                                         C (&acc)[NV][ZL]) {
   int cur = -2147483647;
-  C tA[ZL], tB[ZL];
+  C r0[ZL], r1[ZL];  // rows cur and cur + 1
 #pragma unroll
-  for (int i = 0; i < ZL; ++i) { tA[i] = C(0); tB[i] = C(0); }
+  for (int i = 0; i < ZL; ++i) { r0[i] = C(0); r1[i] = C(0); }
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
     const int v = FWD ? q : NV - 1 - q;
-    if (!((mask >> v) & 1u)) continue;
-    const C u = geo_outer(xf0 + C(v), c, inner);
-    C flo;
-    int i0;
-    floor_split(u, flo, i0);
-    const C wv = u - flo;
-    const C e = exk ? exk[v] * eyv : C(1);
-    C w0 = (C(1) - wv) * e, w1 = wv * e;
-    if (esk) {
-      w0 = unsigned(i0) < unsigned(g.nd) ? w0 * esk[i0] : C(0);
-      w1 = unsigned(i0 + 1) < unsigned(g.nd) ? w1 * esk[i0 + 1] : C(0);
-    }
+    const BpEnt<C> en = tb.e[v][kk];
+    const int i0 = en.i0;
     if (i0 != cur) {
       if (i0 == cur + 1) {
 #pragma unroll
-        for (int i = 0; i < ZL; ++i) tA[i] = tB[i];
+        for (int i = 0; i < ZL; ++i) r0[i] = r1[i];
       } else {
-        bp_load_row<SI, C, ZL>(g, srow, i0, tA);
+        bp_load_row<SI, C, ZL>(g, srow, i0, r0);
       }
-      bp_load_row<SI, C, ZL>(g, srow, i0 + 1, tB);
+      bp_load_row<SI, C, ZL>(g, srow, i0 + 1, r1);
       cur = i0;
     }
 #pragma unroll
-    for (int i = 0; i < ZL; ++i) acc[v][i] = fma(w1, tB[i], fma(w0, tA[i], acc[v][i]));
+    for (int i = 0; i < ZL; ++i) acc[v][i] = fma(en.w1, r1[i], fma(en.w0, r0[i], acc[v][i]));
   }
 }
 
@@ -375,7 +415,10 @@ __device__ __forceinline__ void bp_angle(const Geo<C>& g, const SI* srow, const 
 // Tile: NV voxel columns along x per warp, one row per warp (8 rows per
 // block), ZL z values per lane.  need: per (iy, ix) column flag (nullptr:
 // every column); columns without it are skipped (and left unwritten in
-// kBpStore mode unless need is nullptr).
+// kBpStore mode unless need is nullptr).  Angles go in chunks (32 for FP32,
+// 16 for FP64): the lanes fill the warp's BpTable for the chunk, then the warp
+// applies the chunk's angles in order, so every voxel sums its angles in
+// increasing order.
 template <typename SI, typename S, typename C, int ZL, int NV, int MINB, int MODE, typename O>
 __global__ void __launch_bounds__(kThreads, MINB)
 k_backproject(const Geo<C> g, const SI* __restrict__ sino, const Bufs<S, C> b, O* __restrict__ out,
@@ -390,6 +433,8 @@ k_backproject(const Geo<C> g, const SI* __restrict__ sino, const Bufs<S, C> b, O
   double red[NR > 0 ? NR : 1] = {};
   StepScalars<C> sc{};
   if (MODE != kBpStore) sc = read_scalars<C>(b.st);
+  __shared__ __align__(16) BpTable<C, NV> tabs[kWarps];
+  BpTable<C, NV>& tb = tabs[warp];
 
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int tz = int(t % nzc);
@@ -412,21 +457,27 @@ k_backproject(const Geo<C> g, const SI* __restrict__ sino, const Bufs<S, C> b, O
     for (int v = 0; v < NV; ++v)
 #pragma unroll
       for (int i = 0; i < ZL; ++i) acc[v][i] = C(0);
-    if (mask != 0u && z0 < g.nz) {
+    // the whole warp takes part (table fill + shuffle-free broadcast reads);
+    // a lane past the end of a ragged z column reads the column's first
+    // group and never stores its result
+    if (mask != 0u) {
       const C yf = C(iy) - g.cy;
       const C xf0 = C(tx * NV) - g.cx;
-      const SI* sz = sino + z0;
-      for (int k = 0; k < g.na; ++k) {
-        const C c = g.cs[2 * k], s = g.cs[2 * k + 1];
-        const C inner = geo_inner(yf, s, g.off);
-        const C eyv = g.ex ? g.ey[(size_t)k * g.ny + iy] : C(1);
-        const SI* srow = sz + (size_t)k * g.nd * g.nz;
-        const C* exk = g.ex ? g.ex + (size_t)k * g.nx + tx * NV : nullptr;
-        const C* esk = g.es ? g.es + (size_t)k * g.nd : nullptr;
-        if (c >= C(0))
-          bp_angle<SI, C, ZL, NV, true>(g, srow, exk, esk, eyv, xf0, c, inner, mask, acc);
-        else
-          bp_angle<SI, C, ZL, NV, false>(g, srow, exk, esk, eyv, xf0, c, inner, mask, acc);
+      const SI* sz = sino + (z0 < g.nz ? z0 : 0);
+      constexpr int KC = bp_chunk<C>();
+      for (int k0 = 0; k0 < g.na; k0 += KC) {
+        if (lane < KC && k0 + lane < g.na) bp_fill<C, NV>(g, k0 + lane, yf, xf0, iy, tx * NV, mask, tb, lane);
+        __syncwarp();
+        const int kn = min(KC, g.na - k0);
+        for (int kk = 0; kk < kn; ++kk) {
+          const int k = k0 + kk;
+          const SI* srow = sz + (size_t)k * g.nd * g.nz;
+          if (g.cs[2 * k] >= C(0))
+            bp_angle<SI, C, ZL, NV, true>(g, srow, tb, kk, acc);
+          else
+            bp_angle<SI, C, ZL, NV, false>(g, srow, tb, kk, acc);
+        }
+        __syncwarp();
       }
     }
     if (z0 >= g.nz) continue;
