@@ -363,15 +363,26 @@ struct Solver final : SolverBase {
   // sigma derivative).  tmp_a and tmp_b are C volumes distinct from in/out.
   template <typename TI, typename TO>
   void psf3(const TI* in, TO* out, C* tmp_a, C* tmp_b, int deriv, cudaStream_t s) {
-    const int grid = grid_for((long long)V);
     const C* tp[3];
     for (int a = 0; a < 3; ++a) tp[a] = (deriv == a) ? dtaps[a] : taps[a];
-    // identity axes still run a pass with the single tap 1 (R = 0) only when
-    // deriving; otherwise they are skipped by copying through
-    k_conv_axis<TI, C, C><<<grid, kThreads, 0, s>>>(in, tmp_a, tp[0] ? tp[0] : unit_tap(), R[0], nx, ny, nz, 0);
-    k_conv_axis<C, C, C><<<grid, kThreads, 0, s>>>(tmp_a, tmp_b, tp[1] ? tp[1] : unit_tap(), R[1], nx, ny, nz, 1);
-    k_conv_axis<C, TO, C><<<grid, kThreads, 0, s>>>(tmp_b, out, tp[2] ? tp[2] : unit_tap(), R[2], nx, ny, nz, 2);
+    // an axis without blur runs the single tap 1 (R = 0): a copy
+    conv_pass<TI, C>(in, tmp_a, tp[0] ? tp[0] : unit_tap(), R[0], 0, s);
+    conv_pass<C, C>(tmp_a, tmp_b, tp[1] ? tp[1] : unit_tap(), R[1], 1, s);
+    conv_pass<C, TO>(tmp_b, out, tp[2] ? tp[2] : unit_tap(), R[2], 2, s);
     count(3);
+  }
+
+  // One axis pass: VG = 4 z values per thread when nz % 4 == 0.
+  template <typename TI, typename TO>
+  void conv_pass(const TI* in, TO* out, const C* tp, int r, int axis, cudaStream_t s) {
+    const int vg = nz % 4 == 0 ? 4 : 1;
+    const int zt = std::min(nz / vg, kThreads), lpb = kThreads / zt;
+    const long long nb = ((long long)nx * ny + lpb - 1) / lpb;
+    const int grid = int(std::max<long long>(1, std::min<long long>(nb, 152LL * 16)));
+    if (vg == 4)
+      k_conv_axis<TI, TO, C, 4><<<grid, kThreads, 0, s>>>(in, out, tp, r, nx, ny, nz, axis);
+    else
+      k_conv_axis<TI, TO, C, 1><<<grid, kThreads, 0, s>>>(in, out, tp, r, nx, ny, nz, axis);
   }
 
   C* unit = nullptr;

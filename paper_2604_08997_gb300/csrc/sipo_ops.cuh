@@ -563,25 +563,82 @@ k_ray_spans(const Geo<C> g, const uint8_t* __restrict__ need, int2* __restrict__
 
 // ------------------------------------------------------- separable PSF pass
 // out = taps (*) in along one axis (0: x, stride nz; 1: y, stride nx*nz;
-// 2: z, stride 1), zero outside the grid; taps has 2R+1 entries.
-template <typename TI, typename TO, typename C>
+// 2: z, stride 1), zero outside the grid; taps has 2R+1 entries, applied in
+// increasing order.  A thread makes VG consecutive z outputs of one (y, x)
+// column (VG = 4 when nz % 4 == 0, else 1); the threads of a block cover
+// consecutive z groups of consecutive columns, so every access of a warp is
+// contiguous.  Along x and y each tap is one VG-wide load shared by the
+// thread's outputs and the tap range is clipped to the grid; along z the
+// VG + 2R inputs stream through a register window.
+template <typename TI, typename C, int VG>
+__device__ __forceinline__ void conv_load(const TI* p, C (&v)[VG]) {
+  if constexpr (VG == 4 && sizeof(TI) == 4) {
+    const uint4 r = __ldg(reinterpret_cast<const uint4*>(p));
+    v[0] = __uint_as_float(r.x); v[1] = __uint_as_float(r.y);
+    v[2] = __uint_as_float(r.z); v[3] = __uint_as_float(r.w);
+  } else if constexpr (VG == 4 && sizeof(TI) == 2) {
+    const uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
+    v[0] = __uint_as_float(r.x << 16); v[1] = __uint_as_float(r.x & 0xffff0000u);
+    v[2] = __uint_as_float(r.y << 16); v[3] = __uint_as_float(r.y & 0xffff0000u);
+  } else {
+#pragma unroll
+    for (int j = 0; j < VG; ++j) v[j] = to_c(p[j]);
+  }
+}
+
+template <typename TI, typename TO, typename C, int VG>
 __global__ void __launch_bounds__(kThreads)
 k_conv_axis(const TI* __restrict__ in, TO* __restrict__ out, const C* __restrict__ taps, int R,
             int nx, int ny, int nz, int axis) {
-  const long long n = (long long)nx * ny * nz;
-  const long long stride = axis == 0 ? nz : (axis == 1 ? (long long)nx * nz : 1);
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int z = int(idx % nz);
-    const long long r = idx / nz;
-    const int ix = int(r % nx);
-    const int iy = int(r / nx);
-    const int a = axis == 0 ? ix : (axis == 1 ? iy : z);
-    const int na = axis == 0 ? nx : (axis == 1 ? ny : nz);
-    const int m0 = max(0, R - a), m1 = min(2 * R, na - 1 - a + R);
-    C s = C(0);
-    for (int m = m0; m <= m1; ++m) s = fma(taps[m], to_c(in[idx + (m - R) * stride]), s);
-    out[idx] = from_c<TO>(s);
+  const int nzg = nz / VG;
+  const int zt = nzg < kThreads ? nzg : kThreads;  // z groups per block pass
+  const int lpb = kThreads / zt;                    // columns per block pass
+  const int tz = threadIdx.x % zt, tl = threadIdx.x / zt;
+  if (tl >= lpb) return;
+  const int ncol = nx * ny;
+  const size_t stride = axis == 0 ? (size_t)nz : (axis == 1 ? (size_t)nx * nz : 1);
+  for (int colx = blockIdx.x * lpb + tl; colx < ncol; colx += gridDim.x * lpb) {
+    const int ix = colx % nx, iy = colx / nx;
+    const size_t cbase = (size_t)colx * nz;
+    for (int zg = tz; zg < nzg; zg += zt) {
+      const int z0 = zg * VG;
+      C acc[VG];
+#pragma unroll
+      for (int j = 0; j < VG; ++j) acc[j] = C(0);
+      if (axis < 2) {
+        const int a = axis == 0 ? ix : iy;
+        const int na = axis == 0 ? nx : ny;
+        const int m0 = max(0, R - a), m1 = min(2 * R, na - 1 - a + R);
+        const TI* p = in + cbase + z0 + (long long)(m0 - R) * (long long)stride;
+        for (int m = m0; m <= m1; ++m, p += stride) {
+          C v[VG];
+          conv_load<TI, C, VG>(p, v);
+          const C t = __ldg(taps + m);
+#pragma unroll
+          for (int j = 0; j < VG; ++j) acc[j] = fma(t, v[j], acc[j]);
+        }
+      } else {
+        const TI* p = in + cbase;
+        C w[VG];
+#pragma unroll
+        for (int j = 0; j < VG; ++j) {
+          const int z = z0 - R + j;
+          w[j] = (z >= 0 && z < nz) ? to_c(p[z]) : C(0);
+        }
+        for (int m = 0; m <= 2 * R; ++m) {
+          const C t = __ldg(taps + m);
+#pragma unroll
+          for (int j = 0; j < VG; ++j) acc[j] = fma(t, w[j], acc[j]);
+#pragma unroll
+          for (int j = 0; j + 1 < VG; ++j) w[j] = w[j + 1];
+          const int z = z0 - R + m + VG;
+          w[VG - 1] = (z >= 0 && z < nz) ? to_c(p[z]) : C(0);
+        }
+      }
+      TO* o = out + cbase + z0;
+#pragma unroll
+      for (int j = 0; j < VG; ++j) o[j] = from_c<TO>(acc[j]);
+    }
   }
 }
 
