@@ -42,6 +42,33 @@ SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# two fused operator kernels, from one ncu capture of this workload
+# (profiles/k_project_csg256_f32.md, profiles/k_backproject_csg256_f32.md).
+# It is reported only while the kernel sources still hash to the value they
+# had at the capture; after any change to them it is null until re-captured.
+KERNEL_SOURCES = ["sipo_device.cuh", "sipo_solver.cuh", "sipo_ops.cuh", "sipo_launch.h",
+                  "sipo_project.cu", "sipo_backproject.cu"]
+TRAFFIC = {("csg256", "f32"): {"sources_sha256_16": "54845c8fb90826c5",
+                               "project": 279749888, "backproject": 234198272}}
+
+
+def kernel_sources_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2604_08997_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(workload: str, storage: str, kernel: str):
+    rec = TRAFFIC.get((workload, storage))
+    if rec is None or rec["sources_sha256_16"] != kernel_sources_hash():
+        return None
+    return rec[kernel]
+
+
 # ------------------------------------------------------------- distributed
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -252,7 +279,8 @@ def run_gpu(args, dist, rank, world, device):
     wl = make_workload(args.workload)
     geo, cp = geometry_dict(wl), case_dict(wl)
     tgt = torch.from_numpy(wl.target).to(device)
-    tol = dict(storage=storage, kkt_tol=0.0, max_iter=args.warmup, check_every=args.check_every)
+    tol = dict(storage=storage, kkt_tol=0.0, max_iter=args.warmup, check_every=args.check_every,
+               tile_cfg=args.bp_tile)
     ctx = sipo.sipo_create(geo, tgt, cp, tol)
     sipo.sipo_solve(ctx)                      # W warm-up iterations (graph captured here)
     sipo.sipo_set_tolerances(ctx, 0.0, args.steps, args.check_every)
@@ -282,10 +310,12 @@ def run_gpu(args, dist, rank, world, device):
     bp_taps, fp_taps = tap_counts(wl, need, act_col)
     bp_ms = phases["backproject"]
     fp_ms = phases["project_primal"]
+    tr_bp = captured_traffic(args.workload, args.storage, "backproject")
+    tr_fp = captured_traffic(args.workload, args.storage, "project")
     if bp_ms >= fp_ms:
-        dom, dom_ms, taps = "k_backproject (fused dual update)", bp_ms, bp_taps
+        dom, dom_ms, taps, traffic = "k_backproject (fused dual update)", bp_ms, bp_taps, tr_bp
     else:
-        dom, dom_ms, taps = "k_project (fused primal update)", fp_ms, fp_taps
+        dom, dom_ms, taps, traffic = "k_project (fused primal update)", fp_ms, fp_taps, tr_fp
     # algorithmic HBM bytes: every input element once, every output once
     el = 2 if args.storage == "bf16" else (8 if args.storage == "f64" else 4)
     cw = 8 if args.storage == "f64" else 4
@@ -302,7 +332,8 @@ def run_gpu(args, dist, rank, world, device):
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x "
                                f"{SM_MAX_MHZ:.0f} MHz (no measured FP32 peak exists)",
                 "units": "taps (one FMA = 2 FLOP per tap per z value)", "units_per_launch": taps,
@@ -311,10 +342,12 @@ def run_gpu(args, dist, rank, world, device):
                 "backproject": {"ms": bp_ms, "taps": bp_taps,
                                 "tflops": 2.0 * bp_taps / (bp_ms * 1e-3) / 1e12,
                                 "alg_bytes": bytes_bp, "gbs": bytes_bp / (bp_ms * 1e-3) / 1e9,
+                                "traffic": tr_bp,
                                 "hbm_frac_of_measured": bytes_bp / (bp_ms * 1e-3) / 1e9 / hbm},
                 "project": {"ms": fp_ms, "taps": fp_taps,
                             "tflops": 2.0 * fp_taps / (fp_ms * 1e-3) / 1e12,
                             "alg_bytes": bytes_fp, "gbs": bytes_fp / (fp_ms * 1e-3) / 1e9,
+                            "traffic": tr_fp,
                             "hbm_frac_of_measured": bytes_fp / (fp_ms * 1e-3) / 1e9 / hbm},
                 "hbm_peak_gbs": hbm}
     # time to relative KKT 1e-4: the requested instance, and the strictest
@@ -382,6 +415,8 @@ def main(argv=None):
     p.add_argument("--workload", default="csg256")
     p.add_argument("--storage", default="f32", choices=["f32", "bf16", "f64"])
     p.add_argument("--check-every", type=int, default=64)
+    p.add_argument("--bp-tile", type=int, default=-1,
+                   help="backprojector tile table entry (-1: autotuned at creation)")
     p.add_argument("--profile-iters", type=int, default=8)
     p.add_argument("--kkt-iters", type=int, default=2048)
     p.add_argument("--feasible-ratio", type=float, default=0.85)
