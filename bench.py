@@ -277,6 +277,10 @@ def run_gpu(args, dist, rank, world, device):
     sipo.build()
     storage = {"f32": sipo.SIPO_F32, "bf16": sipo.SIPO_BF16, "f64": sipo.SIPO_F64}[args.storage]
     wl = make_workload(args.workload)
+    if args.case is not None:
+        wl.case = args.case
+        if args.case == 1:
+            wl.tol_lo = wl.tol_hi = args.delta
     geo, cp = geometry_dict(wl), case_dict(wl)
     tgt = torch.from_numpy(wl.target).to(device)
     tol = dict(storage=storage, kkt_tol=0.0, max_iter=args.warmup, check_every=args.check_every,
@@ -415,6 +419,9 @@ def main(argv=None):
     p.add_argument("--workload", default="csg256")
     p.add_argument("--storage", default="f32", choices=["f32", "bf16", "f64"])
     p.add_argument("--check-every", type=int, default=64)
+    p.add_argument("--case", type=int, default=None, choices=[0, 1, 2],
+                   help="override the workload's LP case (1: tolerance band, 2: inhibition)")
+    p.add_argument("--delta", type=float, default=0.05, help="case-1 dose tolerance")
     p.add_argument("--bp-tile", type=int, default=-1,
                    help="backprojector tile table entry (-1: autotuned at creation)")
     p.add_argument("--profile-iters", type=int, default=8)
