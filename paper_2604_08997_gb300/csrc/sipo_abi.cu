@@ -376,13 +376,27 @@ struct Solver final : SolverBase {
   template <typename TI, typename TO>
   void conv_pass(const TI* in, TO* out, const C* tp, int r, int axis, cudaStream_t s) {
     const int vg = nz % 4 == 0 ? 4 : 1;
-    const int zt = std::min(nz / vg, kThreads), lpb = kThreads / zt;
-    const long long nb = ((long long)nx * ny + lpb - 1) / lpb;
+    const int nzg = nz / vg;
+    long long nb;
+    if (axis < 2) {
+      const int na = axis == 0 ? nx : ny, no = axis == 0 ? ny : nx;
+      nb = (long long)no * ((na + kConvA - 1) / kConvA) * ((nzg + kConvZ - 1) / kConvZ);
+    } else {
+      const int lpb = kThreads / std::min(nzg, kThreads);
+      nb = ((long long)nx * ny + lpb - 1) / lpb;
+    }
     const int grid = int(std::max<long long>(1, std::min<long long>(nb, 152LL * 16)));
-    if (vg == 4)
-      k_conv_axis<TI, TO, C, 4><<<grid, kThreads, 0, s>>>(in, out, tp, r, nx, ny, nz, axis);
-    else
-      k_conv_axis<TI, TO, C, 1><<<grid, kThreads, 0, s>>>(in, out, tp, r, nx, ny, nz, axis);
+    if (axis < 2) {
+      if (vg == 4)
+        k_conv_xy<TI, TO, C, 4><<<grid, kThreads, 0, s>>>(in, out, tp, r, nx, ny, nz, axis);
+      else
+        k_conv_xy<TI, TO, C, 1><<<grid, kThreads, 0, s>>>(in, out, tp, r, nx, ny, nz, axis);
+    } else {
+      if (vg == 4)
+        k_conv_z<TI, TO, C, 4><<<grid, kThreads, 0, s>>>(in, out, tp, r, nx, ny, nz);
+      else
+        k_conv_z<TI, TO, C, 1><<<grid, kThreads, 0, s>>>(in, out, tp, r, nx, ny, nz);
+    }
   }
 
   C* unit = nullptr;

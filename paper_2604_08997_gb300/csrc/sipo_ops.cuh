@@ -565,11 +565,9 @@ k_ray_spans(const Geo<C> g, const uint8_t* __restrict__ need, int2* __restrict__
 // out = taps (*) in along one axis (0: x, stride nz; 1: y, stride nx*nz;
 // 2: z, stride 1), zero outside the grid; taps has 2R+1 entries, applied in
 // increasing order.  A thread makes VG consecutive z outputs of one (y, x)
-// column (VG = 4 when nz % 4 == 0, else 1); the threads of a block cover
-// consecutive z groups of consecutive columns, so every access of a warp is
-// contiguous.  Along x and y each tap is one VG-wide load shared by the
-// thread's outputs and the tap range is clipped to the grid; along z the
-// VG + 2R inputs stream through a register window.
+// column (VG = 4 when nz % 4 == 0, else 1).  Along x and y each tap is one
+// VG-wide load shared by the thread's outputs and the tap range is clipped to
+// the grid; along z the VG + 2R inputs stream through a register window.
 template <typename TI, typename C, int VG>
 __device__ __forceinline__ void conv_load(const TI* p, C (&v)[VG]) {
   if constexpr (VG == 4 && sizeof(TI) == 4) {
@@ -586,58 +584,87 @@ __device__ __forceinline__ void conv_load(const TI* p, C (&v)[VG]) {
   }
 }
 
+// x and y passes.  A block covers kConvZ z groups of kConvA consecutive
+// positions along the blurred axis (one line of the other in-plane axis): the
+// 2R + 1 inputs of neighbouring outputs overlap, so most of each thread's tap
+// loads hit the block's own L1 lines instead of L2.
+constexpr int kConvZ = 16;
+constexpr int kConvA = kThreads / kConvZ;
+
 template <typename TI, typename TO, typename C, int VG>
 __global__ void __launch_bounds__(kThreads)
-k_conv_axis(const TI* __restrict__ in, TO* __restrict__ out, const C* __restrict__ taps, int R,
-            int nx, int ny, int nz, int axis) {
+k_conv_xy(const TI* __restrict__ in, TO* __restrict__ out, const C* __restrict__ taps, int R,
+          int nx, int ny, int nz, int axis) {
+  const int nzg = nz / VG;
+  const int na = axis == 0 ? nx : ny, no = axis == 0 ? ny : nx;
+  const int nta = (na + kConvA - 1) / kConvA, ntz = (nzg + kConvZ - 1) / kConvZ;
+  const long long ntiles = (long long)no * nta * ntz;
+  const int tz = threadIdx.x % kConvZ, ta = threadIdx.x / kConvZ;
+  const size_t stride = axis == 0 ? (size_t)nz : (size_t)nx * nz;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int zt = int(t % ntz);
+    const long long t1 = t / ntz;
+    const int at = int(t1 % nta);
+    const int o = int(t1 / nta);
+    const int a = at * kConvA + ta, zg = zt * kConvZ + tz;
+    if (a >= na || zg >= nzg) continue;
+    const int ix = axis == 0 ? a : o, iy = axis == 0 ? o : a;
+    const size_t cbase = ((size_t)iy * nx + ix) * nz + (size_t)zg * VG;
+    const int m0 = max(0, R - a), m1 = min(2 * R, na - 1 - a + R);
+    const TI* p = in + cbase + (long long)(m0 - R) * (long long)stride;
+    C acc[VG];
+#pragma unroll
+    for (int j = 0; j < VG; ++j) acc[j] = C(0);
+    for (int m = m0; m <= m1; ++m, p += stride) {
+      C v[VG];
+      conv_load<TI, C, VG>(p, v);
+      const C tp = __ldg(taps + m);
+#pragma unroll
+      for (int j = 0; j < VG; ++j) acc[j] = fma(tp, v[j], acc[j]);
+    }
+    TO* op = out + cbase;
+#pragma unroll
+    for (int j = 0; j < VG; ++j) op[j] = from_c<TO>(acc[j]);
+  }
+}
+
+// z pass: a thread makes VG consecutive z outputs of one column, its VG + 2R
+// inputs streaming through a register window; the threads of a block cover
+// consecutive z groups of consecutive columns.
+template <typename TI, typename TO, typename C, int VG>
+__global__ void __launch_bounds__(kThreads)
+k_conv_z(const TI* __restrict__ in, TO* __restrict__ out, const C* __restrict__ taps, int R,
+         int nx, int ny, int nz) {
   const int nzg = nz / VG;
   const int zt = nzg < kThreads ? nzg : kThreads;  // z groups per block pass
   const int lpb = kThreads / zt;                    // columns per block pass
   const int tz = threadIdx.x % zt, tl = threadIdx.x / zt;
   if (tl >= lpb) return;
   const int ncol = nx * ny;
-  const size_t stride = axis == 0 ? (size_t)nz : (axis == 1 ? (size_t)nx * nz : 1);
   for (int colx = blockIdx.x * lpb + tl; colx < ncol; colx += gridDim.x * lpb) {
-    const int ix = colx % nx, iy = colx / nx;
     const size_t cbase = (size_t)colx * nz;
+    const TI* p = in + cbase;
     for (int zg = tz; zg < nzg; zg += zt) {
       const int z0 = zg * VG;
-      C acc[VG];
+      C acc[VG], w[VG];
 #pragma unroll
-      for (int j = 0; j < VG; ++j) acc[j] = C(0);
-      if (axis < 2) {
-        const int a = axis == 0 ? ix : iy;
-        const int na = axis == 0 ? nx : ny;
-        const int m0 = max(0, R - a), m1 = min(2 * R, na - 1 - a + R);
-        const TI* p = in + cbase + z0 + (long long)(m0 - R) * (long long)stride;
-        for (int m = m0; m <= m1; ++m, p += stride) {
-          C v[VG];
-          conv_load<TI, C, VG>(p, v);
-          const C t = __ldg(taps + m);
-#pragma unroll
-          for (int j = 0; j < VG; ++j) acc[j] = fma(t, v[j], acc[j]);
-        }
-      } else {
-        const TI* p = in + cbase;
-        C w[VG];
-#pragma unroll
-        for (int j = 0; j < VG; ++j) {
-          const int z = z0 - R + j;
-          w[j] = (z >= 0 && z < nz) ? to_c(p[z]) : C(0);
-        }
-        for (int m = 0; m <= 2 * R; ++m) {
-          const C t = __ldg(taps + m);
-#pragma unroll
-          for (int j = 0; j < VG; ++j) acc[j] = fma(t, w[j], acc[j]);
-#pragma unroll
-          for (int j = 0; j + 1 < VG; ++j) w[j] = w[j + 1];
-          const int z = z0 - R + m + VG;
-          w[VG - 1] = (z >= 0 && z < nz) ? to_c(p[z]) : C(0);
-        }
+      for (int j = 0; j < VG; ++j) {
+        acc[j] = C(0);
+        const int z = z0 - R + j;
+        w[j] = (z >= 0 && z < nz) ? to_c(p[z]) : C(0);
       }
-      TO* o = out + cbase + z0;
+      for (int m = 0; m <= 2 * R; ++m) {
+        const C tp = __ldg(taps + m);
 #pragma unroll
-      for (int j = 0; j < VG; ++j) o[j] = from_c<TO>(acc[j]);
+        for (int j = 0; j < VG; ++j) acc[j] = fma(tp, w[j], acc[j]);
+#pragma unroll
+        for (int j = 0; j + 1 < VG; ++j) w[j] = w[j + 1];
+        const int z = z0 - R + m + VG;
+        w[VG - 1] = (z >= 0 && z < nz) ? to_c(p[z]) : C(0);
+      }
+      TO* op = out + cbase + z0;
+#pragma unroll
+      for (int j = 0; j < VG; ++j) op[j] = from_c<TO>(acc[j]);
     }
   }
 }
