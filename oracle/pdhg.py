@@ -36,6 +36,21 @@ The readings implemented here (and by the GPU solver) are published methods:
   reduced costs G^T dlam must be non-negative on every primal column, the ray
   non-negative, and its dual objective positive; the largest violation
   (l_inf) relative to the objective <= 1e-6.
+* A bound-based certificate (a reading: Farkas' lemma applied to this LP with
+  an a-priori bound on the rays) tests the first candidate exactly.  Project
+  it onto the support a certificate may have -- lam >= 0, and no lam_up on the
+  rows whose bound moves with a free scalar (band rows in Case 1, where u~ is
+  free upward; gel rows in Case 2, where v~ is) -- and apply A to it exactly:
+  g^ = A (lam^_up - lam^_lo).  For every feasible y,
+      y^T g^ <= -obj,   obj = sum_gel L lam^_lo - sum_const-up U lam^_up,
+  and the constant upper rows bound the rays: sum_j y_j b_j <= B with
+  b = A 1_rows, B = sum_rows U over those rows (Case 2: band rows with U = 1;
+  Case 1: gel rows with U = f~_U).  So y^T g^ >= -kappa B with
+  kappa = max_j max(-g^_j, 0) / b_j over active rays, and obj > kappa B proves
+  that no feasible y exists.  The test asks for obj > 0 and
+  kappa B <= (1 - 1e-3) obj, the margin covering rounding of g^.  The
+  general case has no constant upper rows (every LP of that form is
+  feasible) and no such test.
 """
 from __future__ import annotations
 
@@ -43,7 +58,7 @@ import math
 
 import numpy as np
 
-from .lp import LPData, kkt, metrics, up_bound
+from .lp import CASE1, CASE2, LPData, kkt, metrics, up_bound
 from .operators import Operators
 
 OPTIMAL, PRIMAL_INFEASIBLE, DUAL_INFEASIBLE, ITER_LIMIT = 0, 1, 2, 3
@@ -54,6 +69,7 @@ BETA_NECESSARY = 0.8
 BETA_ARTIFICIAL = 0.36
 OMEGA_SMOOTHING = 0.5
 INFEAS_TOL = 1e-6
+CERT_MARGIN = 1e-3
 
 
 class Preconditioner:
@@ -127,6 +143,46 @@ def _farkas(lp, pc, dq_g, dlam_up, dlam_lo):
     return viol / obj <= INFEAS_TOL
 
 
+def certificate_data(lp: LPData, ops: Operators):
+    """(b, B) of the bound-based certificate: b = A 1_rows on every ray and
+    B = sum of the constant upper bounds over those rows (Case 2: band rows,
+    bound 1; Case 1: gel rows, bound f~_U); None for the general case."""
+    if lp.case == CASE2:
+        rows, B = lp.band, float(lp.band.sum())
+    elif lp.case == CASE1:
+        rows, B = lp.gel, float(np.sum(lp.upper[lp.gel]))
+    else:
+        return None
+    b = ops.A(rows.astype(np.float64).reshape(ops.geo.vol_shape)).ravel()
+    return b, B
+
+
+def certificate(lp: LPData, ops: Operators, dlam_up, dlam_lo, b, B) -> bool:
+    """True if the projected dual difference proves primal infeasibility
+    (bound-based Farkas test of the module docstring)."""
+    band, gel = lp.band, lp.gel
+    lu = np.zeros(lp.labels.size)
+    ll = np.zeros(lp.labels.size)
+    ll[gel] = np.maximum(dlam_lo[gel], 0.0)
+    obj = np.sum(lp.lower[gel] * ll[gel])
+    if lp.case == CASE2:
+        lu[band] = np.maximum(dlam_up[band], 0.0)
+        obj -= lu[band].sum()
+    else:
+        lu[gel] = np.maximum(dlam_up[gel], 0.0)
+        obj -= np.sum(lp.upper[gel] * lu[gel])
+    if not obj > 0:
+        return False
+    g = ops.A((lu - ll).reshape(ops.geo.vol_shape)).ravel()
+    act = lp.active
+    viol = np.maximum(-g[act], 0.0)
+    ba = b[act]
+    if np.any((viol > 0) & (ba <= 0)):
+        return False
+    kappa = np.max(np.where(viol > 0, viol / np.where(ba > 0, ba, 1.0), 0.0), initial=0.0)
+    return kappa * B <= (1.0 - CERT_MARGIN) * obj
+
+
 def solve(lp: LPData, ops: Operators, kkt_tol=1e-4, max_iter=10000,
           check_every=64, omega0=None, verbose=False, history=None):
     """Run the restarted Halpern PDHG; returns a dict with status, T(z) and KKT data.
@@ -153,6 +209,7 @@ def solve(lp: LPData, ops: Operators, kkt_tol=1e-4, max_iter=10000,
     def A(vv):
         return ops.A(vv.reshape(geo.vol_shape)).ravel()
 
+    cert = certificate_data(lp, ops)
     y, u, v = np.zeros(S), 0.0, 1.0
     lam_up, lam_lo = np.zeros(V), np.zeros(V)
     y0, u0, v0, lam_up0, lam_lo0 = y.copy(), u, v, lam_up.copy(), lam_lo.copy()
@@ -191,7 +248,9 @@ def solve(lp: LPData, ops: Operators, kkt_tol=1e-4, max_iter=10000,
                     and info["rel_gap"] <= kkt_tol):
                 status = OPTIMAL
             elif k > 0 and (_farkas(lp, pc, g_p - g0, lam_up_p - lam_up0, lam_lo_p - lam_lo0)
-                            or _farkas(lp, pc, g_p - g, lam_up_p - lam_up, lam_lo_p - lam_lo)):
+                            or _farkas(lp, pc, g_p - g, lam_up_p - lam_up, lam_lo_p - lam_lo)
+                            or (cert is not None
+                                and certificate(lp, ops, lam_up_p - lam_up0, lam_lo_p - lam_lo0, *cert))):
                 status = PRIMAL_INFEASIBLE
             elif k == max_iter:
                 status = ITER_LIMIT
