@@ -132,6 +132,9 @@ struct Solver final : SolverBase {
   S *q = nullptr, *qp = nullptr, *kq = nullptr;
   C *d = nullptr, *d0 = nullptr, *dp = nullptr;
   C *braw = nullptr, *t1 = nullptr, *t2 = nullptr, *t3 = nullptr, *tvol = nullptr;
+  C *cert_b = nullptr, *cert_q = nullptr;  // bound-based certificate: A 1_rows, candidate
+  bool cert_on = false;
+  double cert_B = 0.0;
   Scal* st = nullptr;
   double* part = nullptr;
   double* trace = nullptr;
@@ -256,6 +259,7 @@ struct Solver final : SolverBase {
     b.d = d; b.d0 = d0; b.dp = dp; b.row = row; b.ft = ft_is_const ? nullptr : ft; b.lab = lab;
     b.ft_const = ft_const; b.up_ratio = C(up_ratio); b.has_u = has_u; b.has_v = has_v;
     b.band_rhs = C(band_rhs); b.st = st; b.part = part;
+    b.cert_b = cert_b; b.cert_q = cert_q;
     return b;
   }
 
@@ -597,6 +601,23 @@ struct Solver final : SolverBase {
     const double h_hat2 = sums[5] + sums[6];
     omega0 = (c_hat2 > 0 && h_hat2 > 0) ? std::sqrt(c_hat2 / h_hat2) : 1.0;
     if (tol.primal_weight > 0) omega0 = tol.primal_weight;
+    // bound-based infeasibility certificate (Cases 1 and 2): b = A 1_rows and
+    // B = sum of the constant upper bounds of those rows
+    cert_on = cp.kase == SIPO_CASE1 || cp.kase == SIPO_CASE2;
+    if (cert_on) {
+      cert_q = dalloc<C>(V);
+      cert_b = dalloc<C>(SN);
+      k_cert_rows<C><<<gv, kThreads, 0, stream>>>(lab, t1, cp.kase == SIPO_CASE2 ? 2 : 1, (long long)V);
+      if (psf) {
+        psf3<C, C>(t1, t2, t3, braw, -1, stream);
+        ck(cudaMemsetAsync(braw, 0, V * sizeof(C), stream), "memset");
+        launch_project<C, C, C, kFpStore, C>(g, t2, Bufs<C, C>{}, cert_b, nullptr, zl, stream);
+      } else {
+        launch_project<C, C, C, kFpStore, C>(g, t1, Bufs<C, C>{}, cert_b, nullptr, zl, stream);
+      }
+      cert_B = cp.kase == SIPO_CASE2 ? double(n_band) * band_rhs : up_ratio * sums[2];
+      count(3);
+    }
     count(16);
     choose_tiles();
   }
@@ -630,6 +651,9 @@ struct Solver final : SolverBase {
     h.trace = trace;
     h.trace_cap = kTraceCap;
     h.trace_n = 0;
+    h.cert_B = cert_B;
+    h.cert_on = cert_on ? 1 : 0;
+    h.cert = 0;
     *h_st = h;
     ck(cudaMemcpyAsync(st, h_st, sizeof(Scal), cudaMemcpyHostToDevice, stream), "state");
     ck(cudaStreamSynchronize(stream), "begin solve");
@@ -741,6 +765,18 @@ struct Solver final : SolverBase {
     }
     launch_project<S, S, C, kFpResid, C>(g, psf ? kq : qp, B, (C*)nullptr, act_col, zl, s, nbits, rspan);
     count(1);
+    if (cert_on) {
+      // bound-based certificate of the epoch difference lam+ - lam0
+      k_cert_vol<S, C><<<kRedBlocks, kThreads, 0, s>>>(B, (long long)V);
+      const C* cq = cert_q;
+      if (psf) {
+        psf3<C, C>(cert_q, t3, t1, t2, -1, s);
+        cq = t3;
+      }
+      launch_project<C, S, C, kFpCert, C>(g, cq, B, (C*)nullptr, act_col, zl, s, nbits, rspan);
+      k_cert_decide<<<1, kThreads, 0, s>>>(st, part);
+      count(3);
+    }
     k_scalar_check<<<1, kThreads, 0, s>>>(st, part);
     count(1);
     if (ze > 1) {

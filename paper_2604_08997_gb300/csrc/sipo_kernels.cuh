@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kThreads) k_scalar_step(Scal* st, const double
 __global__ void __launch_bounds__(kThreads) k_scalar_check(Scal* st, const double* part) {
   if (st->done) return;
   double s[kNumSlots];
-  for (int i = kSlRp2; i < kNumSlots; ++i) {
+  for (int i = kSlRp2; i <= kSlFrG; ++i) {
     const bool mx = i == kSlFkNeg || i == kSlFrNeg || i == kSlFkG || i == kSlFrG;
     s[i] = mx ? block_max_slot(part, i) : block_sum_slot(part, i);
   }
@@ -336,7 +336,8 @@ __global__ void __launch_bounds__(kThreads) k_scalar_check(Scal* st, const doubl
   int status = -1;
   if (rel_p <= st->kkt_tol && rel_d <= st->kkt_tol && rel_gap <= st->kkt_tol) {
     status = 0;
-  } else if (st->k > 0 && ((fe >= 0.0 && fe <= kInfeasTol) || (fr >= 0.0 && fr <= kInfeasTol))) {
+  } else if (st->k > 0 && ((fe >= 0.0 && fe <= kInfeasTol) || (fr >= 0.0 && fr <= kInfeasTol) ||
+                            st->cert)) {
     status = 1;
   }
   if (status < 0 && st->k >= st->max_iter) status = 3;
@@ -375,6 +376,72 @@ __global__ void __launch_bounds__(kThreads) k_scalar_check(Scal* st, const doubl
   }
   st->restart = restart;
   st->k += 1;
+}
+
+// ------------------------------------------- bound-based certificate
+// Primal infeasibility by Farkas' lemma with a bound on the rays (a reading of
+// the infeasibility diagnostic of Secs. 2.7.1-2.7.2).  The constant upper rows
+// bound every feasible ray set: Case 2, sum_band d <= |band|; Case 1,
+// sum_gel d <= sum_gel f~_U.  With b = A 1_rows (those rows) and B that sum,
+// a candidate lam^ >= 0 without lam_up on the rows whose bound moves with a
+// free scalar (gel in Case 2, band in Case 1) satisfies, for every feasible y,
+// y^T A(lam^_up - lam^_lo) <= -obj, while y^T g^ >= -kappa B with
+// kappa = max over active rays of max(-g^_j, 0) / b_j.  obj > kappa B thus
+// proves infeasibility; the test asks for kappa B <= (1 - kCertMargin) obj.
+
+// rows indicator (1 on the bounding rows, else 0) for b = A 1_rows
+template <typename C>
+__global__ void __launch_bounds__(kThreads) k_cert_rows(const uint8_t* __restrict__ lab, C* __restrict__ out,
+                                                        int kase, long long n) {
+  const uint8_t rows = kase == 2 ? kBand : kGel;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = lab[i] == rows ? C(1) : C(0);
+}
+
+// The epoch difference lam+ - lam0 projected onto the certificate's support,
+// lam^_up - lam^_lo written to cert_q, and the FP64 partials of its dual
+// objective obj = sum_gel L lam^_lo - sum_const-up U lam^_up.
+template <typename S, typename C>
+__global__ void __launch_bounds__(kThreads) k_cert_vol(Bufs<S, C> b, long long n) {
+  if (b.st->done) return;
+  const bool case2 = b.has_v != 0;
+  double red[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const uint8_t l = b.lab[i];
+    C qv = C(0);
+    if (l == kGel) {
+      const C f = b.ft ? b.ft[i] : b.ft_const;
+      const C dlo = to_c(b.lpl[i]) - to_c(b.ll0[i]);
+      const C llh = dlo > C(0) ? dlo : C(0);
+      red[0] += double(f) * double(llh);
+      C luh = C(0);
+      if (!case2) {
+        const C dup = to_c(b.lpu[i]) - to_c(b.lu0[i]);
+        luh = dup > C(0) ? dup : C(0);
+        red[0] -= double(f) * double(b.up_ratio) * double(luh);
+      }
+      qv = luh - llh;
+    } else if (l == kBand && case2) {
+      const C dup = to_c(b.lpu[i]) - to_c(b.lu0[i]);
+      const C luh = dup > C(0) ? dup : C(0);
+      red[0] -= double(b.band_rhs) * double(luh);
+      qv = luh;
+    }
+    b.cert_q[i] = qv;
+  }
+  block_reduce_store<1>(red, b.part, kSlCertObj);
+}
+
+// One block: the verdict from the partials of k_cert_vol and of the
+// projector's certificate mode.
+__global__ void __launch_bounds__(kThreads) k_cert_decide(Scal* st, const double* part) {
+  if (st->done) return;
+  const double obj = block_sum_slot(part, kSlCertObj);
+  const double kappa = block_max_slot(part, kSlCertK);
+  if (threadIdx.x != 0) return;
+  st->cert = (obj > 0.0 && kappa * st->cert_B <= (1.0 - kCertMargin) * obj) ? 1 : 0;
 }
 
 // --------------------------------------------------------- blend kernels

@@ -21,7 +21,7 @@
 
 namespace sipo {
 
-enum FpMode : int { kFpStore = 0, kFpPrimal = 1, kFpPrimalCheck = 2, kFpResid = 3 };
+enum FpMode : int { kFpStore = 0, kFpPrimal = 1, kFpPrimalCheck = 2, kFpResid = 3, kFpCert = 4 };
 enum BpMode : int { kBpStore = 0, kBpDual = 1, kBpDualCheck = 2 };
 
 
@@ -236,7 +236,7 @@ k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __r
   const bool use_bits = nb.rows != nullptr;
   if (MODE != kFpStore && b.st->done) return;
   constexpr int ZC = 32 * ZL;
-  constexpr int NR = MODE == kFpPrimalCheck ? 2 : (MODE == kFpResid ? 4 : 0);
+  constexpr int NR = MODE == kFpPrimalCheck ? 2 : (MODE == kFpResid ? 4 : (MODE == kFpCert ? 1 : 0));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nzc = (g.nz + ZC - 1) / ZC;
   const int njb = (g.nd + kWarps - 1) / kWarps;
@@ -308,12 +308,15 @@ k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __r
       primal_update<S, C, ZL, false>(b, sc, base, acc, red);
     } else if constexpr (MODE == kFpPrimalCheck) {
       primal_update<S, C, ZL, true>(b, sc, base, acc, red);
-    } else {
+    } else if constexpr (MODE == kFpResid) {
       resid_update<S, C, ZL>(b, base, acc, red);
+    } else {
+      cert_update<S, C, ZL>(b, base, acc, red);
     }
   }
   if constexpr (MODE == kFpPrimalCheck) block_reduce_store<2>(red, b.part, kSlFpX);
   if constexpr (MODE == kFpResid) block_reduce_store<4, kResidMaxMask>(red, b.part, kSlRd2);
+  if constexpr (MODE == kFpCert) block_reduce_store<1, 1u>(red, b.part, kSlCertK);
 }
 
 // ----------------------------------------------------------- backprojector

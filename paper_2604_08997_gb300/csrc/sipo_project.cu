@@ -71,6 +71,10 @@ template void launch_ray_spans<double>(const Geo<double>&, const uint8_t*, int2*
 SIPO_FP_SOLVER(float, float)
 SIPO_FP_SOLVER(__nv_bfloat16, float)
 SIPO_FP_SOLVER(double, double)
+// bound-based certificate: the candidate volume is in the compute type
+SIPO_FP(float, float, float, kFpCert, float)
+SIPO_FP(float, __nv_bfloat16, float, kFpCert, float)
+SIPO_FP(double, double, double, kFpCert, double)
 SIPO_FP(float, float, float, kFpStore, float)
 SIPO_FP(double, double, double, kFpStore, double)
 SIPO_FP(__nv_bfloat16, __nv_bfloat16, float, kFpStore, float)

@@ -17,6 +17,8 @@
 // blend kernel forms the next iterate.
 #pragma once
 
+#include <math_constants.h>
+
 #include "sipo_device.cuh"
 
 namespace sipo {
@@ -52,6 +54,9 @@ enum Slot : int {
   kSlRd2s,        // preconditioned
   kSlFkG,         // Farkas: max(-(g+ - g0), 0) on active rays (max-reduced)
   kSlFrG,         // Farkas: max(-(g+ - g), 0) on active rays (residual direction, max-reduced)
+  // bound-based certificate of the epoch difference (check step)
+  kSlCertObj,     // dual objective of the projected candidate
+  kSlCertK,       // max over active rays of max(-g^, 0) / b (max-reduced)
   kNumSlots
 };
 
@@ -72,7 +77,14 @@ struct Scal {
   // per-check trace: kTraceFields doubles per entry, up to trace_cap entries
   double* trace;
   int trace_cap, trace_n;
+  // bound-based infeasibility certificate: B, whether the case has one, and
+  // the verdict of the current check
+  double cert_B;
+  int cert_on, cert;
 };
+
+// Margin of the bound-based certificate: kappa * B <= (1 - kCertMargin) obj.
+constexpr double kCertMargin = 1e-3;
 
 // k, kkt, rel_primal, rel_dual, rel_gap, pobj, omega, restarts, and the
 // relative violations of the two Farkas candidates (epoch difference, residual
@@ -104,6 +116,9 @@ struct Bufs {
   C band_rhs;           // right side of band rows: 0 (u~ variable) or 1 (Case 2)
   Scal* st;
   double* part;
+  // bound-based certificate: b = A 1_rows per ray, the candidate volume
+  const C* cert_b;
+  C* cert_q;
 };
 
 // Halpern weights and steps read once per kernel.
@@ -284,6 +299,22 @@ __device__ __forceinline__ void primal_update(const Bufs<S, C>& b, const StepSca
   } else {
     store_z<S, C, ZL>(b.yp + base, yo);
     store_z<C, C, ZL>(b.gc + base, g);
+  }
+}
+
+// Bound-based certificate: largest max(-g^, 0) / b over active rays (red[0];
+// +inf where a violated ray has b = 0).
+template <typename S, typename C, int ZL>
+__device__ __forceinline__ void cert_update(const Bufs<S, C>& b, size_t base, const C (&g)[ZL], double* red) {
+  C col[ZL], bb[ZL];
+  load_z<C, C, ZL>(b.col + base, col);
+  load_z<C, C, ZL>(b.cert_b + base, bb);
+#pragma unroll
+  for (int i = 0; i < ZL; ++i) {
+    if (col[i] > C(0) && g[i] < C(0)) {
+      const double v = -double(g[i]);
+      red[0] = fmax(red[0], bb[i] > C(0) ? v / double(bb[i]) : CUDART_INF);
+    }
   }
 }
 

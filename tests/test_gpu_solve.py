@@ -204,3 +204,25 @@ def test_batched_solve_matches_individual_solves(sipo):
         assert a["iters"] == b["iters"]
         assert a["pobj"] == b["pobj"] and a["kkt"] == b["kkt"]
     assert batched[-1]["status"] == sipo.SIPO_PRIMAL_INFEASIBLE
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_blurred_inhibition_certified_infeasible(sipo, storage):
+    """Blurred, attenuated 16^3 Case-2 part at r = 0.8: the bound-based Farkas
+    certificate proves infeasibility; FP64 at the oracle's iteration."""
+    n = 16
+    tgt = csg_3d(n, vial_radius=n * 0.47, band_width=2, seed=2, feature=(3.0, 6.0))
+    ang = uniform_angles(24)
+    sig = (1.5, 1.5, 2.5)
+    lp, ops = build_lp(Geometry(n, n, n, ang, n, vial_radius=n * 0.47, mu=0.08, psf_sigma=sig), tgt,
+                       CaseParams(case=2, inhibit_ratio=0.8, band_width=2))
+    ref = pdhg.solve(lp, ops, kkt_tol=1e-4, max_iter=1024)
+    assert ref["status"] == pdhg.PRIMAL_INFEASIBLE
+    st = sipo.SIPO_F64 if storage == "f64" else sipo.SIPO_F32
+    ctx = sipo.sipo_create(dict(nx=n, ny=n, nz=n, angles=ang, n_det=n, vial_radius=n * 0.47, mu=0.08,
+                                psf_sigma=sig), tgt, dict(kase=2, inhibit_ratio=0.8, band_width=2),
+                           dict(storage=st, kkt_tol=1e-4, max_iter=1024))
+    res = sipo.sipo_solve(ctx)
+    assert res["status"] == sipo.SIPO_PRIMAL_INFEASIBLE, res
+    if storage == "f64":
+        assert res["iters"] == ref["iters"]
