@@ -436,8 +436,15 @@ k_backproject(const Geo<C> g, const SI* __restrict__ sino, const Bufs<S, C> b, O
   double red[NR > 0 ? NR : 1] = {};
   StepScalars<C> sc{};
   if (MODE != kBpStore) sc = read_scalars<C>(b.st);
-  __shared__ __align__(16) BpTable<C, NV> tabs[kWarps];
-  BpTable<C, NV>& tb = tabs[warp];
+  // per warp: the angle table, reused after the angle loop to stage the
+  // accumulators when they fit, so that the fused epilogue need not keep them
+  // in registers
+  constexpr size_t kStageBytes = size_t(NV) * ZL * 32 * sizeof(C);
+  constexpr bool kStage = MODE != kBpStore && kStageBytes <= 4096;
+  constexpr size_t kWarpBytes = sizeof(BpTable<C, NV>) > (kStage ? kStageBytes : 0) ? sizeof(BpTable<C, NV>)
+                                                                                   : kStageBytes;
+  __shared__ __align__(16) unsigned char smem_warp[kWarps][kWarpBytes];
+  BpTable<C, NV>& tb = *reinterpret_cast<BpTable<C, NV>*>(smem_warp[warp]);
 
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int tz = int(t % nzc);
@@ -483,7 +490,21 @@ k_backproject(const Geo<C> g, const SI* __restrict__ sino, const Bufs<S, C> b, O
         __syncwarp();
       }
     }
-    if (z0 >= g.nz) continue;
+    using LS = ZLayout<C, ZL>;
+    C* stage = reinterpret_cast<C*>(smem_warp[warp]);
+    if constexpr (kStage) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int q = 0; q < LS::NG; ++q)
+#pragma unroll
+          for (int i = 0; i < LS::G; ++i) stage[((v * LS::NG + q) * 32 + lane) * LS::G + i] = acc[v][q * LS::G + i];
+      __syncwarp();
+    }
+    if (z0 >= g.nz) {
+      __syncwarp();
+      continue;
+    }
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const int ix = tx * NV + v;
@@ -498,11 +519,13 @@ k_backproject(const Geo<C> g, const SI* __restrict__ sino, const Bufs<S, C> b, O
         for (int q = 0; q < L::NG; ++q) {
           C part[L::G];
 #pragma unroll
-          for (int i = 0; i < L::G; ++i) part[i] = acc[v][q * L::G + i];
+          for (int i = 0; i < L::G; ++i)
+            part[i] = kStage ? stage[((v * L::NG + q) * 32 + lane) * L::G + i] : acc[v][q * L::G + i];
           dual_update<S, C, L::G, MODE == kBpDualCheck>(b, sc, base + q * L::kStride, part, red);
         }
       }
     }
+    __syncwarp();
   }
   if constexpr (MODE == kBpDual) block_reduce_store<2>(red, b.part, kSlSBand);
   if constexpr (MODE == kBpDualCheck) block_reduce_store<kCheckSlots, kCheckMaxMask>(red, b.part, kSlRp2);
