@@ -380,6 +380,31 @@ def run_gpu(args, dist, rank, world, device):
                                "alpha": rk["alpha"]}
             if ctx_k is not ctx:
                 sipo.sipo_destroy(ctx_k)
+        if args.escalate > 0:
+            # precision escalation: BF16 storage for at most N iterations, then
+            # FP32 warm-started from its last check (both contexts created first)
+            for label, cpk in runs:
+                lo = sipo.sipo_create(geo, tgt, cpk, dict(tol, storage=sipo.SIPO_BF16, kkt_tol=1e-4,
+                                                          max_iter=args.escalate))
+                hi = sipo.sipo_create(geo, tgt, cpk, dict(tol, storage=sipo.SIPO_F32, kkt_tol=1e-4,
+                                                          max_iter=args.kkt_iters))
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rl = sipo.sipo_solve(lo)
+                if rl["status"] != sipo.SIPO_OPTIMAL and rl["status"] != sipo.SIPO_PRIMAL_INFEASIBLE:
+                    sipo.sipo_warm_start(hi, lo)
+                    rh = sipo.sipo_solve(hi)
+                else:
+                    rh = rl
+                torch.cuda.synchronize()
+                tk = time.perf_counter() - t0
+                kkt_info["bf16_%d_then_f32_%s" % (args.escalate, label)] = {
+                    "inhibit_ratio": cpk.get("inhibit_ratio"), "seconds": tk,
+                    "iters_bf16": rl["iters"], "kkt_bf16": rl["kkt"],
+                    "iters_f32": rh["iters"] if rh is not rl else 0, "status": rh["status_name"],
+                    "kkt": rh["kkt"], "objective": rh["pobj"]}
+                sipo.sipo_destroy(lo)
+                sipo.sipo_destroy(hi)
     # end to end through the C ABI from pinned host memory
     tgt_h = torch.from_numpy(wl.target).pin_memory()
     y_h = torch.empty((wl.n_angles, wl.n_det, wl.nz), dtype=torch.float32).pin_memory()
@@ -427,6 +452,8 @@ def main(argv=None):
     p.add_argument("--profile-iters", type=int, default=8)
     p.add_argument("--kkt-iters", type=int, default=2048)
     p.add_argument("--feasible-ratio", type=float, default=0.85)
+    p.add_argument("--escalate", type=int, default=0,
+                   help="also time BF16 storage for N iterations, then FP32 warm-started from it")
     p.add_argument("--cpu-seconds", type=float, default=20.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     args = p.parse_args(argv)

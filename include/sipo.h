@@ -167,6 +167,19 @@ int sipo_create(const sipo_geometry *geo, const float *f_T, int f_T_location,
  * INVALID_ARG, CUDA, TIMEOUT. */
 int sipo_solve(sipo_ctx *ctx, void *y_out, int y_location, sipo_result *res);
 
+/* Warm start, for precision escalation (a reading of the mixed-precision
+ * requirement: iterates stored in BF16 stall above tight tolerances, so a
+ * BF16 solve is continued in FP32 from where it stopped).  Copies the point
+ * T(z) of the last KKT check of `src`'s most recent solve, with its scalars
+ * u~, v~ and its primal weight, into `dst`, converting the storage type; the
+ * next sipo_solve or sipo_solve_batched of `dst` starts from it, as a restart
+ * point (iterate and anchor), instead of from zero.  Both contexts must hold
+ * the same problem (sizes, angles, case parameters, labels; checked through
+ * a fingerprint) and may differ in storage and tile settings.  Synchronises
+ * both contexts' work.  Errors: INVALID_ARG (null, same context, different
+ * problems, src never solved), CUDA. */
+int sipo_warm_start(sipo_ctx *dst, const sipo_ctx *src);
+
 /* Solves n independent contexts as one batch (a parameter sweep): one CUDA
  * graph holds one check period of every context as parallel branches (each on
  * its context's stream), so small LPs share the device and the host waits

@@ -70,6 +70,7 @@ SIGNATURES = {
     "sipo_solve": (c_int, [c_void_p, c_void_p, c_int, POINTER(sipo_result)]),
     "sipo_solve_batched": (c_int, [POINTER(c_void_p), c_int, POINTER(c_void_p), c_int,
                                    POINTER(sipo_result)]),
+    "sipo_warm_start": (c_int, [c_void_p, c_void_p]),
     "sipo_project": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     "sipo_backproject": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     "sipo_psf_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
@@ -235,6 +236,11 @@ def sipo_solve(ctx: Context, y_out=None) -> dict:
         ptr, loc = _ptr(y_out)
     _check(load().sipo_solve(ctx.handle, c_void_p(ptr), loc, ctypes.byref(res)))
     return res.as_dict()
+
+
+def sipo_warm_start(dst: Context, src: Context) -> None:
+    """sipo_warm_start(dst, src): dst's next solve starts from src's last T(z)."""
+    _check(load().sipo_warm_start(dst.handle, src.handle))
 
 
 def sipo_solve_batched(ctxs, y_outs=None) -> list[dict]:

@@ -78,7 +78,29 @@ struct SolverBase {
   virtual void init_for_batch() = 0;
   virtual void enqueue_period(cudaStream_t s) = 0;
   virtual const Scal& host_state() const = 0;
+  // warm start: the last check's T(z) of a finished solve (device arrays and
+  // their element types), a problem fingerprint, and the import of such a point
+  struct Point {
+    const void *yp, *gp, *lpu, *lpl, *dp;
+    int s_dtype, c_dtype;
+    Scal st;
+  };
+  virtual Point point() const = 0;
+  virtual std::vector<double> fingerprint() const = 0;
+  virtual void warm_from(const SolverBase& src) = 0;
 };
+
+// Element conversion of n values of dtype `in_dtype` at `in` into `out`.
+template <typename TO>
+void convert_from(const void* in, int in_dtype, TO* out, long long n, cudaStream_t s) {
+  const int grid = grid_for(n);
+  if (in_dtype == SIPO_F64)
+    k_convert<double, TO><<<grid, kThreads, 0, s>>>(static_cast<const double*>(in), out, n);
+  else if (in_dtype == SIPO_BF16)
+    k_convert<__nv_bfloat16, TO><<<grid, kThreads, 0, s>>>(static_cast<const __nv_bfloat16*>(in), out, n);
+  else
+    k_convert<float, TO><<<grid, kThreads, 0, s>>>(static_cast<const float*>(in), out, n);
+}
 
 // Autotuned backprojector tile per problem shape (process-wide cache).
 struct TileKey {
@@ -215,7 +237,8 @@ struct Solver final : SolverBase {
   }
 
   void init_for_batch() override {
-    init_state();
+    if (!warm_pending) init_state();
+    warm_pending = false;
     launches = 0;
     t_start = std::chrono::steady_clock::now();
   }
@@ -228,6 +251,67 @@ struct Solver final : SolverBase {
 
   const Scal& host_state() const override { return *h_st; }
 
+  // ------------------------------------------------------------ warm start
+  bool warm_pending = false;
+
+  static int dtype_of_s() {
+    return sizeof(S) == 8 ? SIPO_F64 : (sizeof(S) == 2 ? SIPO_BF16 : SIPO_F32);
+  }
+
+  Point point() const override {
+    Point pt{yp, gp, lpu, lpl, dp, dtype_of_s(), compute_dtype(), *h_st};
+    return pt;
+  }
+
+  std::vector<double> fingerprint() const override {
+    std::vector<double> f = {double(nx), double(ny), double(nz), double(na), double(nd), double(cp.kase),
+                             double(n_band), double(n_gel), f_crit, cp.tol_lo, cp.tol_hi,
+                             cp.inhibit_ratio, double(cp.band_width), psf ? 1.0 : 0.0};
+    f.insert(f.end(), angles.begin(), angles.end());
+    return f;
+  }
+
+  // The next solve starts from src's last T(z): it becomes both the iterate and
+  // the restart anchor (exactly what a restart does), with src's primal weight.
+  void warm_from(const SolverBase& src) override {
+    if (src.fingerprint() != fingerprint())
+      fail(SIPO_ERR_INVALID_ARG, "warm start: the two contexts do not hold the same problem");
+    const Point pt = src.point();
+    if (pt.st.k <= 0 && pt.st.done == 0)
+      fail(SIPO_ERR_INVALID_ARG, "warm start: the source context has not been solved");
+    init_state();
+    convert_from<S>(pt.yp, pt.s_dtype, yp, (long long)SN, stream);
+    convert_from<C>(pt.gp, pt.c_dtype, gp, (long long)SN, stream);
+    convert_from<S>(pt.lpu, pt.s_dtype, lpu, (long long)V, stream);
+    convert_from<S>(pt.lpl, pt.s_dtype, lpl, (long long)V, stream);
+    convert_from<C>(pt.dp, pt.c_dtype, dp, (long long)V, stream);
+    Scal h = *h_st;
+    h.u = h.u0 = h.up = pt.st.up;
+    h.v = h.v0 = h.vp = pt.st.vp;
+    h.omega = pt.st.omega;
+    h.restart = 1;
+    *h_st = h;
+    ck(cudaMemcpyAsync(st, h_st, sizeof(Scal), cudaMemcpyHostToDevice, stream), "state");
+    // the copy reads the pinned mirror when it runs: finish it before the
+    // mirror is written again below
+    ck(cudaStreamSynchronize(stream), "warm start");
+    const Bufs<S, C> B = bufs();
+    const long long nvv = (long long)(V / ze), nvs = (long long)(SN / ze);
+    if (ze > 1) {
+      k_blend_sino<S, C, z_group<C>()><<<grid_for(nvs), kThreads, 0, stream>>>(B, nvs);
+      k_blend_vol<S, C, z_group<C>()><<<kRedBlocks, kThreads, 0, stream>>>(B, nvv);
+    } else {
+      k_blend_sino<S, C, 1><<<grid_for(nvs), kThreads, 0, stream>>>(B, nvs);
+      k_blend_vol<S, C, 1><<<kRedBlocks, kThreads, 0, stream>>>(B, nvv);
+    }
+    h.restart = 0;
+    *h_st = h;
+    ck(cudaMemcpyAsync(st, h_st, sizeof(Scal), cudaMemcpyHostToDevice, stream), "state");
+    ck(cudaStreamSynchronize(stream), "warm start");
+    count(7);
+    warm_pending = true;
+  }
+
   void set_tolerances(const sipo_tolerances* t) override {
     const int p = t->check_every > 0 ? t->check_every : 64;
     if (p != P || t->storage != tol.storage)
@@ -236,6 +320,12 @@ struct Solver final : SolverBase {
     tol.kkt_tol = t->kkt_tol;
     tol.max_iter = t->max_iter;
     if (t->primal_weight > 0) omega0 = t->primal_weight;
+    if (warm_pending) {  // the imported state is kept; only the limits change
+      h_st->kkt_tol = tol.kkt_tol;
+      h_st->max_iter = tol.max_iter;
+      ck(cudaMemcpyAsync(st, h_st, sizeof(Scal), cudaMemcpyHostToDevice, stream), "state");
+      ck(cudaStreamSynchronize(stream), "tolerances");
+    }
   }
 
   Geo<C> geo() const {
@@ -629,7 +719,8 @@ struct Solver final : SolverBase {
   }
 
   void begin_solve() override {
-    init_state();
+    if (!warm_pending) init_state();
+    warm_pending = false;
     build_graph();
     launches = 0;
     t_start = std::chrono::steady_clock::now();
@@ -1116,6 +1207,15 @@ int sipo_solve(sipo_ctx* ctx, void* y_out, int y_location, sipo_result* res) {
   if (!ctx || !res) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
   run_solve(ctx->c.s.get());
   ctx->c.s->finish_solve(y_out, y_location, res);
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
+int sipo_warm_start(sipo_ctx* dst, const sipo_ctx* src) {
+  SIPO_TRY
+  if (!dst || !src) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
+  if (dst == src) sipo::fail(SIPO_ERR_INVALID_ARG, "warm start: source and destination are the same context");
+  dst->c.s->warm_from(*src->c.s);
   return SIPO_OK;
   SIPO_CATCH
 }

@@ -226,3 +226,47 @@ def test_blurred_inhibition_certified_infeasible(sipo, storage):
     assert res["status"] == sipo.SIPO_PRIMAL_INFEASIBLE, res
     if storage == "f64":
         assert res["iters"] == ref["iters"]
+
+
+def test_warm_start_continues_from_the_source_point(sipo):
+    """A solve warm-started from a finished FP64 solve of the same problem stops
+    at its first check with the same objective; a context holding another
+    problem is refused."""
+    case, extra = TINY[2]
+    lp, ops, geo, tgt, cp = _tiny(case, extra)
+    tol = dict(storage=sipo.SIPO_F64, kkt_tol=1e-9, max_iter=100000)
+    src = sipo.sipo_create(geo, tgt, cp, tol)
+    r0 = sipo.sipo_solve(src)
+    assert r0["status"] == sipo.SIPO_OPTIMAL
+    dst = sipo.sipo_create(geo, tgt, cp, tol)
+    sipo.sipo_warm_start(dst, src)
+    r1 = sipo.sipo_solve(dst)
+    assert r1["status"] == sipo.SIPO_OPTIMAL and r1["iters"] <= 64
+    assert abs(r1["pobj"] - r0["pobj"]) <= 1e-8 * abs(r0["pobj"])
+    other = sipo.sipo_create(geo, tgt, dict(cp, inhibit_ratio=0.7), tol)
+    with pytest.raises(sipo.SipoError):
+        sipo.sipo_warm_start(other, src)
+
+
+def test_bf16_escalated_to_fp32_reaches_the_target(sipo):
+    """Precision escalation on the reduced 48^3 Case-2 instance: BF16 storage
+    for at most 1024 iterations, then FP32 warm-started from its last check,
+    to KKT 1e-4; the objective agrees with the oracle optimum."""
+    n = 48
+    tgt = csg_3d(n, vial_radius=22.5, band_width=2, seed=2, feature=(3.0, 12.0))
+    ang = uniform_angles(68)
+    geo = dict(nx=n, ny=n, nz=n, angles=ang, n_det=n, vial_radius=22.5)
+    cp = dict(kase=2, inhibit_ratio=0.8, band_width=2)
+    lp, ops = build_lp(Geometry(n, n, n, ang, n, vial_radius=22.5), tgt,
+                       CaseParams(case=2, inhibit_ratio=0.8, band_width=2))
+    ref = pdhg.solve(lp, ops, kkt_tol=1e-5, max_iter=60000)
+    if ref["status"] != pdhg.OPTIMAL:
+        pytest.skip("instance not optimal in the oracle")
+    low = sipo.sipo_create(geo, tgt, cp, dict(storage=sipo.SIPO_BF16, kkt_tol=1e-4, max_iter=1024))
+    rl = sipo.sipo_solve(low)
+    high = sipo.sipo_create(geo, tgt, cp, dict(storage=sipo.SIPO_F32, kkt_tol=1e-4, max_iter=60000))
+    sipo.sipo_warm_start(high, low)
+    rh = sipo.sipo_solve(high)
+    assert rh["status"] == sipo.SIPO_OPTIMAL, rh
+    assert abs(rh["pobj"] - ref["obj"]) <= 1e-3 * abs(ref["obj"])
+    assert rh["kkt"] <= 1e-4 and rl["iters"] <= 1024
