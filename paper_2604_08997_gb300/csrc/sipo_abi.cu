@@ -634,11 +634,12 @@ struct Solver final : SolverBase {
     part = dalloc<double>(size_t(kNumSlots) * kRedBlocks);
     trace = dalloc<double>(size_t(kTraceCap) * kTraceFields);
     ensure_temps();
-    if (psf) {
-      kq = dalloc<S>(V);
-      braw = dalloc<C>(V);
-      ck(cudaMemsetAsync(braw, 0, V * sizeof(C), stream), "memset");
-    }
+    if (psf) kq = dalloc<S>(V);
+    // P^T y-bar in the compute type: the PSF path blurs it; the check step of
+    // both paths hands it to the element-wise dual update (k_dual), whose FP64
+    // check reductions would otherwise spill inside the backprojector
+    braw = dalloc<C>(V);
+    ck(cudaMemsetAsync(braw, 0, V * sizeof(C), stream), "memset");
     const Geo<C> g = geo();
     const Bufs<S, C> B = bufs();
     // active rays: [P_mu f_T]_j > 0 with the unblurred operator (Sec. 2.2)
@@ -851,8 +852,9 @@ struct Solver final : SolverBase {
       dual_launch<true>(B, t3, nvv, s);
       enqueue_psf_q(qp, s);
     } else {
-      launch_backproject<S, S, C, kBpDualCheck, C>(g, ybar, B, (C*)nullptr, need, zl, s, bp_nv);
+      launch_backproject<S, S, C, kBpStore, C>(g, ybar, B, braw, need, zl, s, bp_nv);
       count(1);
+      dual_launch<true>(B, braw, nvv, s);
     }
     launch_project<S, S, C, kFpResid, C>(g, psf ? kq : qp, B, (C*)nullptr, act_col, zl, s, nbits, rspan);
     count(1);

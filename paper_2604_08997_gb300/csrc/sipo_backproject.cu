@@ -35,7 +35,6 @@ void launch_backproject(const Geo<C>& g, const SI* sino, const Bufs<S, C>& b, O*
                                                     O*, const uint8_t*, int, cudaStream_t, int);
 #define SIPO_BP_SOLVER(S, C)       \
   SIPO_BP(S, S, C, kBpDual, C)     \
-  SIPO_BP(S, S, C, kBpDualCheck, C) \
   SIPO_BP(S, S, C, kBpStore, C)
 
 SIPO_BP_SOLVER(float, float)

@@ -22,7 +22,7 @@
 namespace sipo {
 
 enum FpMode : int { kFpStore = 0, kFpPrimal = 1, kFpPrimalCheck = 2, kFpResid = 3, kFpCert = 4 };
-enum BpMode : int { kBpStore = 0, kBpDual = 1, kBpDualCheck = 2 };
+enum BpMode : int { kBpStore = 0, kBpDual = 1 };
 
 
 // --------------------------------------------------------------- projector
@@ -428,7 +428,7 @@ k_backproject(const Geo<C> g, const SI* __restrict__ sino, const Bufs<S, C> b, O
               const uint8_t* __restrict__ need) {
   if (MODE != kBpStore && b.st->done) return;
   constexpr int ZC = 32 * ZL;
-  constexpr int NR = MODE == kBpDualCheck ? kCheckSlots : (MODE == kBpDual ? 2 : 0);
+  constexpr int NR = MODE == kBpDual ? 2 : 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ntx = (g.nx + NV - 1) / NV, nty = (g.ny + kWarps - 1) / kWarps;
   const int nzc = (g.nz + ZC - 1) / ZC;
@@ -521,14 +521,13 @@ k_backproject(const Geo<C> g, const SI* __restrict__ sino, const Bufs<S, C> b, O
 #pragma unroll
           for (int i = 0; i < L::G; ++i)
             part[i] = kStage ? stage[((v * L::NG + q) * 32 + lane) * L::G + i] : acc[v][q * L::G + i];
-          dual_update<S, C, L::G, MODE == kBpDualCheck>(b, sc, base + q * L::kStride, part, red);
+          dual_update<S, C, L::G, false>(b, sc, base + q * L::kStride, part, red);
         }
       }
     }
     __syncwarp();
   }
   if constexpr (MODE == kBpDual) block_reduce_store<2>(red, b.part, kSlSBand);
-  if constexpr (MODE == kBpDualCheck) block_reduce_store<kCheckSlots, kCheckMaxMask>(red, b.part, kSlRp2);
 }
 
 // ----------------------------------------------------------- ray row spans
