@@ -49,8 +49,8 @@ SM_MAX_MHZ = 2070.0
 # had at the capture; after any change to them it is null until re-captured.
 KERNEL_SOURCES = ["sipo_device.cuh", "sipo_solver.cuh", "sipo_ops.cuh", "sipo_launch.h",
                   "sipo_project.cu", "sipo_backproject.cu"]
-TRAFFIC = {("csg256", "f32"): {"sources_sha256_16": "b77dcc492895e23b",
-                               "project": 280769536, "backproject": 223789312}}
+TRAFFIC = {("csg256", "f32"): {"sources_sha256_16": "acd83c62d33e2107",
+                               "project": 281752576, "backproject": 224114944}}
 
 
 def kernel_sources_hash() -> str:
