@@ -276,6 +276,7 @@ struct Solver final : SolverBase {
   void warm_from(const SolverBase& src) override {
     if (src.fingerprint() != fingerprint())
       fail(SIPO_ERR_INVALID_ARG, "warm start: the two contexts do not hold the same problem");
+    ck(cudaStreamSynchronize(src.strm()), "warm start: source");
     const Point pt = src.point();
     if (pt.st.k <= 0 && pt.st.done == 0)
       fail(SIPO_ERR_INVALID_ARG, "warm start: the source context has not been solved");

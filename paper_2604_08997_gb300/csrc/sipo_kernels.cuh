@@ -539,7 +539,9 @@ __global__ void __launch_bounds__(kThreads) k_blend_vol(Bufs<S, C> b, long long 
   block_reduce_store<2>(red, b.part, kSlSBand);
 }
 
-// Stand-alone dual update (used when the PSF sits between P^T and the prox).
+// Stand-alone dual update from a stored d_bar: used when the PSF sits between
+// P^T and the prox, and by every check step (whose FP64 reductions would spill
+// registers inside the backprojector).
 template <typename S, typename C, int ZL, bool CHECK>
 __global__ void __launch_bounds__(kThreads) k_dual(Bufs<S, C> b, const C* __restrict__ dbar,
                                                    long long nvec) {

@@ -3,8 +3,9 @@
 // Backprojection (Eqs. 2-3, P^T): every voxel sums, over all angles, the two
 // linearly interpolated detector taps floor(u) and floor(u)+1.  The operator is
 // slice-separable (z is the rotation axis), so one weight pair per
-// (x, y, angle) serves the whole z column: lanes hold z, the geometry is
-// warp-uniform, and each tap is one coalesced 16-byte vector load per lane.
+// (x, y, angle) serves the whole z column: the lanes first compute the weights
+// of 32 angles at once into a per-warp table, then the warp applies them with
+// lanes holding z, each sinogram row one coalesced load of the warp's z segment.
 //
 // Projection (P, the exact transpose): gather form.  For each ray (angle, bin)
 // the kernel walks the dominant axis of the ray direction and, on each row or

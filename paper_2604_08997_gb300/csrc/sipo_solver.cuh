@@ -12,9 +12,10 @@
 //   backprojector d_bar = A^T (2 y+ - y), then the dual prox on every row
 // and the restarted Halpern iteration z <- w (2 T(z) - z) + (1 - w) z0 is
 // fused into the same epilogues.  Every `check_every` iterations the step
-// instead writes T(z) to separate buffers, evaluates its KKT error, and a
-// scalar kernel decides termination, infeasibility and restarts before a
-// blend kernel forms the next iterate.
+// instead writes T(z) to separate buffers (the dual prox then runs in the
+// element-wise k_dual<CHECK> with the FP64 check reductions), evaluates its
+// KKT error and the infeasibility tests, and a scalar kernel decides
+// termination and restarts before blend kernels form the next iterate.
 #pragma once
 
 #include <math_constants.h>
@@ -27,7 +28,7 @@ namespace sipo {
 enum Slot : int {
   kSlSBand = 0,   // sum_band lam_up of the current iterate          (Eq. 48)
   kSlSGel,        // sum_gel f~ lam_up of the current iterate        (Eq. 49)
-  // backprojector, check step (13 slots, contiguous)
+  // check-step dual update, k_dual<CHECK> (18 slots, contiguous)
   kSlRp2,         // unscaled primal residual^2 of T(z)
   kSlRp2s,        // preconditioned primal residual^2
   kSlDobL,        // sum_gel L lam_lo+          (dual objective)
@@ -90,7 +91,7 @@ constexpr double kCertMargin = 1e-3;
 // relative violations of the two Farkas candidates (epoch difference, residual
 // direction; -1 when the candidate's dual objective is not positive)
 constexpr int kTraceFields = 10;
-constexpr int kCheckSlots = kSlFpX - kSlRp2;  // backprojector check-step slots
+constexpr int kCheckSlots = kSlFpX - kSlRp2;  // check-step dual-update slots
 // max-reduced slots among them (Farkas negativity, l_inf) and among the
 // projector residual slots (kSlRd2 .. kSlFrG)
 constexpr unsigned kCheckMaxMask = (1u << (kSlFkNeg - kSlRp2)) | (1u << (kSlFrNeg - kSlRp2));
