@@ -45,20 +45,29 @@ SM_MAX_MHZ = 2070.0
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # two fused operator kernels, from one ncu capture of this workload
 # (profiles/k_project_csg256_f32.md, profiles/k_backproject_csg256_f32.md).
-# It is reported only while the kernel sources still hash to the value they
-# had at the capture; after any change to them it is null until re-captured.
+# It is reported only while the kernel sources (code, comments aside) still
+# hash to the value they had at the capture; after any change to the code it
+# is null until re-captured.
 KERNEL_SOURCES = ["sipo_device.cuh", "sipo_solver.cuh", "sipo_ops.cuh", "sipo_launch.h",
                   "sipo_project.cu", "sipo_backproject.cu"]
-TRAFFIC = {("csg256", "f32"): {"sources_sha256_16": "acd83c62d33e2107",
+TRAFFIC = {("csg256", "f32"): {"sources_sha256_16": "ec3dfee9f2b7db7f",
                                "project": 281752576, "backproject": 224114944}}
+
+
+def _code_only(text: str) -> str:
+    """Source text without comments and blank space (comments do not change a kernel)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.strip() for line in text.splitlines() if line.strip())
 
 
 def kernel_sources_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2604_08997_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2604_08997_gb300", "csrc", f)) as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
