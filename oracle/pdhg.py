@@ -26,8 +26,10 @@ The readings implemented here (and by the GPU solver) are published methods:
   r = ||z - T(z)|| (preconditioned norm weighted by omega) decides restarts:
   sufficient decay r <= 0.2 r0, necessary decay r <= 0.8 r0 without progress
   since the previous check, or an artificial restart when the epoch reaches
-  36% of all iterations.  A restart moves z and z0 to T(z) and updates omega by
-  log-smoothing (0.5) towards ||lam - lam0|| / ||x - x0|| (scaled norms).
+  36% of all iterations.  A restart moves z and z0 to T(z) and updates omega
+  towards ||lam - lam0|| / ||x - x0|| (scaled norms): the first restart sets
+  it to that ratio (omega0 = ||c|| / ||h|| can be two orders of magnitude off,
+  e.g. in Case 1), later ones by log-smoothing (0.5).
 * Primal infeasibility (Secs. 2.7.1-2.7.2 treat an infeasible LP as a
   diagnostic): at each check two candidate directions are tested as a Farkas
   ray -- the dual difference lam+ - lam0 since the last restart, and the dual
@@ -277,8 +279,8 @@ def solve(lp: LPData, ops: Operators, kkt_tol=1e-4, max_iter=10000,
             el2 = np.sum(pc.row_up * (lam_up_p - lam_up0) ** 2) \
                 + np.sum(pc.row_lo * (lam_lo_p - lam_lo0) ** 2)
             if ex2 > 1e-30 and el2 > 1e-30:
-                omega = math.exp(OMEGA_SMOOTHING * 0.5 * math.log(el2 / ex2)
-                                 + (1.0 - OMEGA_SMOOTHING) * math.log(omega))
+                th = 1.0 if restarts == 0 else OMEGA_SMOOTHING
+                omega = math.exp(th * 0.5 * math.log(el2 / ex2) + (1.0 - th) * math.log(omega))
             y, u, v, lam_up, lam_lo = y_p, u_p, v_p, lam_up_p, lam_lo_p
             y0, u0, v0 = y_p.copy(), u_p, v_p
             lam_up0, lam_lo0 = lam_up_p.copy(), lam_lo_p.copy()

@@ -360,8 +360,9 @@ __global__ void __launch_bounds__(kThreads) k_scalar_check(Scal* st, const doubl
   if (restart) {
     const double ex2 = s[kSlOmX] + st->col_u * (up - u0) * (up - u0) + st->col_v * (vp - v0) * (vp - v0);
     const double el2 = s[kSlOmL];
-    if (ex2 > 1e-30 && el2 > 1e-30)
-      om = exp(kOmegaSmoothing * 0.5 * log(el2 / ex2) + (1.0 - kOmegaSmoothing) * log(om));
+    // the first restart sets omega to the measured ratio, later ones smooth
+    const double th = st->restarts == 0 ? 1.0 : kOmegaSmoothing;
+    if (ex2 > 1e-30 && el2 > 1e-30) om = exp(th * 0.5 * log(el2 / ex2) + (1.0 - th) * log(om));
     st->omega = om;
     st->u = up; st->v = vp; st->u0 = up; st->v0 = vp;
     st->k_in = 0;
