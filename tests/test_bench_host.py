@@ -1,0 +1,39 @@
+"""Host-side pieces of bench.py checked on the CPU: the tap counts behind the
+roofline figures against the oracle's explicit backprojection matrix, and the
+kernel-source fingerprint that gates the recorded DRAM traffic."""
+import types
+
+import numpy as np
+import pytest
+
+import bench
+from oracle.operators import Geometry, Operators
+
+
+def test_tap_counts_match_the_explicit_matrix():
+    """bench.tap_counts against the stored non-zeros of the oracle's P^T on a
+    small geometry whose detector coordinates are never integers (so every
+    in-range tap has a non-zero weight)."""
+    n, nd, na, nz = 12, 15, 9, 3
+    angles = np.arange(na) * np.pi / na + 0.1234
+    rng = np.random.default_rng(0)
+    need = rng.random((n, n)) < 0.5
+    act_col = rng.random((na, nd)) < 0.6
+    wl = types.SimpleNamespace(n=n, n_det=nd, nz=nz, vial_radius=5.0, angles=angles)
+    bp, fp = bench.tap_counts(wl, need, act_col)
+    ops = Operators(Geometry(n, n, 1, angles, nd, vial_radius=5.0), precision="f64")
+    PT = ops.PT.tocsr()                           # rows: voxels (y, x); columns: rays (angle, bin)
+    c = np.arange(n) - (n - 1) / 2.0
+    Y, X = np.meshgrid(c, c, indexing="ij")
+    rows = (need & (X * X + Y * Y <= 25.0)).ravel()
+    sub = PT[np.flatnonzero(rows)]
+    assert bp == sub.nnz * nz
+    cols = np.flatnonzero(act_col.ravel())
+    assert fp == sub[:, cols].nnz * nz
+
+
+def test_kernel_fingerprint_ignores_comments_only():
+    code = "int a = 1;  // one\n/* block\n comment */\nint b = 2;\n"
+    assert bench._code_only(code) == "int a = 1;\nint b = 2;"
+    assert bench._code_only(code.replace("// one", "// uno")) == bench._code_only(code)
+    assert bench._code_only(code.replace("= 2", "= 3")) != bench._code_only(code)
