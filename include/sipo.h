@@ -175,7 +175,8 @@ int sipo_solve(sipo_ctx *ctx, void *y_out, int y_location, sipo_result *res);
  * next sipo_solve or sipo_solve_batched of `dst` starts from it, as a restart
  * point (iterate and anchor), instead of from zero.  Both contexts must hold
  * the same problem (sizes, angles, case parameters, labels; checked through
- * a fingerprint) and may differ in storage and tile settings.  Synchronises
+ * a fingerprint), must have been created with the same device current, and
+ * may differ in storage and tile settings.  Synchronises
  * both contexts' work.  Errors: INVALID_ARG (null, same context, different
  * problems, src never solved), CUDA. */
 int sipo_warm_start(sipo_ctx *dst, const sipo_ctx *src);

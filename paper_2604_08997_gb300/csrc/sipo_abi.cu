@@ -185,7 +185,10 @@ struct Solver final : SolverBase {
     return static_cast<T*>(p);
   }
 
+  int device = 0;  // the device current at creation; every array lives there
+
   Solver(const sipo_geometry* g, const sipo_case_params* c, const sipo_tolerances* t, cudaStream_t s) {
+    ck(cudaGetDevice(&device), "cudaGetDevice");
     nx = g->nx; ny = g->ny; nz = g->nz; na = g->n_angles; nd = g->n_det;
     V = size_t(nx) * ny * nz;
     SN = size_t(na) * nd * nz;
@@ -264,7 +267,8 @@ struct Solver final : SolverBase {
   }
 
   std::vector<double> fingerprint() const override {
-    std::vector<double> f = {double(nx), double(ny), double(nz), double(na), double(nd), double(cp.kase),
+    std::vector<double> f = {double(device), double(nx), double(ny), double(nz), double(na), double(nd),
+                             double(cp.kase),
                              double(n_band), double(n_gel), f_crit, cp.tol_lo, cp.tol_hi,
                              cp.inhibit_ratio, double(cp.band_width), psf ? 1.0 : 0.0};
     f.insert(f.end(), angles.begin(), angles.end());
@@ -275,7 +279,7 @@ struct Solver final : SolverBase {
   // the restart anchor (exactly what a restart does), with src's primal weight.
   void warm_from(const SolverBase& src) override {
     if (src.fingerprint() != fingerprint())
-      fail(SIPO_ERR_INVALID_ARG, "warm start: the two contexts do not hold the same problem");
+      fail(SIPO_ERR_INVALID_ARG, "warm start: the two contexts do not hold the same problem on one device");
     ck(cudaStreamSynchronize(src.strm()), "warm start: source");
     const Point pt = src.point();
     if (pt.st.k <= 0 && pt.st.done == 0)
