@@ -186,8 +186,9 @@ int sipo_warm_start(sipo_ctx *dst, const sipo_ctx *src);
  * its context's stream), so small LPs share the device and the host waits
  * once per period.  Contexts that finish keep their branch but exit at once.
  * In a batch the iteration limit of each context is rounded up to a whole
- * number of its check periods.  Each context must appear once; contexts
- * created on the same stream run one after another.  y_outs may be NULL or an
+ * number of its check periods.  Each context must appear once, all must have
+ * been created on one device; contexts created on the same stream run one
+ * after another.  y_outs may be NULL or an
  * array of n nullable pointers (same rules as sipo_solve).  results: n
  * entries. */
 int sipo_solve_batched(sipo_ctx **ctxs, int n, void **y_outs, int y_location,

@@ -86,6 +86,7 @@ struct SolverBase {
     Scal st;
   };
   virtual Point point() const = 0;
+  virtual int dev() const = 0;
   virtual std::vector<double> fingerprint() const = 0;
   virtual void warm_from(const SolverBase& src) = 0;
 };
@@ -260,6 +261,8 @@ struct Solver final : SolverBase {
   static int dtype_of_s() {
     return sizeof(S) == 8 ? SIPO_F64 : (sizeof(S) == 2 ? SIPO_BF16 : SIPO_F32);
   }
+
+  int dev() const override { return device; }
 
   Point point() const override {
     Point pt{yp, gp, lpu, lpl, dp, dtype_of_s(), compute_dtype(), *h_st};
@@ -1237,6 +1240,8 @@ int sipo_solve_batched(sipo_ctx** ctxs, int n, void** y_outs, int y_location, si
     s[i] = ctxs[i]->c.s.get();
     for (int j = 0; j < i; ++j)
       if (s[j] == s[i]) sipo::fail(SIPO_ERR_INVALID_ARG, "a context appears twice in the batch");
+    if (s[i]->dev() != s[0]->dev())
+      sipo::fail(SIPO_ERR_INVALID_ARG, "the contexts of a batch must have been created on one device");
   }
   for (auto* x : s) x->init_for_batch();
   // One graph per check period of the whole batch: every context's period is
