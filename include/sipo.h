@@ -151,8 +151,10 @@ typedef struct sipo_result {
  * labels, the active-ray mask (Pi_act = {[P f_T]_j != 0}, Sec. 2.2), the
  * normalised target (Sec. 2.5 / Eqs. 30-31 / Eq. 39) and the diagonal
  * preconditioners, all on the device.  `stream` (cudaStream_t or NULL) is the
- * context's stream for solves; creation itself synchronises it.  On success
- * *out owns all internal device memory until sipo_destroy.  Errors:
+ * context's stream for solves; creation itself synchronises it.  The context
+ * lives on the device current at creation; every later call on it must be
+ * made with that device current.  On success *out owns all internal device
+ * memory until sipo_destroy.  Errors:
  * INVALID_ARG (sizes, NaN/negative target, empty gel, mu > 0 without vial),
  * OOM, CUDA. */
 int sipo_create(const sipo_geometry *geo, const float *f_T, int f_T_location,
