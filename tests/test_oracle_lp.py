@@ -220,27 +220,30 @@ def test_planted_sign_error_is_caught(monkeypatch):
 
 
 def _best_certificate(lp, ops):
-    """Largest obj - B * kappa over candidates of the bound-based certificate
-    (Case 2 support: lam_up on band rows, lam_lo on gel rows, sum <= 1), as an
-    LP for HiGHS in (lam_up_band, lam_lo_gel, t): t >= kappa is enforced by
-    A(lam_up - lam_lo) + t b >= 0 on every active ray.  Returns the value and
-    the maximiser as full-length dual vectors."""
+    """Largest obj - B * kappa over candidates of the bound-based certificate,
+    as an LP for HiGHS in (lam_up on its rows, lam_lo on gel, t) with
+    sum lam <= 1: t >= kappa is enforced by A(lam_up - lam_lo) + t b >= 0 on
+    every active ray.  lam_up lives on band rows (Case 2, bound 1) or gel
+    rows (Case 1, bound f~_U).  Returns the value and the maximiser as
+    full-length dual vectors."""
     act = np.flatnonzero(lp.active)
-    band, gel = np.flatnonzero(lp.band), np.flatnonzero(lp.gel)
+    gel = np.flatnonzero(lp.gel)
+    up = np.flatnonzero(lp.band) if lp.case == CASE2 else gel
+    U = np.ones(up.size) if lp.case == CASE2 else lp.upper[gel]
     b, B = pdhg.certificate_data(lp, ops)
-    Ab = ops.PT[band][:, act].T.toarray()
+    Au = ops.PT[up][:, act].T.toarray()
     Ag = ops.PT[gel][:, act].T.toarray()
-    nb, ng = band.size, gel.size
-    G = np.hstack([-Ab, Ag, -b[act][:, None]])
-    G = np.vstack([G, np.concatenate([np.ones(nb + ng), [0.0]])[None, :]])
+    nu, ng = up.size, gel.size
+    G = np.hstack([-Au, Ag, -b[act][:, None]])
+    G = np.vstack([G, np.concatenate([np.ones(nu + ng), [0.0]])[None, :]])
     h = np.concatenate([np.zeros(act.size), [1.0]])
-    c = np.concatenate([np.ones(nb), -lp.lower[gel], [B]])      # minimise -(obj - B t)
-    res = linprog(c, A_ub=G, b_ub=h, bounds=[(0, None)] * (nb + ng + 1), method="highs")
+    c = np.concatenate([U, -lp.lower[gel], [B]])      # minimise -(obj - B t)
+    res = linprog(c, A_ub=G, b_ub=h, bounds=[(0, None)] * (nu + ng + 1), method="highs")
     assert res.status == 0
     lu = np.zeros(lp.labels.size)
     ll = np.zeros(lp.labels.size)
-    lu[band] = res.x[:nb]
-    ll[gel] = res.x[nb:nb + ng]
+    lu[up] = res.x[:nu]
+    ll[gel] = res.x[nu:nu + ng]
     return -res.fun, lu, ll
 
 
@@ -259,6 +262,18 @@ def test_bound_certificate_is_sound_and_complete_on_tiny_lps():
     val, lu, ll = _best_certificate(lp, ops)
     assert val > 1e-3
     assert pdhg.certificate(lp, ops, lu, ll, *pdhg.certificate_data(lp, ops))
+
+
+@pytest.mark.parametrize("delta", [0.0, 0.05])
+def test_bound_certificate_cannot_fire_on_feasible_case1(delta):
+    """Case 1 (lam_up on gel rows, bound f~_U): on feasible LPs, down to the
+    equality case delta = 0, the best candidate HiGHS finds has
+    obj - B kappa <= 0 and the oracle's test rejects it."""
+    lp, ops = _tiny(CASE1, dict(tol_lo=delta, tol_hi=delta))
+    assert simplex.solve_dense(lp, ops)[0] == "optimal"
+    val, lu, ll = _best_certificate(lp, ops)
+    assert val <= 1e-9
+    assert not pdhg.certificate(lp, ops, lu, ll, *pdhg.certificate_data(lp, ops))
 
 
 def test_bound_certificate_detects_blurred_inhibition(monkeypatch):
