@@ -22,7 +22,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -105,11 +104,6 @@ def max_over_ranks(x: float, dist, device=None) -> float:
     return float(t.item())
 
 
-def replica_seed(base: int, rank: int) -> int:
-    """Each rank's independent replica uses the same seeded instance."""
-    return base
-
-
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
     """Samples nvidia-smi SM clocks and throttle reasons while active."""
@@ -173,7 +167,7 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- workload
-def make_workload(name: str, seed_offset: int = 0):
+def make_workload(name: str):
     from synthetic.targets import workload
     return workload(name)
 
@@ -202,7 +196,8 @@ def workload_config(wl, storage_name):
 def oracle_iteration_rate(wl, max_seconds: float = 20.0, nz_sample: int = 2):
     """Oracle PDHG iterations on `nz_sample` middle z-slices of the workload
     (the operator is slice-separable, so per-iteration work scales with nz),
-    scaled to the full nz.  Returns (iter/s at full size, sample description)."""
+    scaled to the full nz.  Returns (iter/s at full size, sample description,
+    seconds per sampled iteration, threads busy on average while timed)."""
     from oracle import pdhg
     from oracle.lp import CaseParams, build_lp
     from oracle.operators import Geometry
@@ -217,9 +212,9 @@ def oracle_iteration_rate(wl, max_seconds: float = 20.0, nz_sample: int = 2):
     t_setup = time.perf_counter() - t0
     iters = 2
     while True:
-        t0 = time.perf_counter()
+        t0, c0 = time.perf_counter(), time.process_time()
         pdhg.solve(lp, ops, kkt_tol=0.0, max_iter=iters, check_every=10 ** 9)
-        dt = time.perf_counter() - t0
+        dt, dc = time.perf_counter() - t0, time.process_time() - c0
         if dt * 2 > max_seconds or iters >= 64:
             break
         iters *= 2
@@ -228,12 +223,13 @@ def oracle_iteration_rate(wl, max_seconds: float = 20.0, nz_sample: int = 2):
     desc = (f"oracle restarted Halpern PDHG (numpy/scipy FP64, explicit sparse P^T) on {nz_sample} of "
             f"{wl.nz} z-slices for {iters} iterations ({dt:.1f} s, setup {t_setup:.1f} s), "
             f"per-iteration time scaled by nz/{nz_sample}")
-    return 1.0 / full, desc, per_iter
+    cores = max(1, round(dc / dt)) if dt > 0 else 1      # threads busy on average
+    return 1.0 / full, desc, per_iter, cores
 
 
 def cpu_baseline(wl, max_seconds=20.0):
-    rate, desc, _ = oracle_iteration_rate(wl, max_seconds)
-    return {"value": rate, "unit": "iter/s", "cores": 1, "kind": "oracle", "sample": desc}
+    rate, desc, _, cores = oracle_iteration_rate(wl, max_seconds)
+    return {"value": rate, "unit": "iter/s", "cores": cores, "kind": "oracle", "sample": desc}
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -476,13 +472,13 @@ def main(argv=None):
             return 0
         wl = make_workload(args.workload)
         t0 = time.perf_counter()
-        rate, desc, per_iter = oracle_iteration_rate(wl, args.cpu_seconds)
+        rate, desc, per_iter, cores = oracle_iteration_rate(wl, args.cpu_seconds)
         out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "iter/s",
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": 1e3 / rate, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                "config": workload_config(wl, "f64"),
-               "cpu_baseline": {"value": rate, "unit": "iter/s", "cores": 1, "kind": "oracle",
+               "cpu_baseline": {"value": rate, "unit": "iter/s", "cores": cores, "kind": "oracle",
                                 "sample": desc},
                "e2e": {"value": rate, "unit": "iter/s", "h2d_bytes_per_step": 0,
                        "d2h_bytes_per_step": 0},
