@@ -201,6 +201,7 @@ def oracle_iteration_rate(wl, max_seconds: float = 20.0, nz_sample: int = 2):
     from oracle import pdhg
     from oracle.lp import CaseParams, build_lp
     from oracle.operators import Geometry
+    nz_sample = min(nz_sample, wl.nz)
     z0 = wl.nz // 2 - nz_sample // 2
     tgt = np.ascontiguousarray(wl.target[:, :, z0:z0 + nz_sample])
     geo = Geometry(wl.n, wl.n, nz_sample, wl.angles, wl.n_det, vial_radius=wl.vial_radius,
