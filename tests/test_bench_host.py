@@ -37,3 +37,25 @@ def test_kernel_fingerprint_ignores_comments_only():
     assert bench._code_only(code) == "int a = 1;\nint b = 2;"
     assert bench._code_only(code.replace("// one", "// uno")) == bench._code_only(code)
     assert bench._code_only(code.replace("= 2", "= 3")) != bench._code_only(code)
+
+
+def test_reference_arm_prints_the_contract_line(capsys):
+    """bench.py --impl reference on the 64^2 disc workload: one JSON line with
+    the keys the benchmark contract names, the oracle as the CPU baseline and
+    an end-to-end block without host-device copies."""
+    import json
+    rc = bench.main(["--impl", "reference", "--workload", "disc64", "--cpu-seconds", "1",
+                     "--steps", "2", "--warmup", "3"])
+    assert rc == 0
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert "workload" in d["config"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
