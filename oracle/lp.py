@@ -1,5 +1,7 @@
 """Oracle LP data: domain partition, normalisation, residuals and metrics (FP64).
 
+Test infrastructure only (like the whole oracle package): never imported by the product path.
+
 Domain partition (Sec. 2.2, Fig. 2):
   gel  = {f_T != 0}
   band = non-gel voxels with K f_T != 0, or (reading, following the band width

@@ -1,5 +1,7 @@
 """Oracle forward model: P^T, P, attenuation and the PSF K (FP64, CPU).
 
+Test infrastructure only (like the whole oracle package): never imported by the product path.
+
 Forward model (Sec. 2.3, Eqs. 2-3): the dose is f = A^T g with A^T = K P^T,
 where P^T backprojects a sinogram g into object space and K is the object-space
 PSF.  P is the adjoint of P^T (Sec. 2.3), and A = P K^T = P K (K symmetric).

@@ -1,5 +1,7 @@
 """Oracle restarted Halpern PDHG for the SiPO LP (FP64, CPU, explicit sparse A).
 
+Test infrastructure only (like the whole oracle package): never imported by the product path.
+
 The paper solves the LP with a matrix-free primal-dual hybrid gradient method
 driven by the KKT conditions (Sec. 2.8, Sec. 6.1) and gives no further recipe.
 The readings implemented here (and by the GPU solver) are published methods:

@@ -1,5 +1,7 @@
 """Single-output evaluation of the oracle operators at full size (FP64).
 
+Test infrastructure only (like the whole oracle package): never imported by the product path.
+
 At 256^3 x 360 views the explicit matrices are too large for quick tests, but
 any one output of P^T, P or K is a short sum that follows directly from the
 definitions in `operators` (Sec. 2.3, Eqs. 2-3): these functions compute that

@@ -1,5 +1,7 @@
 """Dense two-phase tableau simplex with Bland's rule (oracle, tiny LPs only).
 
+Test infrastructure only (like the whole oracle package): never imported by the product path.
+
 Used to pin the PDHG oracle: on tiny instances the LP of Eqs. 19-24
 (general), 32-37 (Case 1) or 40-45 (Case 2) is written out as a dense matrix
 and solved exactly (up to rounding) by the textbook simplex method.  Bland's
