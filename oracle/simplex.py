@@ -20,6 +20,7 @@ from .operators import Operators
 
 TOL = 1e-10
 PIVOT_TOL = 1e-9
+FEAS_TOL = 1e-9
 
 
 def _pivot(T, basis, r, c):
@@ -84,11 +85,13 @@ def simplex_ineq(G, h, c, max_iter=200000):
         _run(T, basis, cost1, np.ones(ntot, dtype=bool), max_iter)
         if T[:, -1] @ cost1[basis] > 1e-9 * max(1.0, np.abs(h).max()):
             return "infeasible", None, None
+        # an artificial still basic (at level zero) leaves through the largest
+        # entry of its row; a row with no usable entry is redundant and keeps it
         for r in range(m):
             if basis[r] >= n + m:
-                nz = np.flatnonzero(np.abs(T[r, :n + m]) > 1e-9)
-                if nz.size:
-                    _pivot(T, basis, r, nz[0])
+                j = int(np.argmax(np.abs(T[r, :n + m])))
+                if abs(T[r, j]) > 1e-9:
+                    _pivot(T, basis, r, j)
     cost2 = np.zeros(ntot + 1)
     cost2[:n] = c
     allowed = np.zeros(ntot, dtype=bool)
@@ -98,6 +101,12 @@ def simplex_ineq(G, h, c, max_iter=200000):
         return status, None, None
     x = np.zeros(ntot)
     x[basis] = T[:, -1]
+    # The tableau carries the rounding of every pivot; a pivot on a near-zero
+    # entry can push the vertex off the feasible set, and such a vertex is not
+    # an optimum: refuse it rather than report its objective.
+    scale = max(1.0, np.abs(h).max())
+    if x.min() < -FEAS_TOL * scale or (G @ x[:n] - h).max() > FEAS_TOL * scale:
+        raise RuntimeError("simplex lost primal feasibility")
     return "optimal", x[:n], float(c @ x[:n])
 
 

@@ -1,7 +1,7 @@
 """Seeded synthetic targets and geometries for the SiPO projection LP.
 
-This module only draws shapes: binary target dose fields f_T (1 inside the
-part, 0 outside) and angle lists. It holds none of the method's arithmetic
+This module only draws shapes: target dose fields f_T (binary: 1 inside the
+part, 0 outside; or graded: one prescribed level per part) and angle lists. It holds none of the method's arithmetic
 (no projector, no LP, no solver), so both the CPU oracle and the CUDA path may
 consume what it produces.
 
@@ -11,7 +11,9 @@ slice is the same with nz = 1.  Voxel centres sit at i - (n - 1)/2.
 
 The paper measures on a binary logo (Sec. 3.1) and a 3-D "Thinker" model
 (Sec. 3.4), neither of which is available; these generators stand in for them
-with binary parts of matched scale.
+with binary parts of matched scale.  The grayscale experiment of Sec. 3.3
+(one response level per character of the logo) is stood in for by discs with
+one level each.
 """
 from __future__ import annotations
 
@@ -23,6 +25,7 @@ import numpy as np
 __all__ = [
     "uniform_angles",
     "discs_2d",
+    "graded_discs_2d",
     "csg_3d",
     "lattice_3d",
     "Workload",
@@ -58,6 +61,28 @@ def discs_2d(n: int = 64, n_discs: int = 3, r_range=(6.0, 14.0),
         cx, cy = rho * math.cos(phi), rho * math.sin(phi)
         f |= (xx - cx) ** 2 + (yy - cy) ** 2 <= r * r
     return f.astype(np.float32)[:, :, None].copy()
+
+
+def graded_discs_2d(n: int = 64, levels=(1.0, 0.7, 0.45), r_range=(6.0, 14.0),
+                    container_radius: float = 28.0, seed: int = 1) -> np.ndarray:
+    """Discs with one prescribed level each (a multi-level grayscale target),
+    returned as [n][n][1] float32.
+
+    Disc k has level levels[k] and is placed like a disc of `discs_2d`; where
+    discs overlap the later one wins, so every gel voxel carries exactly one
+    of the levels.
+    """
+    rng = np.random.default_rng(seed)
+    c = _centred(n)
+    yy, xx = np.meshgrid(c, c, indexing="ij")
+    f = np.zeros((n, n), dtype=np.float32)
+    for level in levels:
+        r = rng.uniform(*r_range)
+        rho = (container_radius - r) * math.sqrt(rng.uniform())
+        phi = rng.uniform(0.0, 2.0 * math.pi)
+        cx, cy = rho * math.cos(phi), rho * math.sin(phi)
+        f[(xx - cx) ** 2 + (yy - cy) ** 2 <= r * r] = np.float32(level)
+    return f[:, :, None].copy()
 
 
 def _random_unit(rng) -> np.ndarray:

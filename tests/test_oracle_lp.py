@@ -18,7 +18,7 @@ from oracle import pdhg, simplex
 from oracle.lp import (BAND, CASE1, CASE2, EXT, GEL, GENERAL, CaseParams, build_lp,
                        metrics, partition)
 from oracle.operators import Geometry
-from synthetic.targets import discs_2d, uniform_angles
+from synthetic.targets import discs_2d, graded_discs_2d, uniform_angles
 
 TINY = [
     (GENERAL, {}),
@@ -142,6 +142,119 @@ def test_pdhg_matches_highs_on_small_slice(case, extra):
     res = pdhg.solve(lp, ops, kkt_tol=1e-8, max_iter=40000)
     assert res["status"] == pdhg.OPTIMAL
     assert abs(res["obj"] - ref.fun) <= 1e-6 * abs(ref.fun)
+
+
+def _physical_highs(f_T, case, extra, ops, labels, active):
+    """The projection LP written in dose units straight from the case
+    definitions (Sec. 2.6.2 general form, Sec. 2.7.1 Case 1, Sec. 2.7.2 Case 2),
+    with none of the oracle's normalisation by f_crit:
+
+    - general: min w1 u + w2 v, f_T <= f <= v f_T on gel, f <= u min f_T on band;
+    - Case 1:  min u, (1 - d_lo) f_T <= f <= (1 + d_hi) f_T on gel,
+               f <= u (1 - d_lo) min f_T on band;
+    - Case 2:  min v, f_T <= f <= v f_T on gel, f <= r min f_T on band;
+
+    with f = P^T y over the active rays and y >= 0.  The objective is a ratio
+    of doses, so it equals the normalised LP's optimum (Sec. 2.5)."""
+    fT = np.asarray(f_T, np.float64).ravel()
+    act = np.flatnonzero(active)
+    M = ops.PT[:, act]
+    gel, band = np.flatnonzero(labels == GEL), np.flatnonzero(labels == BAND)
+    fmin = fT[gel].min()
+    ny, nb, ng = act.size, band.size, gel.size
+    if case == CASE1:
+        lo, hi = (1 - extra["tol_lo"]) * fT[gel], (1 + extra["tol_hi"]) * fT[gel]
+        scale_u = (1 - extra["tol_lo"]) * fmin
+    else:
+        lo, hi = fT[gel], None
+        scale_u = fmin
+    # columns: y (ny), u, v
+    col = lambda vals, n: sp.csr_matrix((vals, (np.arange(n), np.zeros(n, int))), shape=(n, 1))
+    zb, zg = sp.csr_matrix((nb, 1)), sp.csr_matrix((ng, 1))
+    if case == CASE2:
+        band_blk = sp.hstack([M[band], zb, zb])
+        band_rhs = np.full(nb, extra["inhibit_ratio"] * fmin)
+    else:
+        band_blk = sp.hstack([M[band], col(-np.full(nb, scale_u), nb), zb])
+        band_rhs = np.zeros(nb)
+    if case == CASE1:
+        up_blk, up_rhs = sp.hstack([M[gel], zg, zg]), hi
+    else:
+        up_blk, up_rhs = sp.hstack([M[gel], zg, col(-fT[gel], ng)]), np.zeros(ng)
+    G = sp.vstack([band_blk, up_blk, sp.hstack([-M[gel], zg, zg])]).tocsr()
+    h = np.concatenate([band_rhs, up_rhs, -lo])
+    c = np.zeros(ny + 2)
+    if case == GENERAL:
+        c[ny], c[ny + 1] = 1.0, 1.0
+    elif case == CASE1:
+        c[ny] = 1.0
+    else:
+        c[ny + 1] = 1.0
+    bounds = [(0, None)] * ny + [(0, None) if case != CASE2 else (0, 0),
+                                 (0, None) if case != CASE1 else (0, 0)]
+    return linprog(c, A_ub=G, b_ub=h, bounds=bounds, method="highs")
+
+
+# (levels, seed, case, params): one response level per disc; the Case-2 ratio
+# sits below the instance's feasibility threshold (about 0.80 for the first
+# target, 0.95 for the second).
+GRAY = [((1.0, 0.85, 0.7), 4, GENERAL, {}),
+        ((1.0, 0.85, 0.7), 4, CASE1, dict(tol_lo=0.1, tol_hi=0.1)),
+        ((1.0, 0.85, 0.7), 4, CASE2, dict(inhibit_ratio=0.9)),
+        ((1.0, 0.6, 0.8), 5, GENERAL, {}),
+        ((1.0, 0.6, 0.8), 5, CASE1, dict(tol_lo=0.1, tol_hi=0.1)),
+        ((1.0, 0.6, 0.8), 5, CASE2, dict(inhibit_ratio=1.0))]
+
+
+def _gray(levels, seed, case, extra):
+    tgt = graded_discs_2d(10, levels=levels, r_range=(1.5, 3.0), container_radius=4.0, seed=seed)
+    geo = Geometry(10, 10, 1, uniform_angles(8), 15)
+    lp, ops = build_lp(geo, tgt, CaseParams(case=case, band_width=2, **extra))
+    return tgt, lp, ops
+
+
+@pytest.mark.parametrize("levels,seed,case,extra", GRAY)
+def test_grayscale_target_matches_dose_unit_lp(levels, seed, case, extra):
+    """Multi-level targets (Sec. 3.3: one prescribed level per part): HiGHS on
+    the oracle's normalised LP and on the LP written in dose units from the
+    definitions give one optimum, and the oracle PDHG reaches it.  A
+    normalisation that treated the target as binary, or divided by the wrong
+    f_crit, moves the first away from the second."""
+    tgt, lp, ops = _gray(levels, seed, case, extra)
+    assert np.unique(lp.ft[lp.gel]).size == 3
+    ref = _physical_highs(tgt, case, extra, ops, lp.labels, lp.active)
+    assert ref.status == 0
+    nrm = _highs(lp, ops)
+    assert nrm.status == 0
+    assert abs(nrm.fun - ref.fun) <= 1e-9 * abs(ref.fun)
+    res = pdhg.solve(lp, ops, kkt_tol=1e-10, max_iter=80000)
+    assert res["status"] == pdhg.OPTIMAL
+    assert abs(res["obj"] - ref.fun) <= 1e-8 * abs(ref.fun)
+    assert abs(metrics(lp, res["d"])["s"] - 1.0) < 1e-7
+
+
+def test_grayscale_case2_below_threshold_is_infeasible():
+    """Below the feasibility threshold both LP forms are infeasible for HiGHS
+    and the oracle PDHG reports Case 2 infeasible on the multi-level target."""
+    extra = dict(inhibit_ratio=0.7)
+    tgt, lp, ops = _gray((1.0, 0.85, 0.7), 4, CASE2, extra)
+    assert _physical_highs(tgt, CASE2, extra, ops, lp.labels, lp.active).status == 2
+    assert _highs(lp, ops).status == 2
+    res = pdhg.solve(lp, ops, kkt_tol=1e-9, max_iter=40000)
+    assert res["status"] == pdhg.PRIMAL_INFEASIBLE
+
+
+def test_simplex_refuses_a_vertex_off_the_feasible_set():
+    """On a multi-level target a pivot on a near-zero tableau entry drives the
+    dense simplex off the feasible set; it must raise, not report that
+    vertex's objective as the optimum (HiGHS gives the true one)."""
+    _, lp, ops = _gray((1.0, 0.6, 0.8), 5, GENERAL, {})
+    try:
+        st, obj, _ = simplex.solve_dense(lp, ops)
+    except RuntimeError as e:
+        assert "feasibility" in str(e)
+        return
+    assert abs(obj - _highs(lp, ops).fun) <= 1e-8 * abs(obj)
 
 
 def test_scale_invariance_bitwise_and_general():
