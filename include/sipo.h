@@ -183,6 +183,22 @@ int sipo_solve(sipo_ctx *ctx, void *y_out, int y_location, sipo_result *res);
  * problems, src never solved), CUDA. */
 int sipo_warm_start(sipo_ctx *dst, const sipo_ctx *src);
 
+/* Primal start, for the two-stage design of Sec. 3.2 (a Case-1 solve fixes
+ * the process bound, a Case-2 solve at that bound then recovers conformity,
+ * starting from the Case-1 point rescaled).  The next sipo_solve or
+ * sipo_solve_batched of `ctx` starts from the primal point y, a normalised
+ * projection as sipo_solve returns it ([n_angles][n_det][nz], FP32, or FP64
+ * when storage is SIPO_F64, host or device per y_location, read before the
+ * call returns), instead of from zero.  y is projected onto the primal domain
+ * (negative, NaN and inactive-ray values become 0).  u and v are u~ (general,
+ * Case 1) and v~ (general, Case 2); a negative or non-finite value asks for
+ * the smallest the point allows (u~ = max of A^T y on band rows, v~ = max of
+ * A^T y / f~ on gel rows and at least 1); the one a case lacks is ignored.
+ * Duals start at zero, the primal weight at its default, and the point is
+ * both iterate and restart anchor.  Synchronises ctx's stream.  Errors:
+ * INVALID_ARG (null, bad location), CUDA. */
+int sipo_set_primal(sipo_ctx *ctx, const void *y, int y_location, double u, double v);
+
 /* Solves n independent contexts as one batch (a parameter sweep): one CUDA
  * graph holds one check period of every context as parallel branches (each on
  * its context's stream), so small LPs share the device and the host waits

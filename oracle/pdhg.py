@@ -187,11 +187,32 @@ def certificate(lp: LPData, ops: Operators, dlam_up, dlam_lo, b, B) -> bool:
     return kappa * B <= (1.0 - CERT_MARGIN) * obj
 
 
+def primal_start(lp: LPData, ops: Operators, y, u=None, v=None):
+    """A caller's primal point made admissible as a starting point: y projected
+    onto y >= 0 on the active rays and 0 elsewhere (the primal domain of
+    Eqs. 23-24); u~ and v~ as given when admissible (u~ >= 0, v~ >= 1), else
+    the smallest values the point allows: u~ = max of A^T y over band rows,
+    v~ = max of A^T y / f~ over gel rows (the band and gel upper rows of
+    Eqs. 20-21, 33-34, 41-42), clamped to the implied bounds u~ >= 0, v~ >= 1.
+    Returns (y, u, v)."""
+    y = np.where(lp.active & (np.asarray(y, np.float64).ravel() > 0), np.asarray(y, np.float64).ravel(), 0.0)
+    d = ops.AT(y.reshape(ops.geo.sino_shape)).ravel()
+    if lp.has_u and not (u is not None and math.isfinite(u) and u >= 0):
+        u = max(0.0, float(d[lp.band].max(initial=0.0)))
+    if lp.has_v and not (v is not None and math.isfinite(v) and v >= 1):
+        gel = lp.gel
+        v = max(1.0, float(np.max(d[gel] / lp.ft[gel])))
+    return y, (float(u) if lp.has_u else 0.0), (float(v) if lp.has_v else 1.0)
+
+
 def solve(lp: LPData, ops: Operators, kkt_tol=1e-4, max_iter=10000,
-          check_every=64, omega0=None, verbose=False, history=None):
+          check_every=64, omega0=None, verbose=False, history=None, start=None):
     """Run the restarted Halpern PDHG; returns a dict with status, T(z) and KKT data.
 
     `iters` counts PDHG steps; the returned point is T(z) at the last check.
+    `start` = (y, u, v) starts from that primal point (made admissible by
+    `primal_start`; None entries for u, v ask for the smallest admissible)
+    with zero duals, instead of from y = 0, u~ = 0, v~ = 1.
     """
     geo = ops.geo
     pc = Preconditioner(lp, ops)
@@ -215,6 +236,8 @@ def solve(lp: LPData, ops: Operators, kkt_tol=1e-4, max_iter=10000,
 
     cert = certificate_data(lp, ops)
     y, u, v = np.zeros(S), 0.0, 1.0
+    if start is not None:
+        y, u, v = primal_start(lp, ops, *start)
     lam_up, lam_lo = np.zeros(V), np.zeros(V)
     y0, u0, v0, lam_up0, lam_lo0 = y.copy(), u, v, lam_up.copy(), lam_lo.copy()
     g0 = np.zeros(S)

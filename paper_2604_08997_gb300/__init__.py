@@ -10,12 +10,13 @@ from ._abi import (SIPO_BF16, SIPO_CASE1, SIPO_CASE2, SIPO_F32, SIPO_F64, SIPO_G
                    load, sipo_backproject, sipo_create, sipo_destroy, sipo_get_array,
                    sipo_kernel_launch_count, sipo_profile, sipo_project, sipo_psf_apply,
                    sipo_psf_grad, sipo_set_psf_sigma, sipo_set_tolerances, sipo_get_trace, sipo_solve,
-                   sipo_solve_batched, sipo_warm_start)
+                   sipo_set_primal, sipo_solve_batched, sipo_warm_start)
 from .build import build
+from .two_stage import two_stage_solve
 
 __all__ = [
     "build", "load", "Context", "SipoError", "sipo_create", "sipo_solve", "sipo_solve_batched",
-    "sipo_warm_start",
+    "sipo_warm_start", "sipo_set_primal", "two_stage_solve",
     "sipo_project", "sipo_backproject", "sipo_psf_apply", "sipo_psf_grad", "sipo_set_psf_sigma",
     "sipo_get_array", "sipo_set_tolerances", "sipo_get_trace", "sipo_profile", "sipo_kernel_launch_count", "sipo_destroy",
     "SIPO_F32", "SIPO_F64", "SIPO_BF16", "SIPO_GENERAL", "SIPO_CASE1", "SIPO_CASE2",

@@ -71,6 +71,7 @@ SIGNATURES = {
     "sipo_solve_batched": (c_int, [POINTER(c_void_p), c_int, POINTER(c_void_p), c_int,
                                    POINTER(sipo_result)]),
     "sipo_warm_start": (c_int, [c_void_p, c_void_p]),
+    "sipo_set_primal": (c_int, [c_void_p, c_void_p, c_int, c_double, c_double]),
     "sipo_project": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     "sipo_backproject": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     "sipo_psf_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
@@ -241,6 +242,14 @@ def sipo_solve(ctx: Context, y_out=None) -> dict:
 def sipo_warm_start(dst: Context, src: Context) -> None:
     """sipo_warm_start(dst, src): dst's next solve starts from src's last T(z)."""
     _check(load().sipo_warm_start(dst.handle, src.handle))
+
+
+def sipo_set_primal(ctx: Context, y, u: float = -1.0, v: float = -1.0) -> None:
+    """sipo_set_primal(ctx, y, location, u, v): ctx's next solve starts from
+    the primal point y (host or device, the compute dtype, [n_angles][n_det][nz])
+    with u~ = u, v~ = v (negative: the smallest the point allows) and zero duals."""
+    p, loc = _ptr(y)
+    _check(load().sipo_set_primal(ctx.handle, c_void_p(p), loc, float(u), float(v)))
 
 
 def sipo_solve_batched(ctxs, y_outs=None) -> list[dict]:

@@ -89,6 +89,8 @@ struct SolverBase {
   virtual int dev() const = 0;
   virtual std::vector<double> fingerprint() const = 0;
   virtual void warm_from(const SolverBase& src) = 0;
+  // start from a caller's primal point (y, u~, v~) with zero duals
+  virtual void primal_from(const void* y, int loc, double u, double v) = 0;
 };
 
 // Element conversion of n values of dtype `in_dtype` at `in` into `out`.
@@ -317,6 +319,66 @@ struct Solver final : SolverBase {
     ck(cudaMemcpyAsync(st, h_st, sizeof(Scal), cudaMemcpyHostToDevice, stream), "state");
     ck(cudaStreamSynchronize(stream), "warm start");
     count(7);
+    warm_pending = true;
+  }
+
+  // The next solve starts from a caller's primal point: y (compute type,
+  // [n_angles][n_det][nz]) projected onto y >= 0 and the active rays, the
+  // scalars u~ and v~ (a negative or non-finite value: the smallest the point
+  // allows, max of A^T y over band rows for u~ and max of A^T y / f~ over gel
+  // rows, at least 1, for v~), zero duals and the default primal weight.  The
+  // point becomes iterate and restart anchor, as after a restart.
+  void primal_from(const void* y_in, int loc, double u, double v) override {
+    init_state();
+    const Geo<C> g = geo();
+    const Bufs<S, C> B = bufs();
+    // gp (zero at a start) holds the caller's values until they are projected
+    ck(cudaMemcpyAsync(gp, y_in, SN * sizeof(C), loc == SIPO_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                       stream), "primal start");
+    k_import_primal<S, C><<<grid_for((long long)SN), kThreads, 0, stream>>>(gp, col, yp, (long long)SN);
+    zero(gp, SN);
+    // d = A^T y with the operator of a check step's plain backprojection
+    launch_backproject<S, S, C, kBpStore, C>(g, yp, B, psf ? braw : dp, need, zl, stream, bp_nv);
+    if (psf) psf3<C, C>(braw, dp, t1, t2, -1, stream);
+    count(3);
+    const bool need_u = has_u && !(u >= 0.0 && std::isfinite(u));
+    const bool need_v = has_v && !(v >= 1.0 && std::isfinite(v));
+    if (need_u || need_v) {
+      k_metrics<C><<<kRedBlocks, kThreads, 0, stream>>>(dp, lab, fT, ft_is_const ? nullptr : ft, ft_const, f_crit,
+                                                       (long long)V, part);
+      count(1);
+      std::vector<double> hp(8 * size_t(kRedBlocks));
+      ck(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, stream), "start");
+      ck(cudaStreamSynchronize(stream), "primal start");
+      double mx_band = 0.0, mx_gel = 1.0;
+      for (int b = 0; b < kRedBlocks; ++b) {
+        mx_band = std::max(mx_band, hp[2 * kRedBlocks + b]);
+        mx_gel = std::max(mx_gel, hp[7 * kRedBlocks + b]);
+      }
+      if (need_u) u = mx_band;
+      if (need_v) v = mx_gel;
+      zero(part, size_t(kNumSlots) * kRedBlocks);
+    }
+    Scal h = *h_st;
+    if (has_u) h.u = h.u0 = h.up = u;
+    if (has_v) h.v = h.v0 = h.vp = v;
+    h.restart = 1;
+    *h_st = h;
+    ck(cudaMemcpyAsync(st, h_st, sizeof(Scal), cudaMemcpyHostToDevice, stream), "state");
+    ck(cudaStreamSynchronize(stream), "primal start");
+    const long long nvv = (long long)(V / ze), nvs = (long long)(SN / ze);
+    if (ze > 1) {
+      k_blend_sino<S, C, z_group<C>()><<<grid_for(nvs), kThreads, 0, stream>>>(B, nvs);
+      k_blend_vol<S, C, z_group<C>()><<<kRedBlocks, kThreads, 0, stream>>>(B, nvv);
+    } else {
+      k_blend_sino<S, C, 1><<<grid_for(nvs), kThreads, 0, stream>>>(B, nvs);
+      k_blend_vol<S, C, 1><<<kRedBlocks, kThreads, 0, stream>>>(B, nvv);
+    }
+    count(2);
+    h.restart = 0;
+    *h_st = h;
+    ck(cudaMemcpyAsync(st, h_st, sizeof(Scal), cudaMemcpyHostToDevice, stream), "state");
+    ck(cudaStreamSynchronize(stream), "primal start");
     warm_pending = true;
   }
 
@@ -1226,6 +1288,15 @@ int sipo_warm_start(sipo_ctx* dst, const sipo_ctx* src) {
   if (!dst || !src) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
   if (dst == src) sipo::fail(SIPO_ERR_INVALID_ARG, "warm start: source and destination are the same context");
   dst->c.s->warm_from(*src->c.s);
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
+int sipo_set_primal(sipo_ctx* ctx, const void* y, int y_location, double u, double v) {
+  SIPO_TRY
+  if (!ctx || !y) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
+  if (y_location != SIPO_HOST && y_location != SIPO_DEVICE) sipo::fail(SIPO_ERR_INVALID_ARG, "bad location");
+  ctx->c.s->primal_from(y, y_location, u, v);
   return SIPO_OK;
   SIPO_CATCH
 }

@@ -166,6 +166,19 @@ __global__ void k_convert(const TI* __restrict__ in, TO* __restrict__ out, long 
     out[i] = from_c<TO>(to_c(in[i]));
 }
 
+// A caller's primal point projected onto the primal domain of Eqs. 23-24:
+// y >= 0 on active rays (positive column sum), 0 on the others.  A NaN
+// fails the comparison and is dropped like a negative value.
+template <typename S, typename C>
+__global__ void k_import_primal(const C* __restrict__ in, const C* __restrict__ col, S* __restrict__ out,
+                                long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const C v = in[i];
+    out[i] = from_c<S>(col[i] > C(0) && v > C(0) ? v : C(0));
+  }
+}
+
 // Indicator volume 1_band + 2 * 1_gel (column abs-sums of G, Pock-Chambolle).
 template <typename C>
 __global__ void k_row_indicator(const uint8_t* __restrict__ lab, C* __restrict__ out, long long n) {

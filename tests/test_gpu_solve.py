@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 from oracle import pdhg, simplex
 from oracle.lp import CaseParams, build_lp, kkt, metrics
 from oracle.operators import Geometry
-from synthetic.targets import csg_3d, discs_2d, uniform_angles, workload
+from synthetic.targets import csg_3d, discs_2d, graded_discs_2d, uniform_angles, workload
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
@@ -91,25 +91,32 @@ def test_fp64_iterates_track_the_oracle(sipo, case, extra):
         assert abs(a - b) <= 1e-7 * max(abs(b), 1e-3), (key, a, b)
 
 
-def _layered_target(n, nz):
+def _layered_target(n, nz, graded=False):
     """Per-slice disc targets that change along z, so a mix-up of z values
-    between lanes or 16-byte groups changes the result."""
+    between lanes or 16-byte groups changes the result; `graded` gives each
+    slice's discs their own levels (a multi-level target, Sec. 3.3)."""
     t = np.empty((n, n, nz), np.float32)
     for z in range(nz):
-        t[:, :, z] = discs_2d(n, n_discs=1, r_range=(1.5, 3.0), container_radius=4.0, seed=z % 7)[:, :, 0]
+        if graded:
+            lv = (1.0, 0.85, 0.7) if z % 2 else (0.8, 1.0)
+            t[:, :, z] = graded_discs_2d(n, levels=lv, r_range=(1.5, 3.0), container_radius=4.0,
+                                         seed=z % 7)[:, :, 0]
+        else:
+            t[:, :, z] = discs_2d(n, n_discs=1, r_range=(1.5, 3.0), container_radius=4.0, seed=z % 7)[:, :, 0]
     return t
 
 
-@pytest.mark.parametrize("storage,nz,iters,rtol,atol", [("f64", 128, 320, 1e-7, 1e-10),
-                                                        ("f32", 256, 64, 1e-4, 1e-5)])
-def test_deep_z_solve_tracks_the_oracle(sipo, storage, nz, iters, rtol, atol):
+@pytest.mark.parametrize("storage,nz,iters,rtol,atol,graded", [("f64", 128, 320, 1e-7, 1e-10, False),
+                                                               ("f32", 256, 64, 1e-4, 1e-5, False),
+                                                               ("f64", 128, 320, 1e-7, 1e-10, True)])
+def test_deep_z_solve_tracks_the_oracle(sipo, storage, nz, iters, rtol, atol, graded):
     """The fused solver kernels with two 16-byte groups per lane (FP64 at
     nz = 128, FP32 at nz = 256) against the FP64 oracle PDHG.  FP32 iterates
     differ from FP64 ones by rounding (~1e-7 relative per step), so the FP32
     case runs one check period and allows 1e-4 relative plus 1e-5 absolute on
     the (already normalised) residuals."""
     n, na, nd = 10, 8, 15
-    tgt = _layered_target(n, nz)
+    tgt = _layered_target(n, nz, graded)
     ang = uniform_angles(na)
     cp = dict(kase=2, inhibit_ratio=0.6, band_width=2)
     lp, ops = build_lp(Geometry(n, n, nz, ang, nd), tgt, CaseParams(case=2, inhibit_ratio=0.6, band_width=2))
@@ -123,6 +130,32 @@ def test_deep_z_solve_tracks_the_oracle(sipo, storage, nz, iters, rtol, atol):
     for key in ("pobj", "dobj", "rel_primal", "rel_dual"):
         a, b = res[key], ref["info"][key]
         assert abs(a - b) <= rtol * abs(b) + atol, (key, a, b)
+
+
+GRAY = [(0, {}), (1, dict(tol_lo=0.1, tol_hi=0.1)), (2, dict(inhibit_ratio=0.9))]
+
+
+@pytest.mark.parametrize("case,extra", GRAY)
+def test_grayscale_target_reaches_the_oracle_optimum(sipo, case, extra):
+    """A multi-level target (one level per disc, Sec. 3.3) puts a per-voxel
+    normalised profile f~ into every solver kernel; the GPU solves in FP64 and
+    FP32 reach the oracle PDHG's optimum (the oracle's own value is pinned to
+    HiGHS on the dose-unit LP by the CPU tests)."""
+    n, na, nd = 10, 8, 15
+    tgt = graded_discs_2d(n, levels=(1.0, 0.85, 0.7), r_range=(1.5, 3.0), container_radius=4.0, seed=4)
+    ang = uniform_angles(na)
+    lp, ops = build_lp(Geometry(n, n, 1, ang, nd), tgt, CaseParams(case=case, band_width=2, **extra))
+    ref = pdhg.solve(lp, ops, kkt_tol=1e-10, max_iter=80000)
+    assert ref["status"] == pdhg.OPTIMAL
+    geo = dict(nx=n, ny=n, nz=1, angles=ang, n_det=nd)
+    cp = dict(kase=case, band_width=2, **extra)
+    for storage, tol, rel in ((sipo.SIPO_F64, 1e-10, 1e-7), (sipo.SIPO_F32, 1e-5, 1e-4)):
+        ctx = sipo.sipo_create(geo, tgt, cp, dict(storage=storage, kkt_tol=tol, max_iter=100000))
+        res = sipo.sipo_solve(ctx)
+        assert res["status"] == sipo.SIPO_OPTIMAL, (storage, res)
+        assert abs(res["pobj"] - ref["obj"]) <= rel * abs(ref["obj"]), (storage, res["pobj"], ref["obj"])
+        if storage == sipo.SIPO_F64:
+            assert abs(res["s"] - 1.0) < 1e-6
 
 
 def test_disc64_case1_fp64_to_1e6(sipo):
@@ -270,3 +303,71 @@ def test_bf16_escalated_to_fp32_reaches_the_target(sipo):
     assert rh["status"] == sipo.SIPO_OPTIMAL, rh
     assert abs(rh["pobj"] - ref["obj"]) <= 1e-3 * abs(ref["obj"])
     assert rh["kkt"] <= 1e-4 and rl["iters"] <= 1024
+
+
+def _stage1(graded):
+    """Case 1 (d = 0.1) solved by the oracle on the tiny binary or multi-level
+    disc target, and the Case-2 LP at the ratio r = u~* it fixes (Sec. 3.2)."""
+    n, na, nd = 10, 8, 15
+    if graded:
+        tgt = graded_discs_2d(n, levels=(1.0, 0.85, 0.7), r_range=(1.5, 3.0), container_radius=4.0, seed=4)
+    else:
+        tgt = discs_2d(n, n_discs=1, r_range=(2.0, 3.0), container_radius=4.0, seed=3)
+    ang = uniform_angles(na)
+    geom = Geometry(n, n, 1, ang, nd)
+    lp1, ops = build_lp(geom, tgt, CaseParams(case=1, band_width=2, tol_lo=0.1, tol_hi=0.1))
+    r1 = pdhg.solve(lp1, ops, kkt_tol=1e-11, max_iter=100000)
+    assert r1["status"] == pdhg.OPTIMAL
+    r = r1["u"]
+    lp2, _ = build_lp(geom, tgt, CaseParams(case=2, band_width=2, inhibit_ratio=r))
+    geo = dict(nx=n, ny=n, nz=1, angles=ang, n_det=nd)
+    return tgt, geo, ops, r1, r, lp2
+
+
+@pytest.mark.parametrize("graded", [False, True])
+def test_primal_start_tracks_the_oracle(sipo, graded):
+    """sipo_set_primal: the imported point is the oracle's projection of the
+    caller's values (exact in FP64), its dose A^T y agrees, and FP64 solves
+    from that start on both sides keep matching objectives, residuals and
+    restart counts for 320 iterations."""
+    tgt, geo, ops, r1, r, lp2 = _stage1(graded)
+    rng = np.random.default_rng(5)
+    y2 = r1["y"] / r
+    y2 = y2 + np.where(rng.uniform(size=y2.size) < 0.1, -0.05, 0.0)    # some negatives to project
+    ref_y, _, ref_v = pdhg.primal_start(lp2, ops, y2)
+    ref = pdhg.solve(lp2, ops, kkt_tol=0.0, max_iter=320, start=(y2, None, None))
+    cp = dict(kase=2, inhibit_ratio=r, band_width=2)
+    ctx = sipo.sipo_create(geo, tgt, cp, dict(storage=sipo.SIPO_F64, kkt_tol=0.0, max_iter=320))
+    sipo.sipo_set_primal(ctx, np.ascontiguousarray(y2))
+    got = np.empty_like(ref_y)
+    sipo.sipo_get_array(ctx, 2, got)
+    assert np.array_equal(got, ref_y)
+    dose = np.empty(lp2.labels.size)
+    sipo.sipo_get_array(ctx, 5, dose)
+    d_ref = ops.AT(ref_y.reshape(ops.geo.sino_shape)).ravel()
+    m = lp2.labels != 0
+    np.testing.assert_allclose(dose[m], d_ref[m], rtol=1e-12, atol=1e-13)
+    res = sipo.sipo_solve(ctx)
+    assert res["iters"] == 320 and res["restarts"] == ref["restarts"]
+    for key in ("pobj", "dobj", "rel_primal", "rel_dual"):
+        a, b = res[key], ref["info"][key]
+        assert abs(a - b) <= 1e-7 * max(abs(b), 1e-3), (key, a, b)
+
+
+def test_two_stage_solve_matches_the_oracle(sipo):
+    """two_stage_solve in FP64: stage 1 reaches the oracle's Case-1 optimum,
+    its ratio is that u~*, and stage 2, started from the rescaled stage-1
+    point, reaches the oracle's Case-2 optimum at that ratio, which is at
+    most (1 + d) / (1 - d)."""
+    tgt, geo, ops, r1, r, lp2 = _stage1(False)
+    ref2 = pdhg.solve(lp2, ops, kkt_tol=1e-10, max_iter=100000)
+    assert ref2["status"] == pdhg.OPTIMAL
+    tol = dict(storage=sipo.SIPO_F64, kkt_tol=1e-10, max_iter=100000)
+    out = sipo.two_stage_solve(geo, tgt, tol_lo=0.1, tol_hi=0.1, band_width=2, tolerances=tol)
+    s1, s2 = out["stage1"], out["stage2"]
+    assert s1["status"] == sipo.SIPO_OPTIMAL and s2 is not None
+    assert abs(s1["pobj"] - r1["obj"]) <= 1e-7 * abs(r1["obj"])
+    assert abs(out["ratio"] - r) <= 1e-7 * r
+    assert s2["status"] == sipo.SIPO_OPTIMAL
+    assert abs(s2["pobj"] - ref2["obj"]) <= 1e-6 * ref2["obj"]
+    assert s2["pobj"] <= 1.1 / 0.9 * (1 + 1e-7)

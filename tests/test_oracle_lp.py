@@ -257,6 +257,66 @@ def test_simplex_refuses_a_vertex_off_the_feasible_set():
     assert abs(obj - _highs(lp, ops).fun) <= 1e-8 * abs(obj)
 
 
+def _two_stage_instance(graded):
+    if graded:
+        tgt = graded_discs_2d(10, levels=(1.0, 0.85, 0.7), r_range=(1.5, 3.0), container_radius=4.0, seed=4)
+    else:
+        tgt = discs_2d(10, n_discs=1, r_range=(2.0, 3.0), container_radius=4.0, seed=3)
+    return tgt, Geometry(10, 10, 1, uniform_angles(8), 15)
+
+
+@pytest.mark.parametrize("graded", [False, True])
+def test_two_stage_case2_at_the_case1_bound(graded):
+    """Two-stage design (Sec. 3.2): the Case-1 optimum u~* fixes the inhibition
+    ratio r = u~* of a Case-2 solve.  The Case-1 point in Case-2 units,
+    y1 / r, satisfies every Case-2 row (gel d >= f~_T, band d <= 1), so the
+    Case-2 optimum v~* (HiGHS) is at most its spread, itself at most
+    (1 + d_hi) / (1 - d_lo); the oracle PDHG reaches v~* both from zero and
+    from that point (its primal start)."""
+    delta = 0.1
+    tgt, geo = _two_stage_instance(graded)
+    lp1, ops = build_lp(geo, tgt, CaseParams(case=CASE1, band_width=2, tol_lo=delta, tol_hi=delta))
+    r1 = pdhg.solve(lp1, ops, kkt_tol=1e-11, max_iter=100000)
+    assert r1["status"] == pdhg.OPTIMAL
+    ref1 = _highs(lp1, ops)
+    assert abs(r1["u"] - ref1.fun) <= 1e-8 * ref1.fun
+    r = r1["u"]
+    lp2, _ = build_lp(geo, tgt, CaseParams(case=CASE2, band_width=2, inhibit_ratio=r))
+    y2 = r1["y"] / r
+    d2 = ops.AT(y2.reshape(geo.sino_shape)).ravel()
+    assert d2[lp2.band].max() <= 1.0 + 1e-8
+    assert np.all(d2[lp2.gel] >= lp2.ft[lp2.gel] * (1.0 - 1e-8))
+    spread = float(np.max(d2[lp2.gel] / lp2.ft[lp2.gel]))
+    assert spread <= (1 + delta) / (1 - delta) * (1 + 1e-8)
+    ref2 = _highs(lp2, ops)
+    assert ref2.status == 0
+    assert ref2.fun <= spread * (1 + 1e-9)
+    _, u0, v0 = pdhg.primal_start(lp2, ops, y2)
+    assert abs(v0 - spread) <= 1e-12 * spread
+    for start in (None, (y2, None, None)):
+        res = pdhg.solve(lp2, ops, kkt_tol=1e-10, max_iter=100000, start=start)
+        assert res["status"] == pdhg.OPTIMAL
+        assert abs(res["obj"] - ref2.fun) <= 1e-8 * ref2.fun
+
+
+def test_primal_start_projects_onto_the_primal_domain():
+    """primal_start zeroes negative, NaN and inactive-ray entries and keeps the
+    rest; explicit admissible scalars are kept, inadmissible ones replaced by
+    the smallest admissible (v~ >= 1 and v~ f~ >= A^T y on gel)."""
+    tgt, geo = _two_stage_instance(False)
+    lp, ops = build_lp(geo, tgt, CaseParams(case=GENERAL, band_width=2))
+    rng = np.random.default_rng(7)
+    y = rng.normal(size=lp.active.size)
+    y[3] = np.nan
+    yp, u, v = pdhg.primal_start(lp, ops, y, 0.25, -1.0)
+    keep = lp.active & np.nan_to_num(y > 0)
+    assert np.array_equal(yp[keep], y[keep]) and np.all(yp[~keep] == 0.0)
+    assert u == 0.25
+    d = ops.AT(yp.reshape(geo.sino_shape)).ravel()
+    assert v >= 1.0 and np.all(d[lp.gel] <= v * lp.ft[lp.gel] * (1 + 1e-12))
+    assert v == 1.0 or np.any(np.isclose(d[lp.gel], v * lp.ft[lp.gel], rtol=1e-12))
+
+
 def test_scale_invariance_bitwise_and_general():
     """f_T -> 2^k f_T leaves the normalised LP and the iterates bitwise unchanged;
     a general factor leaves the optimum unchanged (Sec. 2.5, Eq. 18)."""
