@@ -161,6 +161,63 @@ int sipo_create(const sipo_geometry *geo, const float *f_T, int f_T_location,
                 const sipo_case_params *cp, const sipo_tolerances *tol,
                 void *stream, sipo_ctx **out);
 
+/* Case 1 with explicit per-voxel dose bounds (Sec. 2.7.1 with response-domain
+ * tolerances: f_L = M^-1(m_L), f_U = M^-1(m_U), Eq. 5, which are in general
+ * not proportional to f_T).  As sipo_create, plus f_L and f_U ([ny][nx][nz]
+ * float32, host or device per `location`, like f_T): the gel rows become
+ * f_L,i / f_crit <= [A^T y]_i <= f_U,i / f_crit with f_crit = min_gel f_L
+ * (the weakest admissible part).  f_T still defines the labels (gel =
+ * f_T > 0), the active rays and the dose metrics; case->kase must be
+ * SIPO_CASE1 and its tol_lo / tol_hi are not used.  Errors: as sipo_create,
+ * and INVALID_ARG where a gel voxel has f_L <= 0, f_U < f_L or a bound that
+ * is not finite. */
+int sipo_create_bounded(const sipo_geometry *geo, const float *f_T, const float *f_L, const float *f_U,
+                        int location, const sipo_case_params *cp, const sipo_tolerances *tol, void *stream,
+                        sipo_ctx **out);
+
+/* Material response model (Sec. 2.1): Richards' generalised logistic curve,
+ * Eq. 4, m = M(f) = alpha + (k - alpha) / [1 + exp(-beta (f - f0))]^(1/gamma),
+ * with lower and upper asymptotes alpha < k, growth rate beta > 0, shape
+ * gamma > 0 and location f0 (resin constants supplied by the caller). */
+typedef struct sipo_response {
+  double alpha, k, beta, gamma, f0;
+} sipo_response;
+
+/* Response-domain post-scaling and metrics of a solved dose (Sec. 2.7, Eq. 28
+ * with unit weights, Eq. 46).  alpha: the post-scaling factor used (physical
+ * dose = alpha * d with d the normalised dose A^T y*); phi: Phi_m(alpha);
+ * psr_m: min_gel M(alpha d) / max_band M(alpha d); dtvr_m and its two parts
+ * ratio_max / ratio_min: max and min over gel of M(alpha d_i) / m_T,i;
+ * m_band_max, m_gel_min: max over band and min over gel of M(alpha d). */
+typedef struct sipo_response_result {
+  double alpha, phi, psr_m, dtvr_m, ratio_min, ratio_max, m_band_max, m_gel_min;
+} sipo_response_result;
+
+/* Elementwise response map on the device, for the front end (target
+ * response to target dose, Eq. 5; tolerance bounds (1 -+ eps) m_T through
+ * `scale`) and for reading doses as responses (Eq. 4).  With v = scale * in:
+ * inverse = 0: out = M(v); inverse = 1: out = M^-1(v)
+ * = f0 - ln[((k - alpha) / (v - alpha))^gamma - 1] / beta for
+ * alpha < v < k, 0 for v <= alpha (no prescription: outside the part).
+ * in, out: n float32 device values (may alias); computed in FP64; enqueued on
+ * `stream` and synchronised.  Errors: INVALID_ARG (bad model, null, scale not
+ * finite, or, with inverse = 1, a value >= k or NaN: outside the invertible
+ * range; out is then written with 0 there), CUDA. */
+int sipo_response_map(const sipo_response *M, const float *in, float *out, long long n, double scale,
+                      int inverse, void *stream);
+
+/* Response-domain back end of ctx's last solve: m_T ([ny][nx][nz] float32,
+ * host or device per `location`, positive on gel) is the target response.
+ * alpha > 0 is used as the post-scaling factor; otherwise (0, negative or
+ * not finite) alpha minimises Phi_m(alpha) = sum_gel (M(alpha d_i) -
+ * m_T,i)^2 (Eq. 28, unit weights) by a grid search: 32 factors spaced
+ * geometrically from 1/16 to 16 times the dose-domain factor of Eq. 27, then
+ * six rounds of 32 linearly spaced factors between the best one's
+ * neighbours.  Synchronises ctx's stream.  Errors: INVALID_ARG (bad model,
+ * null, ctx not solved), CUDA. */
+int sipo_response_metrics(sipo_ctx *ctx, const sipo_response *M, const float *m_T, int location, double alpha,
+                          sipo_response_result *out);
+
 /* Runs the restarted Halpern PDHG (Sec. 2.8) from a zero start until the
  * KKT tolerance, a primal-infeasibility certificate or max_iter, then the
  * post-solve metrics.  y_out (nullable) receives y*, the normalised

@@ -26,8 +26,9 @@ bounds u~ >= 0 and v~ >= 1 are added (they cannot cut the optimum: A^T y >= 0
 and f~_T <= A^T y <= v~ f~_T on gel).
 
 Normalisation: general f_crit = min_gel f_T (Sec. 2.5); Case 1 f_L = (1-dl) f_T,
-f_U = (1+du) f_T, f_crit = min_gel f_L (Eq. 30); Case 2 f_crit = ratio *
-min_gel f_T (reading of the inhibition threshold).
+f_U = (1+du) f_T, or explicit per-voxel f_L, f_U (the response-domain bounds
+M^-1(m_L), M^-1(m_U) of Sec. 2.7.1), f_crit = min_gel f_L (Eq. 30); Case 2
+f_crit = ratio * min_gel f_T (reading of the inhibition threshold).
 """
 from __future__ import annotations
 
@@ -50,6 +51,8 @@ class CaseParams:
     tol_hi: float = 0.05        # Case 1: f_U = (1 + tol_hi) f_T
     inhibit_ratio: float = 0.8  # Case 2: f_crit = ratio * min_gel f_T
     band_width: int = 10        # voxels; < 0 means band-free
+    f_lower: np.ndarray | None = None  # Case 1 with explicit dose bounds f_L, f_U
+    f_upper: np.ndarray | None = None  # (e.g. M^-1 of response bounds, Sec. 2.7.1)
 
 
 EXT, BAND, GEL = 0, 1, 2
@@ -153,8 +156,14 @@ def build_lp(geo: Geometry, f_T: np.ndarray, cp: CaseParams,
         lower[gel] = ft[gel]
         c_u, c_v = cp.w1, cp.w2
     elif cp.case == CASE1:
-        fL = (1.0 - cp.tol_lo) * fT
-        fU = (1.0 + cp.tol_hi) * fT
+        if cp.f_lower is not None:
+            fL = np.asarray(cp.f_lower, dtype=np.float64).ravel()
+            fU = np.asarray(cp.f_upper, dtype=np.float64).ravel()
+            if not (np.all(fL[gel] > 0) and np.all(fU[gel] >= fL[gel])):
+                raise ValueError("explicit bounds need 0 < f_L <= f_U on gel")
+        else:
+            fL = (1.0 - cp.tol_lo) * fT
+            fU = (1.0 + cp.tol_hi) * fT
         f_crit = fL[gel].min()
         ft[gel] = fL[gel] / f_crit
         lower[gel] = ft[gel]

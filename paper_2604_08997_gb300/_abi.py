@@ -57,6 +57,21 @@ class sipo_result(Structure):
         return d
 
 
+class sipo_response(Structure):
+    """Richards' response curve (Eq. 4): alpha, k asymptotes, beta rate, gamma shape, f0 location."""
+    _fields_ = [("alpha", c_double), ("k", c_double), ("beta", c_double), ("gamma", c_double),
+                ("f0", c_double)]
+
+
+class sipo_response_result(Structure):
+    _fields_ = [("alpha", c_double), ("phi", c_double), ("psr_m", c_double), ("dtvr_m", c_double),
+                ("ratio_min", c_double), ("ratio_max", c_double), ("m_band_max", c_double),
+                ("m_gel_min", c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class SipoError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"sipo error {code}: {msg}")
@@ -70,6 +85,13 @@ SIGNATURES = {
     "sipo_solve": (c_int, [c_void_p, c_void_p, c_int, POINTER(sipo_result)]),
     "sipo_solve_batched": (c_int, [POINTER(c_void_p), c_int, POINTER(c_void_p), c_int,
                                    POINTER(sipo_result)]),
+    "sipo_create_bounded": (c_int, [POINTER(sipo_geometry), c_void_p, c_void_p, c_void_p, c_int,
+                                    POINTER(sipo_case_params), POINTER(sipo_tolerances), c_void_p,
+                                    POINTER(c_void_p)]),
+    "sipo_response_map": (c_int, [POINTER(sipo_response), c_void_p, c_void_p, c_longlong, c_double, c_int,
+                                  c_void_p]),
+    "sipo_response_metrics": (c_int, [c_void_p, POINTER(sipo_response), c_void_p, c_int, c_double,
+                                      POINTER(sipo_response_result)]),
     "sipo_warm_start": (c_int, [c_void_p, c_void_p]),
     "sipo_set_primal": (c_int, [c_void_p, c_void_p, c_int, c_double, c_double]),
     "sipo_project": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
@@ -183,16 +205,7 @@ class Context:
             pass
 
 
-def sipo_create(geometry: dict, f_T, case: dict, tolerances: dict, stream=None) -> Context:
-    """sipo_create(geo, f_T, location, case, tol, stream, &ctx).
-
-    geometry: nx, ny, nz, angles (radians), n_det, vial_radius, mu, psf_sigma
-    (x, y, z), psf_trunc.  f_T: float32 [ny][nx][nz] numpy array or torch
-    tensor (host or CUDA).  case: kase, w1, w2, tol_lo, tol_hi, inhibit_ratio,
-    band_width.  tolerances: kkt_tol, max_iter, check_every, storage, tile_cfg.
-    `stream` None: the context creates its own stream.
-    """
-    lib = load()
+def _marshal(geometry: dict, case: dict, tolerances: dict):
     ang = np.ascontiguousarray(np.asarray(geometry["angles"], dtype=np.float64))
     g = sipo_geometry()
     g.nx, g.ny, g.nz = int(geometry["nx"]), int(geometry["ny"]), int(geometry["nz"])
@@ -215,17 +228,92 @@ def sipo_create(geometry: dict, f_T, case: dict, tolerances: dict, stream=None) 
                          int(tolerances.get("storage", SIPO_F32)),
                          int(tolerances.get("tile_cfg", -1)),
                          float(tolerances.get("primal_weight", 0.0)))
-    if isinstance(f_T, np.ndarray) and f_T.dtype != np.float32:
-        raise TypeError("f_T must be float32")
-    ptr, loc = _ptr(f_T)
+    return g, ang, cp, tl
+
+
+def _volume(a, g, name):
+    if isinstance(a, np.ndarray) and a.dtype != np.float32:
+        raise TypeError(f"{name} must be float32")
     expect = g.nx * g.ny * g.nz
-    if int(np.prod(f_T.shape)) != expect:
-        raise ValueError(f"f_T has {int(np.prod(f_T.shape))} elements, geometry needs {expect}")
+    if int(np.prod(a.shape)) != expect:
+        raise ValueError(f"{name} has {int(np.prod(a.shape))} elements, geometry needs {expect}")
+    return _ptr(a)
+
+
+def sipo_create(geometry: dict, f_T, case: dict, tolerances: dict, stream=None) -> Context:
+    """sipo_create(geo, f_T, location, case, tol, stream, &ctx).
+
+    geometry: nx, ny, nz, angles (radians), n_det, vial_radius, mu, psf_sigma
+    (x, y, z), psf_trunc.  f_T: float32 [ny][nx][nz] numpy array or torch
+    tensor (host or CUDA).  case: kase, w1, w2, tol_lo, tol_hi, inhibit_ratio,
+    band_width.  tolerances: kkt_tol, max_iter, check_every, storage, tile_cfg.
+    `stream` None: the context creates its own stream.
+    """
+    lib = load()
+    g, ang, cp, tl = _marshal(geometry, case, tolerances)
+    ptr, loc = _volume(f_T, g, "f_T")
     out = c_void_p()
     st = c_void_p(0) if stream is None else _stream(stream)
     _check(lib.sipo_create(ctypes.byref(g), c_void_p(ptr), loc, ctypes.byref(cp),
                            ctypes.byref(tl), st, ctypes.byref(out)))
+    del ang
     return Context(out, (g.ny, g.nx, g.nz), (g.n_angles, g.n_det, g.nz), tl.storage)
+
+
+def sipo_create_bounded(geometry: dict, f_T, f_L, f_U, case: dict, tolerances: dict,
+                        stream=None) -> Context:
+    """sipo_create_bounded(geo, f_T, f_L, f_U, location, case, tol, stream, &ctx):
+    Case 1 with explicit per-voxel dose bounds f_L <= f_U on gel (all three
+    float32 [ny][nx][nz], on one side: host or CUDA)."""
+    lib = load()
+    g, ang, cp, tl = _marshal(geometry, dict(case, kase=SIPO_CASE1), tolerances)
+    pt, loc = _volume(f_T, g, "f_T")
+    pl, ll = _volume(f_L, g, "f_L")
+    pu, lu = _volume(f_U, g, "f_U")
+    if not (loc == ll == lu):
+        raise ValueError("f_T, f_L and f_U must all be on the host or all on the device")
+    out = c_void_p()
+    st = c_void_p(0) if stream is None else _stream(stream)
+    _check(lib.sipo_create_bounded(ctypes.byref(g), c_void_p(pt), c_void_p(pl), c_void_p(pu), loc,
+                                   ctypes.byref(cp), ctypes.byref(tl), st, ctypes.byref(out)))
+    del ang
+    return Context(out, (g.ny, g.nx, g.nz), (g.n_angles, g.n_det, g.nz), tl.storage)
+
+
+def _response(M) -> sipo_response:
+    if isinstance(M, sipo_response):
+        return M
+    if isinstance(M, dict):
+        return sipo_response(float(M["alpha"]), float(M["k"]), float(M["beta"]), float(M["gamma"]),
+                             float(M["f0"]))
+    return sipo_response(*[float(x) for x in M])
+
+
+def sipo_response_map(M, src, dst, inverse: bool, scale: float = 1.0, stream=None):
+    """dst = M(scale src) (Eq. 4) or, inverse, M^-1(scale src) (Eq. 5); float32 CUDA tensors."""
+    ps, ls = _ptr(src)
+    pd, ld = _ptr(dst)
+    if ls != SIPO_DEVICE or ld != SIPO_DEVICE:
+        raise ValueError("the response map takes device tensors")
+    if src.numel() != dst.numel() or str(src.dtype) != "torch.float32" or str(dst.dtype) != "torch.float32":
+        raise ValueError("src and dst must be float32 tensors of one size")
+    r = _response(M)
+    _check(load().sipo_response_map(ctypes.byref(r), c_void_p(ps), c_void_p(pd), int(src.numel()),
+                                    float(scale), 1 if inverse else 0, _stream(stream)))
+    return dst
+
+
+def sipo_response_metrics(ctx: Context, M, m_T, alpha: float = 0.0) -> dict:
+    """Response-domain post-scaling (Eq. 28; alpha <= 0: minimised) and metrics (Eq. 46)
+    of ctx's last solve; m_T float32 [ny][nx][nz], host or CUDA."""
+    p, loc = _ptr(m_T)
+    if isinstance(m_T, np.ndarray) and m_T.dtype != np.float32:
+        raise TypeError("m_T must be float32")
+    r = _response(M)
+    out = sipo_response_result()
+    _check(load().sipo_response_metrics(ctx.handle, ctypes.byref(r), c_void_p(p), loc, float(alpha),
+                                        ctypes.byref(out)))
+    return out.as_dict()
 
 
 def sipo_solve(ctx: Context, y_out=None) -> dict:

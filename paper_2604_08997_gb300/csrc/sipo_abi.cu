@@ -25,6 +25,7 @@
 #include "sipo_kernels.cuh"
 #include "sipo_launch.h"
 #include "sipo_ops.cuh"
+#include "sipo_response.cuh"
 
 namespace sipo {
 namespace {
@@ -53,7 +54,8 @@ int grid_for(long long n) {
 
 struct SolverBase {
   virtual ~SolverBase() {}
-  virtual void setup(const float* fT_dev) = 0;
+  // fL_dev, fU_dev (Case 1 with explicit bounds, else null): per-voxel dose bounds
+  virtual void setup(const float* fT_dev, const float* fL_dev, const float* fU_dev) = 0;
   virtual void begin_solve() = 0;
   virtual void launch_block(long long n) = 0;
   virtual void request_done() = 0;
@@ -91,6 +93,8 @@ struct SolverBase {
   virtual void warm_from(const SolverBase& src) = 0;
   // start from a caller's primal point (y, u~, v~) with zero duals
   virtual void primal_from(const void* y, int loc, double u, double v) = 0;
+  // response-domain post-scaling and metrics of the last solve's dose
+  virtual void response_metrics(const Richards& M, const float* mT, double alpha, sipo_response_result* out) = 0;
 };
 
 // Element conversion of n values of dtype `in_dtype` at `in` into `out`.
@@ -151,6 +155,8 @@ struct Solver final : SolverBase {
   int2* rspan = nullptr;  // per-ray walked span meeting columns in `need`
   NeedBits nbits{};      // `need` packed as bits for the projector
   C *ft = nullptr, *row = nullptr, *col = nullptr;
+  C* fu = nullptr;            // Case 1 with explicit bounds: f_U / f_crit on gel
+  double fu_sum = 0.0;        // sum_gel f~_U (fingerprint of explicit bounds)
   S *y = nullptr, *y0 = nullptr, *yp = nullptr, *ybar = nullptr;
   C *gp = nullptr, *g0 = nullptr, *gc = nullptr;
   S *lu = nullptr, *ll = nullptr, *lu0 = nullptr, *ll0 = nullptr, *lpu = nullptr, *lpl = nullptr;
@@ -275,7 +281,8 @@ struct Solver final : SolverBase {
     std::vector<double> f = {double(device), double(nx), double(ny), double(nz), double(na), double(nd),
                              double(cp.kase),
                              double(n_band), double(n_gel), f_crit, cp.tol_lo, cp.tol_hi,
-                             cp.inhibit_ratio, double(cp.band_width), psf ? 1.0 : 0.0};
+                             cp.inhibit_ratio, double(cp.band_width), psf ? 1.0 : 0.0,
+                             fu ? 1.0 : 0.0, fu_sum};
     f.insert(f.end(), angles.begin(), angles.end());
     return f;
   }
@@ -382,6 +389,87 @@ struct Solver final : SolverBase {
     warm_pending = true;
   }
 
+  // Response-domain back end of the last solve (Sec. 2.7: Eq. 28 with unit
+  // weights, Eq. 46): alpha > 0 is used as given; otherwise alpha minimises
+  // Phi_m(alpha) = sum_gel (M(alpha d_i) - m_T,i)^2 over a geometric grid of
+  // kPhiCand factors spanning 1/16 to 16 times the dose-domain factor of
+  // Eq. 27, refined six times on a linear grid between the neighbours of the
+  // best candidate (each round shrinks the bracket about 15-fold).
+  void response_metrics(const Richards& M, const float* mT_src, double alpha, sipo_response_result* out) override {
+    if (!solved) fail(SIPO_ERR_INVALID_ARG, "response metrics need a solved context");
+    float* mT = nullptr;
+    double *alphas = nullptr, *rp = nullptr;
+    const size_t np = size_t(kPhiCand) * kRedBlocks;
+    ck(cudaMallocAsync(reinterpret_cast<void**>(&mT), V * sizeof(float), stream), "response tmp");
+    ck(cudaMallocAsync(reinterpret_cast<void**>(&alphas), kPhiCand * sizeof(double), stream), "response tmp");
+    ck(cudaMallocAsync(reinterpret_cast<void**>(&rp), np * sizeof(double), stream), "response tmp");
+    ck(cudaMemcpyAsync(mT, mT_src, V * sizeof(float), cudaMemcpyDefault, stream), "copy m_T");
+    std::vector<double> a(kPhiCand), hp(np);
+    auto phi_round = [&](int& best, double& best_phi) {
+      ck(cudaMemcpyAsync(alphas, a.data(), kPhiCand * sizeof(double), cudaMemcpyHostToDevice, stream), "alphas");
+      k_response_phi<C><<<kRedBlocks, kThreads, 0, stream>>>(dp, lab, mT, M, alphas, (long long)V, rp);
+      count(1);
+      ck(cudaMemcpyAsync(hp.data(), rp, np * sizeof(double), cudaMemcpyDeviceToHost, stream), "phi");
+      ck(cudaStreamSynchronize(stream), "phi");
+      best = 0;
+      best_phi = INFINITY;
+      for (int j = 0; j < kPhiCand; ++j) {
+        double t = 0.0;
+        for (int b = 0; b < kRedBlocks; ++b) t += hp[size_t(j) * kRedBlocks + b];
+        if (t < best_phi) { best_phi = t; best = j; }
+      }
+    };
+    double phi = 0.0;
+    int best = 0;
+    if (alpha > 0) {
+      std::fill(a.begin(), a.end(), alpha);
+      phi_round(best, phi);
+    } else {
+      // centre: the dose-domain factor <f~, f_T> / <f~, f~> (Eq. 27)
+      k_metrics<C><<<kRedBlocks, kThreads, 0, stream>>>(dp, lab, fT, ft_is_const ? nullptr : ft, ft_const, f_crit,
+                                                       (long long)V, part);
+      count(1);
+      std::vector<double> mp(8 * size_t(kRedBlocks));
+      ck(cudaMemcpyAsync(mp.data(), part, mp.size() * sizeof(double), cudaMemcpyDeviceToHost, stream), "metrics");
+      ck(cudaStreamSynchronize(stream), "metrics");
+      double sdf = 0.0, sdd = 0.0;
+      for (int b = 0; b < kRedBlocks; ++b) { sdf += mp[4 * kRedBlocks + b]; sdd += mp[5 * kRedBlocks + b]; }
+      const double a0 = (sdf > 0 && sdd > 0) ? sdf / sdd : 1.0;
+      for (int j = 0; j < kPhiCand; ++j) a[j] = a0 * std::pow(256.0, double(j) / (kPhiCand - 1)) / 16.0;
+      phi_round(best, phi);
+      for (int round = 0; round < 6; ++round) {
+        const double lo = a[std::max(best - 1, 0)], hi = a[std::min(best + 1, kPhiCand - 1)];
+        for (int j = 0; j < kPhiCand; ++j) a[j] = lo + (hi - lo) * double(j) / (kPhiCand - 1);
+        phi_round(best, phi);
+      }
+      alpha = a[best];
+    }
+    k_response_ratio<C><<<kRedBlocks, kThreads, 0, stream>>>(dp, lab, mT, M, alpha, (long long)V, rp);
+    count(1);
+    ck(cudaMemcpyAsync(hp.data(), rp, 4 * size_t(kRedBlocks) * sizeof(double), cudaMemcpyDeviceToHost, stream),
+       "ratio");
+    ck(cudaFreeAsync(mT, stream), "free");
+    ck(cudaFreeAsync(alphas, stream), "free");
+    ck(cudaFreeAsync(rp, stream), "free");
+    ck(cudaStreamSynchronize(stream), "response metrics");
+    double v[4] = {1e300, -1e300, -1e300, 1e300};
+    for (int b = 0; b < kRedBlocks; ++b) {
+      v[0] = std::min(v[0], hp[0 * kRedBlocks + b]);
+      v[1] = std::max(v[1], hp[1 * kRedBlocks + b]);
+      v[2] = std::max(v[2], hp[2 * kRedBlocks + b]);
+      v[3] = std::min(v[3], hp[3 * kRedBlocks + b]);
+    }
+    std::memset(out, 0, sizeof(*out));
+    out->alpha = alpha;
+    out->phi = phi;
+    out->ratio_min = v[0];
+    out->ratio_max = v[1];
+    out->dtvr_m = v[0] > 0 ? v[1] / v[0] : INFINITY;
+    out->m_band_max = n_band > 0 ? v[2] : 0.0;
+    out->m_gel_min = v[3];
+    out->psr_m = (n_band > 0 && v[2] > 0) ? v[3] / v[2] : INFINITY;
+  }
+
   void set_tolerances(const sipo_tolerances* t) override {
     const int p = t->check_every > 0 ? t->check_every : 64;
     if (p != P || t->storage != tol.storage)
@@ -417,7 +505,7 @@ struct Solver final : SolverBase {
     b.y = y; b.y0 = y0; b.yp = yp; b.ybar = ybar; b.col = col; b.gp = gp; b.g0 = g0; b.gc = gc;
     b.lu = lu; b.ll = ll; b.lu0 = lu0; b.ll0 = ll0; b.lpu = lpu; b.lpl = lpl; b.q = q; b.qp = qp;
     b.d = d; b.d0 = d0; b.dp = dp; b.row = row; b.ft = ft_is_const ? nullptr : ft; b.lab = lab;
-    b.ft_const = ft_const; b.up_ratio = C(up_ratio); b.has_u = has_u; b.has_v = has_v;
+    b.ft_const = ft_const; b.up_ratio = C(up_ratio); b.fu = fu; b.has_u = has_u; b.has_v = has_v;
     b.band_rhs = C(band_rhs); b.st = st; b.part = part;
     b.cert_b = cert_b; b.cert_q = cert_q;
     return b;
@@ -582,7 +670,7 @@ struct Solver final : SolverBase {
   }
 
   // -------------------------------------------------------------- setup
-  void setup(const float* fT_src) override {
+  void setup(const float* fT_src, const float* fL_src, const float* fU_src) override {
     if (psf) {
       // the derivative taps exist for every axis with a PSF; identity axes
       // have no sigma to differentiate
@@ -602,6 +690,29 @@ struct Solver final : SolverBase {
     ck(cudaStreamSynchronize(stream), "target stats");
     if (hs.n_bad) fail(SIPO_ERR_INVALID_ARG, "target contains NaN, infinite or negative values");
     if (hs.n_gel == 0) fail(SIPO_ERR_INVALID_ARG, "empty gelation region (target is all zero)");
+    // Case 1 with explicit per-voxel bounds f_L <= f_U on gel (the response-
+    // domain tolerances of Sec. 2.7.1 mapped through M^-1): f_crit = min f_L
+    float* fLd = nullptr;
+    float* fUd = nullptr;
+    if (fL_src) {
+      ck(cudaMallocAsync(reinterpret_cast<void**>(&fLd), V * sizeof(float), stream), "bounds tmp");
+      ck(cudaMallocAsync(reinterpret_cast<void**>(&fUd), V * sizeof(float), stream), "bounds tmp");
+      ck(cudaMemcpyAsync(fLd, fL_src, V * sizeof(float), cudaMemcpyDefault, stream), "copy f_L");
+      ck(cudaMemcpyAsync(fUd, fU_src, V * sizeof(float), cudaMemcpyDefault, stream), "copy f_U");
+      TargetStats bs{0, 0, 0x7f800000u, 0u};
+      ck(cudaMemcpyAsync(d_stats, &bs, sizeof(bs), cudaMemcpyHostToDevice, stream), "stats init");
+      k_bound_stats<<<gv, kThreads, 0, stream>>>(fT, fLd, fUd, (long long)V, d_stats);
+      ck(cudaMemcpyAsync(&bs, d_stats, sizeof(bs), cudaMemcpyDeviceToHost, stream), "stats");
+      ck(cudaStreamSynchronize(stream), "bound stats");
+      if (bs.n_bad) {
+        cudaFreeAsync(fLd, stream);
+        cudaFreeAsync(fUd, stream);
+        cudaStreamSynchronize(stream);
+        fail(SIPO_ERR_INVALID_ARG, "explicit bounds need 0 < f_L <= f_U (finite) on every gel voxel");
+      }
+      hs.min_bits = bs.min_bits;
+      hs.max_bits = bs.max_bits;
+    }
     float fmin_v, fmax_v;
     std::memcpy(&fmin_v, &hs.min_bits, 4);
     std::memcpy(&fmax_v, &hs.max_bits, 4);
@@ -616,6 +727,12 @@ struct Solver final : SolverBase {
       mult = 1.0 / f_crit;
       c_u = cp.w1;
       c_v = cp.w2;
+    } else if (cp.kase == SIPO_CASE1 && fLd) {
+      f_crit = mn;  // min f_L
+      mult = 1.0 / f_crit;
+      up_ratio = 0.0;
+      c_u = 1.0;
+      c_v = 0.0;
     } else if (cp.kase == SIPO_CASE1) {
       f_crit = (1.0 - cp.tol_lo) * mn;
       mult = (1.0 - cp.tol_lo) / f_crit;
@@ -665,7 +782,14 @@ struct Solver final : SolverBase {
       if (ma) ck(cudaFreeAsync(ma, stream), "free");
       if (mb) ck(cudaFreeAsync(mb, stream), "free");
     }
-    if (!ft_is_const) k_ft<C><<<gv, kThreads, 0, stream>>>(fT, lab, mult, ft, (long long)V);
+    if (!ft_is_const) k_ft<C><<<gv, kThreads, 0, stream>>>(fLd ? fLd : fT, lab, mult, ft, (long long)V);
+    if (fLd) {
+      fu = dalloc<C>(V);
+      k_ft<C><<<gv, kThreads, 0, stream>>>(fUd, lab, mult, fu, (long long)V);
+      ck(cudaFreeAsync(fLd, stream), "free");
+      ck(cudaFreeAsync(fUd, stream), "free");
+      count(2);
+    }
     // columns that need the backprojection inside the solve
     need = dalloc<uint8_t>(size_t(nx) * ny);
     {
@@ -743,14 +867,15 @@ struct Solver final : SolverBase {
     }
     (void)B;
     // setup sums
-    k_setup_sums<C><<<kRedBlocks, kThreads, 0, stream>>>(lab, ft_is_const ? nullptr : ft, ft_const, row,
+    k_setup_sums<C><<<kRedBlocks, kThreads, 0, stream>>>(lab, ft_is_const ? nullptr : ft, ft_const, fu, row,
                                                          up_ratio, has_u, has_v, cp.kase, (long long)V, part);
-    std::vector<double> hp(7 * size_t(kRedBlocks));
+    std::vector<double> hp(8 * size_t(kRedBlocks));
     ck(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, stream), "sums");
     ck(cudaStreamSynchronize(stream), "setup");
-    double sums[7] = {};
-    for (int i = 0; i < 7; ++i)
+    double sums[8] = {};
+    for (int i = 0; i < 8; ++i)
       for (int b = 0; b < kRedBlocks; ++b) sums[i] += hp[size_t(i) * kRedBlocks + b];
+    fu_sum = fu ? sums[7] : 0.0;
     n_band = (long long)sums[0];
     n_gel = (long long)sums[1];
     col_u = has_u ? sums[0] : 0.0;
@@ -776,7 +901,7 @@ struct Solver final : SolverBase {
       } else {
         launch_project<C, C, C, kFpStore, C>(g, t1, Bufs<C, C>{}, cert_b, nullptr, zl, stream);
       }
-      cert_B = cp.kase == SIPO_CASE2 ? double(n_band) * band_rhs : up_ratio * sums[2];
+      cert_B = cp.kase == SIPO_CASE2 ? double(n_band) * band_rhs : (fu ? sums[7] : up_ratio * sums[2]);
       count(3);
     }
     count(16);
@@ -1220,9 +1345,8 @@ const char* sipo_phase_name(int i) {
 
 int sipo_tile_count(void) { return sipo::kBpTiles; }
 
-int sipo_create(const sipo_geometry* geo, const float* f_T, int f_T_location, const sipo_case_params* cp,
-                const sipo_tolerances* tol, void* stream, sipo_ctx** out) {
-  SIPO_TRY
+static void create_impl(const sipo_geometry* geo, const float* f_T, const float* f_L, const float* f_U,
+                        const sipo_case_params* cp, const sipo_tolerances* tol, void* stream, sipo_ctx** out) {
   sipo::g_err.clear();
   if (!geo || !f_T || !cp || !tol || !out) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
@@ -1252,11 +1376,29 @@ int sipo_create(const sipo_geometry* geo, const float* f_T, int f_T_location, co
   if (tol->storage == SIPO_F32) s.reset(new sipo::Solver<float>(geo, cp, tol, st));
   else if (tol->storage == SIPO_F64) s.reset(new sipo::Solver<double>(geo, cp, tol, st));
   else s.reset(new sipo::Solver<__nv_bfloat16>(geo, cp, tol, st));
-  (void)f_T_location;
-  s->setup(f_T);
+  s->setup(f_T, f_L, f_U);
   sipo_ctx* c = new sipo_ctx;
   c->c.s = std::move(s);
   *out = c;
+}
+
+int sipo_create(const sipo_geometry* geo, const float* f_T, int f_T_location, const sipo_case_params* cp,
+                const sipo_tolerances* tol, void* stream, sipo_ctx** out) {
+  SIPO_TRY
+  (void)f_T_location;
+  create_impl(geo, f_T, nullptr, nullptr, cp, tol, stream, out);
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
+int sipo_create_bounded(const sipo_geometry* geo, const float* f_T, const float* f_L, const float* f_U,
+                        int location, const sipo_case_params* cp, const sipo_tolerances* tol, void* stream,
+                        sipo_ctx** out) {
+  SIPO_TRY
+  (void)location;
+  if (!f_L || !f_U || !cp) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
+  if (cp->kase != SIPO_CASE1) sipo::fail(SIPO_ERR_INVALID_ARG, "explicit bounds are a Case-1 form");
+  create_impl(geo, f_T, f_L, f_U, cp, tol, stream, out);
   return SIPO_OK;
   SIPO_CATCH
 }
@@ -1297,6 +1439,48 @@ int sipo_set_primal(sipo_ctx* ctx, const void* y, int y_location, double u, doub
   if (!ctx || !y) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
   if (y_location != SIPO_HOST && y_location != SIPO_DEVICE) sipo::fail(SIPO_ERR_INVALID_ARG, "bad location");
   ctx->c.s->primal_from(y, y_location, u, v);
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
+static sipo::Richards richards_of(const sipo_response* M) {
+  if (!M) sipo::fail(SIPO_ERR_INVALID_ARG, "null response model");
+  if (!(std::isfinite(M->alpha) && std::isfinite(M->k) && std::isfinite(M->f0) && M->k > M->alpha &&
+        M->beta > 0 && std::isfinite(M->beta) && M->gamma > 0 && std::isfinite(M->gamma)))
+    sipo::fail(SIPO_ERR_INVALID_ARG, "response model needs finite alpha < k, beta > 0, gamma > 0");
+  return sipo::Richards{M->alpha, M->k, M->beta, M->gamma, M->f0};
+}
+
+int sipo_response_map(const sipo_response* M, const float* in, float* out, long long n, double scale, int inverse,
+                      void* stream) {
+  SIPO_TRY
+  const sipo::Richards r = richards_of(M);
+  if (n < 0 || (n > 0 && (!in || !out))) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
+  if (!std::isfinite(scale)) sipo::fail(SIPO_ERR_INVALID_ARG, "scale must be finite");
+  if (n == 0) return SIPO_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long* d_bad = nullptr;
+  unsigned long long h_bad = 0;
+  sipo::ck(cudaMallocAsync(reinterpret_cast<void**>(&d_bad), sizeof(*d_bad), s), "response map");
+  sipo::ck(cudaMemsetAsync(d_bad, 0, sizeof(*d_bad), s), "response map");
+  sipo::k_response_map<<<sipo::grid_for(n), sipo::kThreads, 0, s>>>(in, out, n, r, scale, inverse ? 1 : 0, d_bad);
+  sipo::ck(cudaGetLastError(), "response map");
+  ++sipo::g_launches;
+  sipo::ck(cudaMemcpyAsync(&h_bad, d_bad, sizeof(h_bad), cudaMemcpyDeviceToHost, s), "response map");
+  sipo::ck(cudaFreeAsync(d_bad, s), "response map");
+  sipo::ck(cudaStreamSynchronize(s), "response map");
+  if (h_bad) sipo::fail(SIPO_ERR_INVALID_ARG, "response outside the invertible range (>= k, or NaN)");
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
+int sipo_response_metrics(sipo_ctx* ctx, const sipo_response* M, const float* m_T, int location, double alpha,
+                          sipo_response_result* out) {
+  SIPO_TRY
+  (void)location;
+  const sipo::Richards r = richards_of(M);
+  if (!ctx || !m_T || !out) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
+  ctx->c.s->response_metrics(r, m_T, std::isfinite(alpha) ? alpha : 0.0, out);
   return SIPO_OK;
   SIPO_CATCH
 }

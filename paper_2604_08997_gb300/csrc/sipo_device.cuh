@@ -58,6 +58,13 @@ struct ZLayout {
   static_assert(ZL % G == 0, "ZL must be a multiple of the group size");
 };
 
+// Offset of element i of a lane's z-vector from its first group.
+template <typename C, int ZL>
+__device__ __forceinline__ constexpr int z_offset(int i) {
+  using L = ZLayout<C, ZL>;
+  return (i / L::G) * L::kStride + i % L::G;
+}
+
 // One group: G elements of storage type S at p.
 template <typename S, typename C, int G>
 __device__ __forceinline__ void load_group(const S* __restrict__ p, C* v) {

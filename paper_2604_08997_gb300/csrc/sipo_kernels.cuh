@@ -47,6 +47,27 @@ __global__ void k_target_stats(const float* __restrict__ f, long long n, TargetS
   atomicMax(&out->max_bits, mx);
 }
 
+// Explicit Case-1 bounds: over the gel voxels (f_T > 0) counts those whose
+// lower bound is not positive and finite or whose upper bound is below it or
+// not finite, and the float bit range of the lower bound (for f_crit).
+__global__ void k_bound_stats(const float* __restrict__ fT, const float* __restrict__ fL,
+                              const float* __restrict__ fU, long long n, TargetStats* out) {
+  unsigned long long bad = 0;
+  unsigned int mn = 0x7f800000u, mx = 0u;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (!(fT[i] > 0.0f)) continue;
+    const float lo = fL[i], hi = fU[i];
+    if (!(lo > 0.0f) || isinf(lo) || !(hi >= lo) || isinf(hi)) { ++bad; continue; }
+    const unsigned int b = __float_as_uint(lo);
+    mn = min(mn, b);
+    mx = max(mx, b);
+  }
+  atomicAdd(&out->n_bad, bad);
+  atomicMin(&out->min_bits, mn);
+  atomicMax(&out->max_bits, mx);
+}
+
 // ----------------------------------------------------------------- labels
 // dist0[v] = 0 on gel, kDistInf elsewhere.
 __global__ void k_gel_init(const float* __restrict__ f, long long n, int* __restrict__ dist,
@@ -217,13 +238,14 @@ __global__ void k_apply_mask(C* __restrict__ col, const uint8_t* __restrict__ ma
 }
 
 // Setup sums (FP64 partials per block, summed on the host):
-// 0 |band|, 1 |gel|, 2 sum_gel f~, 3 sum_gel f~^2, 4 sum_gel (f~ up_ratio)^2,
-// 5 sum U0^2 / row_up over up rows, 6 sum_gel f~^2 / row_lo.
+// 0 |band|, 1 |gel|, 2 sum_gel f~, 3 sum_gel f~^2, 4 sum_gel f~_U^2,
+// 5 sum U0^2 / row_up over up rows, 6 sum_gel f~^2 / row_lo, 7 sum_gel f~_U,
+// with f~_U the Case-1 upper profile (fu, or f~ up_ratio when fu is null).
 template <typename C>
 __global__ void k_setup_sums(const uint8_t* __restrict__ lab, const C* __restrict__ ft, C ft_const,
-                             const C* __restrict__ row, double up_ratio, int has_u, int has_v,
-                             int kase, long long n, double* __restrict__ part) {
-  double v[7] = {};
+                             const C* __restrict__ fu, const C* __restrict__ row, double up_ratio, int has_u,
+                             int has_v, int kase, long long n, double* __restrict__ part) {
+  double v[8] = {};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const uint8_t l = lab[i];
@@ -239,15 +261,17 @@ __global__ void k_setup_sums(const uint8_t* __restrict__ lab, const C* __restric
       v[1] += 1.0;
       v[2] += f;
       v[3] += f * f;
-      v[4] += f * up_ratio * f * up_ratio;
+      const double fU = fu ? double(fu[i]) : f * up_ratio;
+      v[4] += fU * fU;
+      v[7] += fU;
       const double rup = r + (has_v ? f : 0.0);
-      const double U0 = has_v ? 0.0 : f * up_ratio;
+      const double U0 = has_v ? 0.0 : fU;
       if (rup > 0) v[5] += U0 * U0 / rup;
       if (r > 0) v[6] += f * f / r;
     }
   }
   (void)kase;
-  block_reduce_store<7>(v, part, 0);
+  block_reduce_store<8>(v, part, 0);
 }
 
 // ---------------------------------------------------------- scalar kernels
@@ -434,7 +458,8 @@ __global__ void __launch_bounds__(kThreads) k_cert_vol(Bufs<S, C> b, long long n
       if (!case2) {
         const C dup = to_c(b.lpu[i]) - to_c(b.lu0[i]);
         luh = dup > C(0) ? dup : C(0);
-        red[0] -= double(f) * double(b.up_ratio) * double(luh);
+        const C fU = b.fu ? b.fu[i] : f * b.up_ratio;
+        red[0] -= double(fU) * double(luh);
       }
       qv = luh - llh;
     } else if (l == kBand && case2) {

@@ -112,7 +112,8 @@ struct Bufs {
   const C* ft;          // normalised lower profile f~ (nullptr: ft_const)
   const uint8_t* lab;   // region labels
   C ft_const;
-  C up_ratio;           // Case 1: f~_U / f~_L
+  C up_ratio;           // Case 1: f~_U / f~_L when fu is null
+  const C* fu;          // Case 1: explicit upper profile f~_U per voxel (nullptr: f~ up_ratio)
   int has_u, has_v;
   C band_rhs;           // right side of band rows: 0 (u~ variable) or 1 (Case 2)
   Scal* st;
@@ -187,10 +188,12 @@ __device__ __forceinline__ void dual_update(const Bufs<S, C>& b, const StepScala
       continue;
     }
     const C f = ft[i];
+    // constant upper bound of a Case-1 gel row (0 where v~ moves the bound)
+    const C fU = (b.has_v || band) ? C(0) : (b.fu ? b.fu[base + z_offset<C, ZL>(i)] : f * b.up_ratio);
     const C extra = band ? (b.has_u ? C(1) : C(0)) : (b.has_v ? f : C(0));
     const C rup = row[i] + extra;
     const C sig_up = rup > C(0) ? eo / rup : C(0);
-    const C Ubar = band ? (b.has_u ? sc.ubar : b.band_rhs) : (b.has_v ? sc.vbar * f : f * b.up_ratio);
+    const C Ubar = band ? (b.has_u ? sc.ubar : b.band_rhs) : (b.has_v ? sc.vbar * f : fU);
     C lup = lu[i] + sig_up * (dbar[i] - Ubar);
     lup = rnd<S, C>(lup > C(0) ? lup : C(0));
     C llp = C(0);
@@ -214,7 +217,7 @@ __device__ __forceinline__ void dual_update(const Bufs<S, C>& b, const StepScala
       o_ll[i] = llp;
       o_q[i] = lup - llp;
       o_d[i] = dp;
-      const C Ucur = band ? (b.has_u ? sc.up : b.band_rhs) : (b.has_v ? sc.vp * f : f * b.up_ratio);
+      const C Ucur = band ? (b.has_u ? sc.up : b.band_rhs) : (b.has_v ? sc.vp * f : fU);
       const double eu = double(dp) > double(Ucur) ? double(dp) - double(Ucur) : 0.0;
       red[0] += eu * eu;
       if (rup > C(0)) red[1] += eu * eu / double(rup);
@@ -231,18 +234,18 @@ __device__ __forceinline__ void dual_update(const Bufs<S, C>& b, const StepScala
         if (row[i] > C(0)) red[1] += el * el / double(row[i]);
         const double dll = double(llp) - double(ll0[i]);
         red[2] += double(f) * double(llp);
-        red[3] += double(f) * double(b.up_ratio) * double(lup);
+        red[3] += double(fU) * double(lup);
         red[5] += double(f) * double(lup);
         red[6] += double(row[i]) * (double(ll[i]) - double(llp)) * (double(ll[i]) - double(llp));
         red[7] += double(row[i]) * dll * dll;
         red[8] += double(f) * dll;
         red[10] += double(f) * dlu;
-        red[11] += double(f) * double(b.up_ratio) * dlu;
+        red[11] += double(fU) * dlu;
         red[12] = fmax(red[12], -dll);
         const double rl = double(llp) - double(ll[i]);
         red[13] += double(f) * rl;
         red[15] += double(f) * (double(lup) - double(lu[i]));
-        red[16] += double(f) * double(b.up_ratio) * (double(lup) - double(lu[i]));
+        red[16] += double(fU) * (double(lup) - double(lu[i]));
         red[17] = fmax(red[17], -rl);
       }
       const double ru = double(lup) - double(lu[i]);
