@@ -49,8 +49,8 @@ SM_MAX_MHZ = 2070.0
 # is null until re-captured.
 KERNEL_SOURCES = ["sipo_device.cuh", "sipo_solver.cuh", "sipo_ops.cuh", "sipo_launch.h",
                   "sipo_project.cu", "sipo_backproject.cu"]
-TRAFFIC = {("csg256", "f32"): {"sources_sha256_16": "ec3dfee9f2b7db7f",
-                               "project": 281752576, "backproject": 224114944}}
+TRAFFIC = {("csg256", "f32"): {"sources_sha256_16": "adc961dbddc52893",
+                               "project": 279230208, "backproject": 221787264}}
 
 
 def _code_only(text: str) -> str:
