@@ -371,3 +371,51 @@ def test_two_stage_solve_matches_the_oracle(sipo):
     assert s2["status"] == sipo.SIPO_OPTIMAL
     assert abs(s2["pobj"] - ref2["obj"]) <= 1e-6 * ref2["obj"]
     assert s2["pobj"] <= 1.1 / 0.9 * (1 + 1e-7)
+
+
+@pytest.mark.parametrize("case,extra", [(1, dict(tol_lo=0.1, tol_hi=0.1)), (2, dict(inhibit_ratio=0.7))])
+def test_band_width_and_band_free_reach_the_oracle(sipo, case, extra):
+    """The band-width study of Sec. 3.2: FP64 solves with a width-1 band and
+    band-free (every non-gel voxel in the vial is band) reach the oracle's
+    optima, which cannot improve as the band widens."""
+    tgt = discs_2d(14, n_discs=2, r_range=(1.5, 2.5), container_radius=5.0, seed=6)
+    ang = uniform_angles(10)
+    geo = dict(nx=14, ny=14, nz=1, angles=ang, n_det=21)
+    objs = []
+    for W in (1, -1):
+        lp, ops = build_lp(Geometry(14, 14, 1, ang, 21), tgt, CaseParams(case=case, band_width=W, **extra))
+        ref = pdhg.solve(lp, ops, kkt_tol=1e-10, max_iter=100000)
+        assert ref["status"] == pdhg.OPTIMAL
+        ctx = sipo.sipo_create(geo, tgt, dict(kase=case, band_width=W, **extra),
+                               dict(storage=sipo.SIPO_F64, kkt_tol=1e-10, max_iter=100000))
+        labels = np.empty(14 * 14, np.uint8)
+        sipo.sipo_get_array(ctx, 0, labels)
+        assert np.array_equal(labels, lp.labels)
+        res = sipo.sipo_solve(ctx)
+        assert res["status"] == sipo.SIPO_OPTIMAL
+        assert abs(res["pobj"] - ref["obj"]) <= 1e-7 * abs(ref["obj"])
+        objs.append(res["pobj"])
+    assert objs[1] >= objs[0] * (1 - 1e-7)
+
+
+def test_full_turn_with_attenuation_reaches_the_oracle(sipo):
+    """A full 360-degree rotation with Beer-Lambert attenuation (16 views over
+    [0, 2 pi), vial radius 5.8, mu = 0.15): FP64 solves of Case 1 and Case 2
+    reach the oracle optima, and the half turn of the same Case 2 (light from
+    one side only) is reported infeasible, as the oracle reports it."""
+    tgt = discs_2d(12, n_discs=2, r_range=(1.5, 2.5), container_radius=4.5, seed=8)
+    for case, extra, full in ((1, dict(tol_lo=0.1, tol_hi=0.1), True), (2, dict(inhibit_ratio=0.7), True),
+                              (2, dict(inhibit_ratio=0.7), False)):
+        ang = uniform_angles(16, 2 * np.pi) if full else uniform_angles(8, np.pi)
+        lp, ops = build_lp(Geometry(12, 12, 1, ang, 17, vial_radius=5.8, mu=0.15), tgt,
+                           CaseParams(case=case, band_width=2, **extra))
+        ref = pdhg.solve(lp, ops, kkt_tol=1e-10, max_iter=100000)
+        ctx = sipo.sipo_create(dict(nx=12, ny=12, nz=1, angles=ang, n_det=17, vial_radius=5.8, mu=0.15), tgt,
+                               dict(kase=case, band_width=2, **extra),
+                               dict(storage=sipo.SIPO_F64, kkt_tol=1e-10, max_iter=100000))
+        res = sipo.sipo_solve(ctx)
+        if ref["status"] == pdhg.PRIMAL_INFEASIBLE:
+            assert res["status"] == sipo.SIPO_PRIMAL_INFEASIBLE, res
+            continue
+        assert ref["status"] == pdhg.OPTIMAL and res["status"] == sipo.SIPO_OPTIMAL, res
+        assert abs(res["pobj"] - ref["obj"]) <= 1e-7 * abs(ref["obj"])

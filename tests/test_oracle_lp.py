@@ -317,6 +317,66 @@ def test_primal_start_projects_onto_the_primal_domain():
     assert v == 1.0 or np.any(np.isclose(d[lp.gel], v * lp.ft[lp.gel], rtol=1e-12))
 
 
+def _band_instance(case, extra, W):
+    tgt = discs_2d(14, n_discs=2, r_range=(1.5, 2.5), container_radius=5.0, seed=6)
+    geo = Geometry(14, 14, 1, uniform_angles(10), 21)
+    return build_lp(geo, tgt, CaseParams(case=case, band_width=W, **extra))
+
+
+@pytest.mark.parametrize("case,extra", [(GENERAL, {}), (CASE1, dict(tol_lo=0.1, tol_hi=0.1)),
+                                        (CASE2, dict(inhibit_ratio=0.7))])
+def test_band_width_study_is_monotone(case, extra):
+    """Band-region definition (Sec. 3.2): a wider band adds band rows, so the
+    band sets are nested (width 1, 2, 3, band-free) and the optimum (HiGHS)
+    cannot improve; the oracle PDHG reaches the band-free optimum."""
+    prev_band, prev_obj = None, -np.inf
+    for W in (1, 2, 3, -1):
+        lp, ops = _band_instance(case, extra, W)
+        if prev_band is not None:
+            assert np.all(lp.band[prev_band]) and lp.band.sum() > prev_band.sum()
+        ref = _highs(lp, ops)
+        assert ref.status == 0
+        assert ref.fun >= prev_obj - 1e-9 * abs(ref.fun)
+        prev_band, prev_obj = lp.band.copy(), ref.fun
+    res = pdhg.solve(lp, ops, kkt_tol=1e-10, max_iter=100000)
+    assert res["status"] == pdhg.OPTIMAL
+    assert abs(res["obj"] - ref.fun) <= 1e-8 * abs(ref.fun)
+
+
+def _turn_instance(case, extra, full, mu):
+    tgt = discs_2d(12, n_discs=2, r_range=(1.5, 2.5), container_radius=4.5, seed=8)
+    ang = uniform_angles(16, 2 * math.pi) if full else uniform_angles(8, math.pi)
+    geo = Geometry(12, 12, 1, ang, 17, vial_radius=5.8, mu=mu)
+    return build_lp(geo, tgt, CaseParams(case=case, band_width=2, **extra))
+
+
+@pytest.mark.parametrize("case,extra", [(GENERAL, {}), (CASE1, dict(tol_lo=0.1, tol_hi=0.1)),
+                                        (CASE2, dict(inhibit_ratio=0.7))])
+def test_full_turn_against_half_turn(case, extra):
+    """A full 360-degree rotation (Sec. 3.1 uses 1-degree steps over a full
+    turn).  Without attenuation the view at theta + pi mirrors the one at
+    theta (u -> n_det - 1 - u), so 2N views over [0, 2 pi) reach exactly the
+    optimum of N views over [0, pi) (the LP is scale invariant).  With
+    attenuation the far side is dimmer, the full turn holds every half-turn
+    ray and more, and its optimum cannot be worse (here Case 2 turns from
+    infeasible to feasible); the oracle PDHG reaches the full-turn optimum."""
+    half = _highs(*_turn_instance(case, extra, False, 0.0))
+    full = _highs(*_turn_instance(case, extra, True, 0.0))
+    assert half.status == 0 and full.status == 0
+    assert abs(full.fun - half.fun) <= 1e-9 * abs(half.fun)
+    half = _highs(*_turn_instance(case, extra, False, 0.15))
+    lp, ops = _turn_instance(case, extra, True, 0.15)
+    full = _highs(lp, ops)
+    assert full.status == 0
+    if case == CASE2:
+        assert half.status == 2
+    else:
+        assert half.status == 0 and full.fun < half.fun * (1 - 1e-3)
+    res = pdhg.solve(lp, ops, kkt_tol=1e-10, max_iter=100000)
+    assert res["status"] == pdhg.OPTIMAL
+    assert abs(res["obj"] - full.fun) <= 1e-8 * abs(full.fun)
+
+
 def test_scale_invariance_bitwise_and_general():
     """f_T -> 2^k f_T leaves the normalised LP and the iterates bitwise unchanged;
     a general factor leaves the optimum unchanged (Sec. 2.5, Eq. 18)."""
