@@ -240,6 +240,30 @@ int sipo_solve(sipo_ctx *ctx, void *y_out, int y_location, sipo_result *res);
  * problems, src never solved), CUDA. */
 int sipo_warm_start(sipo_ctx *dst, const sipo_ctx *src);
 
+/* Checkpoint (no passage of the paper: solver state for resume).  Copies the
+ * point T(z) of the last KKT check of ctx's most recent solve — the point a
+ * warm start or a resume continues from — out in the compute type (FP32, or
+ * FP64 when storage is SIPO_F64), host or device per `location`: y
+ * [n_angles][n_det][nz], lam_up and lam_lo [ny][nx][nz] (each nullable), and
+ * scalars[4] = {u~, v~, omega, iterations} (nullable).  Synchronises ctx's
+ * stream.  Errors: INVALID_ARG (null ctx, bad location, ctx never solved),
+ * CUDA. */
+int sipo_get_state(sipo_ctx *ctx, void *y, void *lam_up, void *lam_lo, int location, double *scalars);
+
+/* Resume: the next sipo_solve or sipo_solve_batched of ctx starts from the
+ * point (y, lam_up, lam_lo) with scalars[0..2] = {u~, v~, omega} (layouts and
+ * type as sipo_get_state; scalars[3] is not read: the resumed solve counts
+ * its iterations from 0), instead of from zero.  The point is projected onto
+ * the domains of Eqs. 20-24 (y >= 0 on active rays; lam_up >= 0 on band and
+ * gel rows, lam_lo >= 0 on gel rows; other entries 0); A^T y and
+ * A (lam_up - lam_lo) are recomputed; u~, v~ out of their bounds (u~ < 0,
+ * v~ < 1, not finite) become the smallest the point allows, as for
+ * sipo_set_primal, and omega <= 0 the default.  The point becomes iterate and
+ * restart anchor.  Synchronises ctx's stream.  Errors: INVALID_ARG (null, bad
+ * location), CUDA. */
+int sipo_set_state(sipo_ctx *ctx, const void *y, const void *lam_up, const void *lam_lo, int location,
+                   const double *scalars);
+
 /* Primal start, for the two-stage design of Sec. 3.2 (a Case-1 solve fixes
  * the process bound, a Case-2 solve at that bound then recovers conformity,
  * starting from the Case-1 point rescaled).  The next sipo_solve or

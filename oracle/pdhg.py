@@ -205,14 +205,25 @@ def primal_start(lp: LPData, ops: Operators, y, u=None, v=None):
     return y, (float(u) if lp.has_u else 0.0), (float(v) if lp.has_v else 1.0)
 
 
+def dual_point(lp: LPData, lam_up, lam_lo):
+    """A caller's dual point projected onto the dual domain (Eqs. 20-22):
+    lam_up >= 0 on band and gel rows, lam_lo >= 0 on gel rows, 0 elsewhere."""
+    up = np.asarray(lam_up, np.float64).ravel()
+    lo = np.asarray(lam_lo, np.float64).ravel()
+    up = np.where((lp.band | lp.gel) & (up > 0), up, 0.0)
+    lo = np.where(lp.gel & (lo > 0), lo, 0.0)
+    return up, lo
+
+
 def solve(lp: LPData, ops: Operators, kkt_tol=1e-4, max_iter=10000,
-          check_every=64, omega0=None, verbose=False, history=None, start=None):
+          check_every=64, omega0=None, verbose=False, history=None, start=None, dual_start=None):
     """Run the restarted Halpern PDHG; returns a dict with status, T(z) and KKT data.
 
     `iters` counts PDHG steps; the returned point is T(z) at the last check.
     `start` = (y, u, v) starts from that primal point (made admissible by
     `primal_start`; None entries for u, v ask for the smallest admissible)
-    with zero duals, instead of from y = 0, u~ = 0, v~ = 1.
+    with zero duals, instead of from y = 0, u~ = 0, v~ = 1; `dual_start` =
+    (lam_up, lam_lo) adds a dual point (made admissible by `dual_point`).
     """
     geo = ops.geo
     pc = Preconditioner(lp, ops)
@@ -239,8 +250,10 @@ def solve(lp: LPData, ops: Operators, kkt_tol=1e-4, max_iter=10000,
     if start is not None:
         y, u, v = primal_start(lp, ops, *start)
     lam_up, lam_lo = np.zeros(V), np.zeros(V)
+    if dual_start is not None:
+        lam_up, lam_lo = dual_point(lp, *dual_start)
     y0, u0, v0, lam_up0, lam_lo0 = y.copy(), u, v, lam_up.copy(), lam_lo.copy()
-    g0 = np.zeros(S)
+    g0 = A(lam_up - lam_lo) if dual_start is not None else np.zeros(S)
     k_in = 0
     r0 = None
     r_prev = None

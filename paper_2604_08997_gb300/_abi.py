@@ -94,6 +94,8 @@ SIGNATURES = {
                                       POINTER(sipo_response_result)]),
     "sipo_warm_start": (c_int, [c_void_p, c_void_p]),
     "sipo_set_primal": (c_int, [c_void_p, c_void_p, c_int, c_double, c_double]),
+    "sipo_get_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, POINTER(c_double)]),
+    "sipo_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, POINTER(c_double)]),
     "sipo_project": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     "sipo_backproject": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     "sipo_psf_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
@@ -338,6 +340,31 @@ def sipo_set_primal(ctx: Context, y, u: float = -1.0, v: float = -1.0) -> None:
     with u~ = u, v~ = v (negative: the smallest the point allows) and zero duals."""
     p, loc = _ptr(y)
     _check(load().sipo_set_primal(ctx.handle, c_void_p(p), loc, float(u), float(v)))
+
+
+def sipo_get_state(ctx: Context, y, lam_up, lam_lo) -> dict:
+    """Checkpoint: T(z) of ctx's last check into y [n_angles*n_det*nz], lam_up, lam_lo
+    [ny*nx*nz] (compute dtype, all host or all CUDA); returns u, v, omega, iters."""
+    py, ly = _ptr(y)
+    pu, lu = _ptr(lam_up)
+    pl, ll = _ptr(lam_lo)
+    if not (ly == lu == ll):
+        raise ValueError("y, lam_up and lam_lo must all be on the host or all on the device")
+    sc = (c_double * 4)()
+    _check(load().sipo_get_state(ctx.handle, c_void_p(py), c_void_p(pu), c_void_p(pl), ly, sc))
+    return {"u": sc[0], "v": sc[1], "omega": sc[2], "iters": int(sc[3])}
+
+
+def sipo_set_state(ctx: Context, y, lam_up, lam_lo, u: float = -1.0, v: float = -1.0,
+                   omega: float = -1.0) -> None:
+    """Resume: ctx's next solve starts from (y, lam_up, lam_lo, u~, v~, omega)."""
+    py, ly = _ptr(y)
+    pu, lu = _ptr(lam_up)
+    pl, ll = _ptr(lam_lo)
+    if not (ly == lu == ll):
+        raise ValueError("y, lam_up and lam_lo must all be on the host or all on the device")
+    sc = (c_double * 4)(float(u), float(v), float(omega), 0.0)
+    _check(load().sipo_set_state(ctx.handle, c_void_p(py), c_void_p(pu), c_void_p(pl), ly, sc))
 
 
 def sipo_solve_batched(ctxs, y_outs=None) -> list[dict]:

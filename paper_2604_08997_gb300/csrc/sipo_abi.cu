@@ -91,8 +91,11 @@ struct SolverBase {
   virtual int dev() const = 0;
   virtual std::vector<double> fingerprint() const = 0;
   virtual void warm_from(const SolverBase& src) = 0;
-  // start from a caller's primal point (y, u~, v~) with zero duals
-  virtual void primal_from(const void* y, int loc, double u, double v) = 0;
+  // start from a caller's point (y, lam_up, lam_lo, u~, v~, omega); null duals: zero
+  virtual void state_from(const void* y, const void* lam_up, const void* lam_lo, int loc, double u, double v,
+                          double omega) = 0;
+  // the point T(z) of the last check: y, lam_up, lam_lo (compute type) and u~, v~, omega, k
+  virtual void state_to(void* y, void* lam_up, void* lam_lo, int loc, double* scalars) = 0;
   // response-domain post-scaling and metrics of the last solve's dose
   virtual void response_metrics(const Richards& M, const float* mT, double alpha, sipo_response_result* out) = 0;
 };
@@ -228,6 +231,7 @@ struct Solver final : SolverBase {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (stream) cudaStreamSynchronize(stream);
     for (void* p : allocs) cudaFree(p);
+    if (tconv) cudaFree(tconv);
     if (h_st) cudaFreeHost(h_st);
     if (own_stream && stream) cudaStreamDestroy(stream);
   }
@@ -329,25 +333,49 @@ struct Solver final : SolverBase {
     warm_pending = true;
   }
 
-  // The next solve starts from a caller's primal point: y (compute type,
-  // [n_angles][n_det][nz]) projected onto y >= 0 and the active rays, the
-  // scalars u~ and v~ (a negative or non-finite value: the smallest the point
-  // allows, max of A^T y over band rows for u~ and max of A^T y / f~ over gel
-  // rows, at least 1, for v~), zero duals and the default primal weight.  The
-  // point becomes iterate and restart anchor, as after a restart.
-  void primal_from(const void* y_in, int loc, double u, double v) override {
+  // The next solve starts from a caller's point: y (compute type,
+  // [n_angles][n_det][nz]) projected onto y >= 0 and the active rays; the
+  // duals lam_up, lam_lo ([ny][nx][nz], null: zero) projected onto their
+  // domain; the scalars u~ and v~ (a negative or non-finite value: the
+  // smallest the point allows, max of A^T y over band rows for u~ and max of
+  // A^T y / f~ over gel rows, at least 1, for v~); the primal weight omega
+  // (<= 0 or non-finite: the default).  The point becomes iterate and restart
+  // anchor, as after a restart; A^T y and A (lam_up - lam_lo) are recomputed.
+  void state_from(const void* y_in, const void* up_in, const void* lo_in, int loc, double u, double v,
+                  double omega) override {
     init_state();
     const Geo<C> g = geo();
     const Bufs<S, C> B = bufs();
-    // gp (zero at a start) holds the caller's values until they are projected
-    ck(cudaMemcpyAsync(gp, y_in, SN * sizeof(C), loc == SIPO_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
-                       stream), "primal start");
-    k_import_primal<S, C><<<grid_for((long long)SN), kThreads, 0, stream>>>(gp, col, yp, (long long)SN);
-    zero(gp, SN);
+    const cudaMemcpyKind kind = loc == SIPO_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    C* ts = nullptr;
+    ck(cudaMallocAsync(reinterpret_cast<void**>(&ts), SN * sizeof(C), stream), "state tmp");
+    ck(cudaMemcpyAsync(ts, y_in, SN * sizeof(C), kind, stream), "state y");
+    k_import_primal<S, C><<<grid_for((long long)SN), kThreads, 0, stream>>>(ts, col, yp, (long long)SN);
+    ck(cudaFreeAsync(ts, stream), "free");
     // d = A^T y with the operator of a check step's plain backprojection
     launch_backproject<S, S, C, kBpStore, C>(g, yp, B, psf ? braw : dp, need, zl, stream, bp_nv);
     if (psf) psf3<C, C>(braw, dp, t1, t2, -1, stream);
-    count(3);
+    count(2);
+    if (up_in || lo_in) {
+      C *tu = nullptr, *tl = nullptr, *tq = nullptr;
+      ck(cudaMallocAsync(reinterpret_cast<void**>(&tu), V * sizeof(C), stream), "state tmp");
+      ck(cudaMallocAsync(reinterpret_cast<void**>(&tl), V * sizeof(C), stream), "state tmp");
+      ck(cudaMallocAsync(reinterpret_cast<void**>(&tq), V * sizeof(C), stream), "state tmp");
+      if (up_in) ck(cudaMemcpyAsync(tu, up_in, V * sizeof(C), kind, stream), "state lam_up");
+      else ck(cudaMemsetAsync(tu, 0, V * sizeof(C), stream), "memset");
+      if (lo_in) ck(cudaMemcpyAsync(tl, lo_in, V * sizeof(C), kind, stream), "state lam_lo");
+      else ck(cudaMemsetAsync(tl, 0, V * sizeof(C), stream), "memset");
+      k_import_dual<S, C><<<grid_for((long long)V), kThreads, 0, stream>>>(tu, tl, lab, lpu, lpl, tq,
+                                                                          (long long)V);
+      count(1);
+      // A q of the imported duals on the active rays (the T point's g)
+      project(tq, gp, stream);
+      k_apply_mask<C><<<grid_for((long long)SN), kThreads, 0, stream>>>(gp, mask, (long long)SN);
+      count(1);
+      ck(cudaFreeAsync(tu, stream), "free");
+      ck(cudaFreeAsync(tl, stream), "free");
+      ck(cudaFreeAsync(tq, stream), "free");
+    }
     const bool need_u = has_u && !(u >= 0.0 && std::isfinite(u));
     const bool need_v = has_v && !(v >= 1.0 && std::isfinite(v));
     if (need_u || need_v) {
@@ -356,7 +384,7 @@ struct Solver final : SolverBase {
       count(1);
       std::vector<double> hp(8 * size_t(kRedBlocks));
       ck(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, stream), "start");
-      ck(cudaStreamSynchronize(stream), "primal start");
+      ck(cudaStreamSynchronize(stream), "state start");
       double mx_band = 0.0, mx_gel = 1.0;
       for (int b = 0; b < kRedBlocks; ++b) {
         mx_band = std::max(mx_band, hp[2 * kRedBlocks + b]);
@@ -369,10 +397,11 @@ struct Solver final : SolverBase {
     Scal h = *h_st;
     if (has_u) h.u = h.u0 = h.up = u;
     if (has_v) h.v = h.v0 = h.vp = v;
+    if (omega > 0 && std::isfinite(omega)) h.omega = omega;
     h.restart = 1;
     *h_st = h;
     ck(cudaMemcpyAsync(st, h_st, sizeof(Scal), cudaMemcpyHostToDevice, stream), "state");
-    ck(cudaStreamSynchronize(stream), "primal start");
+    ck(cudaStreamSynchronize(stream), "state start");
     const long long nvv = (long long)(V / ze), nvs = (long long)(SN / ze);
     if (ze > 1) {
       k_blend_sino<S, C, z_group<C>()><<<grid_for(nvs), kThreads, 0, stream>>>(B, nvs);
@@ -385,8 +414,41 @@ struct Solver final : SolverBase {
     h.restart = 0;
     *h_st = h;
     ck(cudaMemcpyAsync(st, h_st, sizeof(Scal), cudaMemcpyHostToDevice, stream), "state");
-    ck(cudaStreamSynchronize(stream), "primal start");
+    ck(cudaStreamSynchronize(stream), "state start");
     warm_pending = true;
+  }
+
+  // Checkpoint: the point T(z) of the last check of the most recent solve (the
+  // point a warm start or a resume continues from), in the compute type.
+  void state_to(void* y_out, void* up_out, void* lo_out, int loc, double* scalars) override {
+    ck(cudaStreamSynchronize(stream), "checkpoint");
+    if (!solved) fail(SIPO_ERR_INVALID_ARG, "checkpoint: the context has not been solved");
+    if (y_out) copy_out(yp, SN, y_out, loc, conv_tmp(SN));
+    if (up_out) copy_out(lpu, V, up_out, loc, conv_tmp(V));
+    if (lo_out) copy_out(lpl, V, lo_out, loc, conv_tmp(V));
+    ck(cudaStreamSynchronize(stream), "checkpoint");
+    if (scalars) {
+      scalars[0] = h_st->up;
+      scalars[1] = h_st->vp;
+      scalars[2] = h_st->omega;
+      scalars[3] = double(h_st->k);
+    }
+  }
+
+  // conversion scratch for copies out of BF16 storage (never a state buffer)
+  C* tconv = nullptr;
+  size_t tconv_n = 0;
+  C* conv_tmp(size_t n) {
+    if (std::is_same<S, C>::value) return nullptr;
+    if (tconv_n < n) {
+      if (tconv) {
+        ck(cudaStreamSynchronize(stream), "scratch");
+        ck(cudaFree(tconv), "scratch");
+      }
+      ck(cudaMalloc(reinterpret_cast<void**>(&tconv), n * sizeof(C)), "scratch");
+      tconv_n = n;
+    }
+    return tconv;
   }
 
   // Response-domain back end of the last solve (Sec. 2.7: Eq. 28 with unit
@@ -1134,7 +1196,7 @@ struct Solver final : SolverBase {
     count(1);
     std::vector<double> hp(8 * size_t(kRedBlocks));
     ck(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, stream), "metrics");
-    if (y_out) copy_out(yp, SN, y_out, loc, gp);
+    if (y_out) copy_out(yp, SN, y_out, loc, conv_tmp(SN));
     ck(cudaStreamSynchronize(stream), "metrics");
     double m[8] = {1e300, -1e300, -1e300, 1e300, 0.0, 0.0, 1e300, -1e300};
     for (int b = 0; b < kRedBlocks; ++b) {
@@ -1262,12 +1324,11 @@ struct Solver final : SolverBase {
     } else if (which == 1) {
       ck(cudaMemcpyAsync(out, mask, SN, kind, stream), "mask");
     } else if (which == 2) {
-      copy_out(solved ? yp : y, SN, out, loc, gp);
+      copy_out(solved ? yp : y, SN, out, loc, conv_tmp(SN));
     } else if (which == 3 || which == 4) {
-      if (!tvol) tvol = dalloc<C>(V);
-      copy_out(which == 3 ? (solved ? lpu : lu) : (solved ? lpl : ll), V, out, loc, tvol);
+      copy_out(which == 3 ? (solved ? lpu : lu) : (solved ? lpl : ll), V, out, loc, conv_tmp(V));
     } else if (which == 5) {
-      copy_out(solved ? dp : d, V, out, loc, gp);
+      copy_out(solved ? dp : d, V, out, loc, conv_tmp(V));
     } else {
       fail(SIPO_ERR_INVALID_ARG, "unknown array id");
     }
@@ -1434,11 +1495,30 @@ int sipo_warm_start(sipo_ctx* dst, const sipo_ctx* src) {
   SIPO_CATCH
 }
 
+int sipo_get_state(sipo_ctx* ctx, void* y, void* lam_up, void* lam_lo, int location, double* scalars) {
+  SIPO_TRY
+  if (!ctx) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
+  if (location != SIPO_HOST && location != SIPO_DEVICE) sipo::fail(SIPO_ERR_INVALID_ARG, "bad location");
+  ctx->c.s->state_to(y, lam_up, lam_lo, location, scalars);
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
+int sipo_set_state(sipo_ctx* ctx, const void* y, const void* lam_up, const void* lam_lo, int location,
+                   const double* scalars) {
+  SIPO_TRY
+  if (!ctx || !y || !lam_up || !lam_lo || !scalars) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
+  if (location != SIPO_HOST && location != SIPO_DEVICE) sipo::fail(SIPO_ERR_INVALID_ARG, "bad location");
+  ctx->c.s->state_from(y, lam_up, lam_lo, location, scalars[0], scalars[1], scalars[2]);
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
 int sipo_set_primal(sipo_ctx* ctx, const void* y, int y_location, double u, double v) {
   SIPO_TRY
   if (!ctx || !y) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
   if (y_location != SIPO_HOST && y_location != SIPO_DEVICE) sipo::fail(SIPO_ERR_INVALID_ARG, "bad location");
-  ctx->c.s->primal_from(y, y_location, u, v);
+  ctx->c.s->state_from(y, nullptr, nullptr, y_location, u, v, -1.0);
   return SIPO_OK;
   SIPO_CATCH
 }

@@ -200,6 +200,25 @@ __global__ void k_import_primal(const C* __restrict__ in, const C* __restrict__ 
   }
 }
 
+// A caller's dual point projected onto the dual domain: lam_up >= 0 on band
+// and gel rows, lam_lo >= 0 on gel rows, 0 elsewhere (Eqs. 20-22); stored in
+// the iterate type, and q = lam_up - lam_lo of the stored values in C.
+template <typename S, typename C>
+__global__ void k_import_dual(const C* __restrict__ in_up, const C* __restrict__ in_lo,
+                              const uint8_t* __restrict__ lab, S* __restrict__ up, S* __restrict__ lo,
+                              C* __restrict__ q, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const uint8_t l = lab[i];
+    const C a = in_up[i], b = in_lo[i];
+    const S su = from_c<S>(l != kExt && a > C(0) ? a : C(0));
+    const S sl = from_c<S>(l == kGel && b > C(0) ? b : C(0));
+    up[i] = su;
+    lo[i] = sl;
+    q[i] = to_c(su) - to_c(sl);
+  }
+}
+
 // Indicator volume 1_band + 2 * 1_gel (column abs-sums of G, Pock-Chambolle).
 template <typename C>
 __global__ void k_row_indicator(const uint8_t* __restrict__ lab, C* __restrict__ out, long long n) {

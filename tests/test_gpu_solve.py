@@ -419,3 +419,59 @@ def test_full_turn_with_attenuation_reaches_the_oracle(sipo):
             continue
         assert ref["status"] == pdhg.OPTIMAL and res["status"] == sipo.SIPO_OPTIMAL, res
         assert abs(res["pobj"] - ref["obj"]) <= 1e-7 * abs(ref["obj"])
+
+
+def test_checkpoint_resume_tracks_the_oracle(sipo):
+    """sipo_get_state / sipo_set_state: a checkpoint taken after 256 FP64
+    iterations, written to host arrays and resumed in a fresh context, runs
+    320 more iterations in step with the oracle PDHG started from the same
+    point (objectives, residuals and restart counts agree)."""
+    case, extra = TINY[1]
+    lp, ops, geo, tgt, cp = _tiny(case, extra)
+    src = sipo.sipo_create(geo, tgt, cp, dict(storage=sipo.SIPO_F64, kkt_tol=0.0, max_iter=256))
+    sipo.sipo_solve(src)
+    y = np.empty(lp.active.size)
+    up = np.empty(lp.labels.size)
+    lo = np.empty(lp.labels.size)
+    sc = sipo.sipo_get_state(src, y, up, lo)
+    assert sc["iters"] == 256
+    ref = pdhg.solve(lp, ops, kkt_tol=0.0, max_iter=320, omega0=sc["omega"], start=(y, sc["u"], sc["v"]),
+                     dual_start=(up, lo))
+    dst = sipo.sipo_create(geo, tgt, cp, dict(storage=sipo.SIPO_F64, kkt_tol=0.0, max_iter=320))
+    sipo.sipo_set_state(dst, y, up, lo, sc["u"], sc["v"], sc["omega"])
+    res = sipo.sipo_solve(dst)
+    assert res["iters"] == 320 and res["restarts"] == ref["restarts"]
+    for key in ("pobj", "dobj", "rel_primal", "rel_dual"):
+        a, b = res[key], ref["info"][key]
+        assert abs(a - b) <= 1e-7 * max(abs(b), 1e-3), (key, a, b)
+
+
+def test_resume_at_an_optimum_and_bf16_checkpoint(sipo):
+    """Resuming a context from an optimal checkpoint stops at its first check
+    with the same objective; a BF16 context's checkpoint (FP32 arrays) holds
+    the y that sipo_solve returned, twice in a row (no scratch overwrites the
+    saved point)."""
+    case, extra = TINY[2]
+    lp, ops, geo, tgt, cp = _tiny(case, extra)
+    tol = dict(storage=sipo.SIPO_F64, kkt_tol=1e-9, max_iter=100000)
+    src = sipo.sipo_create(geo, tgt, cp, tol)
+    r0 = sipo.sipo_solve(src)
+    assert r0["status"] == sipo.SIPO_OPTIMAL
+    y = np.empty(lp.active.size)
+    up = np.empty(lp.labels.size)
+    lo = np.empty(lp.labels.size)
+    sc = sipo.sipo_get_state(src, y, up, lo)
+    dst = sipo.sipo_create(geo, tgt, cp, tol)
+    sipo.sipo_set_state(dst, y, up, lo, sc["u"], sc["v"], sc["omega"])
+    r1 = sipo.sipo_solve(dst)
+    assert r1["status"] == sipo.SIPO_OPTIMAL and r1["iters"] <= 64
+    assert abs(r1["pobj"] - r0["pobj"]) <= 1e-8 * abs(r0["pobj"])
+    low = sipo.sipo_create(geo, tgt, cp, dict(storage=sipo.SIPO_BF16, kkt_tol=1e-3, max_iter=2048))
+    y_out = np.empty(lp.active.size, np.float32)
+    sipo.sipo_solve(low, y_out)
+    ys = [np.empty(lp.active.size, np.float32) for _ in range(2)]
+    for yy in ys:
+        sipo.sipo_get_state(low, yy, np.empty(lp.labels.size, np.float32), np.empty(lp.labels.size, np.float32))
+    assert np.array_equal(ys[0], y_out) and np.array_equal(ys[1], y_out)
+    with pytest.raises(sipo.SipoError):
+        sipo.sipo_get_state(sipo.sipo_create(geo, tgt, cp, tol), y, up, lo)

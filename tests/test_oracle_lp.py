@@ -377,6 +377,27 @@ def test_full_turn_against_half_turn(case, extra):
     assert abs(res["obj"] - full.fun) <= 1e-8 * abs(full.fun)
 
 
+def test_resume_from_an_optimal_checkpoint_stops_at_once():
+    """Checkpoint and resume: restarting the oracle from its own returned point
+    T(z) (y, lam_up, lam_lo, u~, v~, omega) of a solve at KKT 1e-10 stops at
+    the first check with the same objective; dual_point keeps an admissible
+    dual point and zeroes the rest."""
+    lp, ops = _tiny(CASE1, dict(tol_lo=0.1, tol_hi=0.1))
+    res = pdhg.solve(lp, ops, kkt_tol=1e-10, max_iter=100000)
+    assert res["status"] == pdhg.OPTIMAL
+    up, lo = pdhg.dual_point(lp, res["lam_up"], res["lam_lo"])
+    assert np.array_equal(up, res["lam_up"]) and np.array_equal(lo, res["lam_lo"])
+    junk = np.full(lp.labels.size, -1.0)
+    up2, lo2 = pdhg.dual_point(lp, np.abs(junk), np.abs(junk))
+    assert np.all(up2[~(lp.band | lp.gel)] == 0) and np.all(lo2[~lp.gel] == 0)
+    assert np.all(pdhg.dual_point(lp, junk, junk)[0] == 0)
+    again = pdhg.solve(lp, ops, kkt_tol=1e-10, max_iter=100000, omega0=res["omega"],
+                       start=(res["y"], res["u"], res["v"]), dual_start=(res["lam_up"], res["lam_lo"]))
+    assert again["status"] == pdhg.OPTIMAL and again["iters"] == 0
+    # one more step from a point at KKT 1e-10 moves the objective within that tolerance
+    assert abs(again["obj"] - res["obj"]) <= 1e-9 * abs(res["obj"])
+
+
 def test_scale_invariance_bitwise_and_general():
     """f_T -> 2^k f_T leaves the normalised LP and the iterates bitwise unchanged;
     a general factor leaves the optimum unchanged (Sec. 2.5, Eq. 18)."""
