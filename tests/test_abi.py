@@ -68,3 +68,44 @@ def test_invalid_arguments_fail_before_device_work(lib):
     assert lib.sipo_destroy(None) == 0
     assert lib.sipo_phase_count() >= 3
     assert lib.sipo_phase_name(0) == b"scalar_step"
+
+
+def test_new_entries_validate_before_device_work(lib):
+    """Bounded creation, the response map and metrics, the state import /
+    export and the primal start refuse bad arguments before any CUDA call."""
+    from paper_2604_08997_gb300 import _abi
+    ang = np.zeros(4)
+    g = _abi.sipo_geometry()
+    g.nx, g.ny, g.nz, g.n_angles, g.n_det = 8, 8, 1, 4, 9
+    g.angles = ang.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    tl = _abi.sipo_tolerances(1e-4, 100, 64, 0, -1, 0.0)
+    tgt = np.ones(64, np.float32)
+    p = ctypes.c_void_p(tgt.ctypes.data)
+    out = ctypes.c_void_p()
+    cp2 = _abi.sipo_case_params(2, 1.0, 1.0, 0.05, 0.05, 0.8, 2)
+    rc = lib.sipo_create_bounded(ctypes.byref(g), p, p, p, 0, ctypes.byref(cp2), ctypes.byref(tl), None,
+                                 ctypes.byref(out))
+    assert rc == -1 and b"Case-1" in lib.sipo_last_error()
+    cp1 = _abi.sipo_case_params(1, 1.0, 1.0, 0.05, 0.05, 0.8, 2)
+    rc = lib.sipo_create_bounded(ctypes.byref(g), p, None, p, 0, ctypes.byref(cp1), ctypes.byref(tl), None,
+                                 ctypes.byref(out))
+    assert rc == -1 and b"null" in lib.sipo_last_error()
+    for bad in ((0.0, 0.0, 8.0, 0.7, 0.5), (0.0, 1.0, -1.0, 0.7, 0.5), (0.0, 1.0, 8.0, 0.0, 0.5),
+                (float("nan"), 1.0, 8.0, 0.7, 0.5)):
+        r = _abi.sipo_response(*bad)
+        rc = lib.sipo_response_map(ctypes.byref(r), p, p, 64, 1.0, 1, None)
+        assert rc == -1 and b"response model" in lib.sipo_last_error()
+        res = _abi.sipo_response_result()
+        rc = lib.sipo_response_metrics(None, ctypes.byref(r), p, 0, 0.0, ctypes.byref(res))
+        assert rc == -1
+    good = _abi.sipo_response(0.0, 1.0, 8.0, 0.7, 0.5)
+    assert lib.sipo_response_map(ctypes.byref(good), p, p, 0, 1.0, 1, None) == 0     # empty: no work
+    rc = lib.sipo_response_map(ctypes.byref(good), p, p, 64, float("inf"), 1, None)
+    assert rc == -1 and b"scale" in lib.sipo_last_error()
+    rc = lib.sipo_response_map(ctypes.byref(good), None, p, 64, 1.0, 1, None)
+    assert rc == -1 and b"null" in lib.sipo_last_error()
+    sc = (ctypes.c_double * 4)()
+    assert lib.sipo_get_state(None, None, None, None, 0, sc) == -1
+    assert lib.sipo_set_state(None, p, p, p, 0, sc) == -1
+    assert lib.sipo_set_primal(None, p, 0, -1.0, -1.0) == -1
+    assert b"null" in lib.sipo_last_error()
