@@ -79,7 +79,7 @@ def response_case2(geometry: dict, m_T, M: Richards, m_crit: float, band_width: 
     m = _device(m_T)
     f_T = response_to_dose(M, m)
     gel_min = m[m > M.alpha].min().reshape(1)
-    ends = response_to_dose(M, torch.cat([torch.tensor([m_crit], dtype=torch.float32, device="cuda"),
+    ends = response_to_dose(M, torch.cat([torch.tensor([m_crit], dtype=torch.float32, device=m.device),
                                           gel_min]))
     ratio = float(ends[0]) / float(ends[1])
     return sipo_create(geometry, f_T, dict(kase=SIPO_CASE2, inhibit_ratio=ratio, band_width=band_width),
