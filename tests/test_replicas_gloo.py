@@ -39,7 +39,7 @@ def _worker(rank, world, port, out):
 def test_max_over_ranks_and_weak_scaling_value():
     world = 2
     port = _free_port()
-    manager = mp.Manager()
+    manager = mp.get_context("spawn").Manager()   # no fork of this multi-threaded process
     out = manager.dict()
     mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
     assert out[0] == out[1] == 2.0
