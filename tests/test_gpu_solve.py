@@ -475,3 +475,31 @@ def test_resume_at_an_optimum_and_bf16_checkpoint(sipo):
     assert np.array_equal(ys[0], y_out) and np.array_equal(ys[1], y_out)
     with pytest.raises(sipo.SipoError):
         sipo.sipo_get_state(sipo.sipo_create(geo, tgt, cp, tol), y, up, lo)
+
+
+def test_host_injected_failures_are_errors_or_statuses(sipo):
+    """Failures injected on the host, none of which faults the device: a NaN,
+    an infinite and a negative target value and an all-zero target are
+    refused with INVALID_ARG (-1) and leave no context; an iteration limit
+    is a status, not an error; changing a setting fixed at creation is
+    refused and leaves the context usable."""
+    case, extra = TINY[2]
+    lp, ops, geo, tgt, cp = _tiny(case, extra)
+    tol = dict(storage=sipo.SIPO_F64, kkt_tol=1e-9, max_iter=64)
+    for bad in (np.nan, np.inf, -1.0):
+        t = tgt.copy()
+        t.flat[0] = bad
+        with pytest.raises(sipo.SipoError) as e:
+            sipo.sipo_create(geo, t, cp, tol)
+        assert e.value.code == -1 and "target" in str(e.value)
+    with pytest.raises(sipo.SipoError) as e:
+        sipo.sipo_create(geo, np.zeros_like(tgt), cp, tol)
+    assert e.value.code == -1 and "empty" in str(e.value)
+    ctx = sipo.sipo_create(geo, tgt, cp, tol)
+    res = sipo.sipo_solve(ctx)
+    assert res["status"] == sipo.SIPO_ITER_LIMIT and res["iters"] == 64
+    with pytest.raises(sipo.SipoError):
+        sipo.sipo_set_tolerances(ctx, 1e-9, 100000, check_every=32)
+    sipo.sipo_set_tolerances(ctx, 1e-9, 100000)
+    res = sipo.sipo_solve(ctx)
+    assert res["status"] == sipo.SIPO_OPTIMAL
