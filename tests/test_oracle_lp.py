@@ -108,7 +108,7 @@ def test_infeasible_case2_reported_by_both():
     assert res["status"] == pdhg.PRIMAL_INFEASIBLE
 
 
-def _highs(lp, ops):
+def _highs(lp, ops, method="highs"):
     act = np.flatnonzero(lp.active)
     M = ops.PT[:, act]
     band, gel = np.flatnonzero(lp.band), np.flatnonzero(lp.gel)
@@ -127,7 +127,7 @@ def _highs(lp, ops):
     c[ny + 1] = lp.c_v if lp.has_v else 0.0
     bounds = [(0, None)] * ny + [(None, None) if lp.has_u else (0, 0),
                                  (None, None) if lp.has_v else (0, 0)]
-    res = linprog(c, A_ub=G, b_ub=h, bounds=bounds, method="highs")
+    res = linprog(c, A_ub=G, b_ub=h, bounds=bounds, method=method)
     return res
 
 
@@ -545,3 +545,21 @@ def test_bound_certificate_detects_blurred_inhibition(monkeypatch):
     monkeypatch.setattr(pdhg, "certificate", lambda *a: False)
     res = pdhg.solve(lp, ops, kkt_tol=1e-4, max_iter=1024)
     assert res["status"] == pdhg.ITER_LIMIT
+
+
+def test_disc64_golden_matches_highs():
+    """The stored Case-1 optimum of the 64x64 / 96-angle / 91-bin workload
+    (tests/golden/disc64_case1.json, written by the oracle's PDHG) against
+    scipy's HiGHS on the same LP (Eqs. 32-37, delta = 0.05); its interior-point
+    method with crossover finishes in seconds where the simplex takes minutes."""
+    import json
+    import os
+    from synthetic.targets import workload
+    with open(os.path.join(os.path.dirname(__file__), "golden", "disc64_case1.json")) as f:
+        gold = json.load(f)
+    wl = workload("disc64")
+    lp, ops = build_lp(Geometry(64, 64, 1, wl.angles, 91), wl.target,
+                       CaseParams(case=CASE1, tol_lo=0.05, tol_hi=0.05, band_width=10))
+    ref = _highs(lp, ops, method="highs-ipm")
+    assert ref.status == 0
+    assert abs(gold["objective"] - ref.fun) <= 1e-7 * abs(ref.fun)
