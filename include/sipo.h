@@ -360,28 +360,37 @@ int sipo_get_trace(sipo_ctx *ctx, double *out, int max_entries);
 int sipo_set_tolerances(sipo_ctx *ctx, const sipo_tolerances *tol);
 
 /* Dose-field metrics for callers that cannot allocate device memory.
- * The paper has no counterpart to this entry point: it repeats the metrics
- * pass that ends sipo_solve (DTVR_f and DSR of Eq. 8, PSR_f of Eq. 46, alpha*
- * of Eq. 27, s = min_gel d / f~_L) for callers that may not call cudaMalloc --
- * a print controller that must not allocate once its real-time loop runs, or
+ * The paper has no counterpart to this entry point.  It repeats the metrics
+ * pass that ends sipo_solve for callers that may not call cudaMalloc -- a
+ * print controller that must not allocate once its real-time loop runs, or
  * code living inside a framework whose caching allocator owns the device
- * memory budget.  It calls no cudaMalloc, cudaFree or other allocating
- * routine: its per-block partial sums live in a static device array of the
- * library (8 x 8192 + 8 doubles, 512 KiB, held by every GPU that loads the
- * library until the process exits).
+ * memory budget.  The five outputs, over gel voxels (label 2) and band voxels
+ * (label 1) of the dose d: dtvr_f = max(d / f~_T) / min(d / f~_T) with
+ * f~_T = f_T / f_crit; dsr = max_band d / min_gel(d / f~_T); psr_f =
+ * min_gel d / max_band d; alpha = sum_gel d f_T / sum_gel d^2; s =
+ * min_gel d / (lower_scale f_T).  It calls no cudaMalloc, cudaFree or other
+ * allocating routine: its per-block partial sums live in a static device
+ * array of the library (8 x 8192 + 8 doubles, 512 KiB, held by every GPU that
+ * loads the library until the process exits).
  * dose: device volume of n_voxels elements of `dtype` (SIPO_F32 or SIPO_F64),
- *   e.g. sipo_get_array(ctx, 5, ...); labels: device uint8 region labels
- *   (sipo_get_array(ctx, 0, ...)); f_T: device float32 target, same layout.
- * f_crit: the normalisation dose (sipo_result.f_crit); lower_scale: f~_L / f_T,
- *   i.e. 1/f_crit for the general form and Case 2, (1 - tol_lo)/f_crit for
- *   Case 1.
+ *   e.g. sipo_get_array(ctx, 5, ...); labels: device uint8 region labels of
+ *   n_voxels bytes (sipo_get_array(ctx, 0, ...)); f_T: device float32 target
+ *   of n_voxels elements, same layout.  The caller guarantees those sizes.
+ * f_crit: the normalisation dose (sipo_result.f_crit); lower_scale: the ratio
+ *   f~_L / f_T of the lower-bound profile, i.e. 1/f_crit for the general form
+ *   and Case 2, (1 - tol_lo)/f_crit for Case 1 with tolerances.  s equals
+ *   sipo_result.s only when the lower profile is such a multiple of f_T; for a
+ *   context made by sipo_create_bounded (explicit per-voxel f_L) it does not.
  * metrics: host array of 5 doubles: dtvr_f, dsr, psr_f, alpha, s.
  * n_voxels above 134217728 (8192 blocks x 256 threads x 64 voxels) is
  * rejected with SIPO_ERR_INVALID_ARG.  The first call with a device current
- * looks up the array's device address for that device; make it before any
- * stream capture.  Calls share the array (each overwrites it completely);
- * calls that overlap on the GPU race on it and must be serialised by the
- * caller.  Synchronises `stream` (NULL: the legacy default stream). */
+ * looks up the array's device address for that device (cudaGetSymbolAddress)
+ * and keeps it for the life of the process: make that first call before any
+ * stream capture, and do not call this entry point again after a
+ * cudaDeviceReset of that device.  Calls share the array (each overwrites it
+ * completely); calls that overlap on the GPU race on it and must be
+ * serialised by the caller.  Synchronises `stream` (NULL: the legacy default
+ * stream). */
 int sipo_dose_metrics_noalloc(const void *dose, int dtype, const uint8_t *labels, const float *f_T,
                               long long n_voxels, double f_crit, double lower_scale,
                               double *metrics, void *stream);

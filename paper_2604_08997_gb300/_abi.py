@@ -471,15 +471,32 @@ def sipo_get_trace(ctx: Context, max_entries: int = 4096) -> np.ndarray:
 def sipo_dose_metrics_noalloc(dose, labels, f_T, f_crit: float, lower_scale: float,
                               stream=None) -> np.ndarray:
     """Metrics of a device dose field without device allocation (see include/sipo.h):
-    returns [dtvr_f, dsr, psr_f, alpha, s]."""
+    returns [dtvr_f, dsr, psr_f, alpha, s].
+
+    dose (float32 or float64), labels (uint8) and f_T (float32) must be device
+    tensors of the same number of elements on one device; anything else is
+    refused here, before the library is called, because the kernel reads
+    n = dose.numel() elements of each."""
+    if str(labels.dtype) not in ("torch.uint8", "uint8"):
+        raise ValueError(f"labels must be uint8, got {labels.dtype}")
+    if str(f_T.dtype) not in ("torch.float32", "float32"):
+        raise ValueError(f"f_T must be float32, got {f_T.dtype}")
+    code = _dtype_code(dose)
+    n = int(dose.numel()) if hasattr(dose, "numel") else int(dose.size)
+    for name, a in (("labels", labels), ("f_T", f_T)):
+        m = int(a.numel()) if hasattr(a, "numel") else int(a.size)
+        if m != n:
+            raise ValueError(f"{name} has {m} elements, dose has {n}")
     pd, ld = _ptr(dose)
     pl, ll = _ptr(labels)
     pf, lf = _ptr(f_T)
     if SIPO_HOST in (ld, ll, lf):
         raise ValueError("dose, labels and f_T must be device tensors")
+    if not (dose.device == labels.device == f_T.device):
+        raise ValueError("dose, labels and f_T must be on one device")
     out = (c_double * 5)()
-    _check(load().sipo_dose_metrics_noalloc(c_void_p(pd), _dtype_code(dose), c_void_p(pl),
-                                            c_void_p(pf), int(dose.numel()), float(f_crit),
+    _check(load().sipo_dose_metrics_noalloc(c_void_p(pd), code, c_void_p(pl),
+                                            c_void_p(pf), n, float(f_crit),
                                             float(lower_scale), out, _stream(stream)))
     return np.array(list(out))
 

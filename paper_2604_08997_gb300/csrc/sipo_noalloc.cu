@@ -12,6 +12,9 @@
 // holds it (8 x 8192 + 8 doubles, 512 KiB) until the process exits.  Its address is
 // looked up once per device with cudaGetSymbolAddress by the first call made
 // with that device current; make that first call before any stream capture.
+// The address is kept for the life of the process, keyed by device ordinal:
+// it stays valid while the device's primary context lives, so the entry
+// point must not be called again after a cudaDeviceReset of that device.
 // All calls share the array and overwrite it completely, so nothing needs
 // clearing, but calls that overlap on the GPU (concurrent streams, several
 // host threads) race on it and must be serialised by the caller.
@@ -177,11 +180,11 @@ int sipo_dose_metrics_noalloc(const void* dose, int dtype, const uint8_t* labels
   if (e != cudaSuccess) return na_fail(SIPO_ERR_CUDA, std::string("sipo_dose_metrics_noalloc: ") + cudaGetErrorString(e));
   const double mn_r = h[0], mx_r = h[1], mx_b = h[2], mn_d = h[3];
   const bool has_band = mx_b > -1e299;
-  metrics[0] = mn_r > 0 ? mx_r / mn_r : INFINITY;                 // DTVR_f (Eq. 8)
-  metrics[1] = (mn_r > 0 && has_band) ? mx_b / mn_r : INFINITY;   // DSR (Eq. 8)
-  metrics[2] = (has_band && mx_b > 0) ? mn_d / mx_b : INFINITY;   // PSR_f (Eq. 46)
-  metrics[3] = h[5] > 0 ? h[4] / h[5] : 0.0;                      // alpha* (Eq. 27)
-  metrics[4] = h[6];                                              // s = min_gel d / f~_L
+  metrics[0] = mn_r > 0 ? mx_r / mn_r : INFINITY;                 // max / min gel ratio d / f~_T
+  metrics[1] = (mn_r > 0 && has_band) ? mx_b / mn_r : INFINITY;   // band maximum over the minimum ratio
+  metrics[2] = (has_band && mx_b > 0) ? mn_d / mx_b : INFINITY;   // gel minimum over band maximum
+  metrics[3] = h[5] > 0 ? h[4] / h[5] : 0.0;                      // least-squares scale onto f_T
+  metrics[4] = h[6];                                              // min_gel d / (lower_scale f_T)
   return SIPO_OK;
 }
 

@@ -109,3 +109,23 @@ def test_new_entries_validate_before_device_work(lib):
     assert lib.sipo_set_state(None, p, p, p, 0, sc) == -1
     assert lib.sipo_set_primal(None, p, 0, -1.0, -1.0) == -1
     assert b"null" in lib.sipo_last_error()
+
+
+def test_noalloc_wrapper_refuses_mismatched_buffers():
+    """The scratch-free metrics wrapper checks dtypes, sizes and locations on the
+    host; each mismatch raises before the library is loaded or called."""
+    torch = pytest.importorskip("torch")
+    from paper_2604_08997_gb300 import _abi
+    d = torch.zeros(8)
+    lab = torch.zeros(8, dtype=torch.uint8)
+    f = torch.ones(8)
+    cases = [
+        (d, lab.to(torch.int32), f, "labels must be uint8"),
+        (d, lab, f.double(), "f_T must be float32"),
+        (d, lab[:7], f, "labels has 7 elements"),
+        (d, lab, f[:6], "f_T has 6 elements"),
+        (d, lab, f, "must be device tensors"),
+    ]
+    for dose, labels, ft, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            _abi.sipo_dose_metrics_noalloc(dose, labels, ft, 1.0, 1.0)
