@@ -55,6 +55,15 @@ The readings implemented here (and by the GPU solver) are published methods:
   kappa B <= (1 - 1e-3) obj, the margin covering rounding of g^.  The
   general case has no constant upper rows (every LP of that form is
   feasible) and no such test.
+* Slice by slice (a reading of the slice-separable forward model of
+  Sec. 2.3): when the PSF has no z extent, A maps the rays of slice z only to
+  the voxels of slice z, so both inequalities above hold for each slice on
+  its own -- y_z^T g^_z <= -obj_z and y_z^T g^_z >= -kappa_z B_z, with obj_z,
+  kappa_z and B_z the same quantities restricted to slice z.  One slice with
+  obj_z > kappa_z B_z (margin as above) proves the whole LP infeasible.  This
+  test implies the whole-volume one (if obj > kappa B then some slice has
+  obj_z > kappa_z B_z), and it is not diluted by feasible slices: a single
+  infeasible slice among many feasible ones carries the certificate alone.
 """
 from __future__ import annotations
 
@@ -148,42 +157,62 @@ def _farkas(lp, pc, dq_g, dlam_up, dlam_lo):
 
 
 def certificate_data(lp: LPData, ops: Operators):
-    """(b, B) of the bound-based certificate: b = A 1_rows on every ray and
+    """(b, B, B_z) of the bound-based certificate: b = A 1_rows on every ray,
     B = sum of the constant upper bounds over those rows (Case 2: band rows,
-    bound 1; Case 1: gel rows, bound f~_U); None for the general case."""
+    bound 1; Case 1: gel rows, bound f~_U) and B_z the same sum per z-slice;
+    None for the general case."""
+    g = ops.geo
     if lp.case == CASE2:
-        rows, B = lp.band, float(lp.band.sum())
+        rows = lp.band
+        U = rows.astype(np.float64)
     elif lp.case == CASE1:
-        rows, B = lp.gel, float(np.sum(lp.upper[lp.gel]))
+        rows = lp.gel
+        U = np.where(rows, lp.upper, 0.0)
     else:
         return None
-    b = ops.A(rows.astype(np.float64).reshape(ops.geo.vol_shape)).ravel()
-    return b, B
+    b = ops.A(rows.astype(np.float64).reshape(g.vol_shape)).ravel()
+    B_z = U.reshape(g.vol_shape).sum(axis=(0, 1))
+    return b, float(U.sum()), B_z
 
 
-def certificate(lp: LPData, ops: Operators, dlam_up, dlam_lo, b, B) -> bool:
+def slices_decoupled(ops: Operators) -> bool:
+    """True when A maps each z-slice's rays to that slice's voxels only: the
+    parallel-beam operator is slice-separable (Sec. 2.3) and only a PSF with a
+    z extent couples slices."""
+    return ops.geo.nz > 1 and ops.geo.psf_radii()[2] == 0
+
+
+def certificate(lp: LPData, ops: Operators, dlam_up, dlam_lo, b, B, B_z=None, per_slice=True):
     """True if the projected dual difference proves primal infeasibility
-    (bound-based Farkas test of the module docstring)."""
+    (bound-based Farkas test of the module docstring), slice by slice when
+    the operator does not couple z-slices."""
     band, gel = lp.band, lp.gel
     lu = np.zeros(lp.labels.size)
     ll = np.zeros(lp.labels.size)
     ll[gel] = np.maximum(dlam_lo[gel], 0.0)
-    obj = np.sum(lp.lower[gel] * ll[gel])
     if lp.case == CASE2:
         lu[band] = np.maximum(dlam_up[band], 0.0)
-        obj -= lu[band].sum()
+        objv = lp.lower * ll - lu
     else:
         lu[gel] = np.maximum(dlam_up[gel], 0.0)
-        obj -= np.sum(lp.upper[gel] * lu[gel])
-    if not obj > 0:
-        return False
+        objv = lp.lower * ll - lp.upper * lu
+    objv = np.where(gel | band, objv, 0.0)
     g = ops.A((lu - ll).reshape(ops.geo.vol_shape)).ravel()
     act = lp.active
-    viol = np.maximum(-g[act], 0.0)
-    ba = b[act]
-    if np.any((viol > 0) & (ba <= 0)):
+    viol = np.where(act, np.maximum(-g, 0.0), 0.0)
+    bad = (viol > 0) & (b <= 0)
+    ratio = np.where(viol > 0, viol / np.where(b > 0, b, 1.0), 0.0)
+    if per_slice and B_z is not None and slices_decoupled(ops):
+        geo = ops.geo
+        obj_z = objv.reshape(geo.vol_shape).sum(axis=(0, 1))
+        kappa_z = ratio.reshape(geo.sino_shape).max(axis=(0, 1))
+        bad_z = bad.reshape(geo.sino_shape).any(axis=(0, 1))
+        ok = (obj_z > 0) & ~bad_z & (kappa_z * B_z <= (1.0 - CERT_MARGIN) * obj_z)
+        return bool(ok.any())
+    obj = float(objv.sum())
+    if not obj > 0 or bad.any():
         return False
-    kappa = np.max(np.where(viol > 0, viol / np.where(ba > 0, ba, 1.0), 0.0), initial=0.0)
+    kappa = float(ratio.max(initial=0.0))
     return kappa * B <= (1.0 - CERT_MARGIN) * obj
 
 

@@ -484,7 +484,7 @@ def _best_certificate(lp, ops):
     gel = np.flatnonzero(lp.gel)
     up = np.flatnonzero(lp.band) if lp.case == CASE2 else gel
     U = np.ones(up.size) if lp.case == CASE2 else lp.upper[gel]
-    b, B = pdhg.certificate_data(lp, ops)
+    b, B, _ = pdhg.certificate_data(lp, ops)
     Au = ops.PT[up][:, act].T.toarray()
     Ag = ops.PT[gel][:, act].T.toarray()
     nu, ng = up.size, gel.size
@@ -563,3 +563,103 @@ def test_disc64_golden_matches_highs():
     ref = _highs(lp, ops, method="highs-ipm")
     assert ref.status == 0
     assert abs(gold["objective"] - ref.fun) <= 1e-7 * abs(ref.fun)
+
+
+def _slice_stack(nz, bad_z, ratio=0.62):
+    """Case 2 on a stack of 12x12 slices (10 views, 17 bins): every slice holds
+    a disc pattern feasible at this ratio except slice bad_z, whose disc needs
+    more contrast than the ratio allows (thresholds found by HiGHS below)."""
+    n, na, nd = 12, 10, 17
+    feas = [discs_2d(n, n_discs=1, r_range=(2.5, 3.5), container_radius=4.5, seed=3),
+            discs_2d(n, n_discs=3, r_range=(1.0, 1.6), container_radius=4.5, seed=3),
+            discs_2d(n, n_discs=1, r_range=(2.5, 3.5), container_radius=4.5, seed=5)]
+    bad = discs_2d(n, n_discs=1, r_range=(2.5, 3.5), container_radius=4.5, seed=1)
+    sl = [feas[i % 3] for i in range(nz)]
+    if bad_z is not None:
+        sl[bad_z] = bad
+    tgt = np.concatenate(sl, axis=2)
+    return build_lp(Geometry(n, n, nz, uniform_angles(na), nd), tgt,
+                    CaseParams(case=CASE2, inhibit_ratio=ratio, band_width=2))
+
+
+def _slice_rows_rays(lp, ops, z):
+    """2-D indices (into the per-slice matrix ops.PT) of slice z's band rows,
+    gel rows and active rays, and their flat 3-D indices."""
+    nz = ops.geo.nz
+    vz = np.arange(lp.labels.size) % nz == z
+    band3, gel3 = np.flatnonzero(lp.band & vz), np.flatnonzero(lp.gel & vz)
+    act3 = np.flatnonzero(lp.active & (np.arange(lp.active.size) % nz == z))
+    return band3 // nz, gel3 // nz, act3 // nz, band3, gel3, act3
+
+
+def _slice_feasible(lp, ops, z):
+    """HiGHS on the rows and rays of slice z alone (the operator is P_2D on
+    every slice, block diagonal over z without a z-extent PSF)."""
+    band, gel, act, _, gel3, _ = _slice_rows_rays(lp, ops, z)
+    M = ops.PT[:, act]
+    G = sp.vstack([M[band], -M[gel]]).tocsr()
+    h = np.concatenate([np.ones(band.size), -lp.lower[gel3]])
+    r = linprog(np.zeros(act.size), A_ub=G, b_ub=h, bounds=[(0, None)] * act.size, method="highs")
+    return r.status == 0
+
+
+def _slice_best_certificate(lp, ops, z):
+    """_best_certificate restricted to slice z: the largest obj_z - B_z kappa_z
+    and its maximiser embedded in full-length dual vectors."""
+    up, gel, act, up3, gel3, act3 = _slice_rows_rays(lp, ops, z)
+    b, _, B_z = pdhg.certificate_data(lp, ops)
+    Au = ops.PT[up][:, act].T.toarray()
+    Ag = ops.PT[gel][:, act].T.toarray()
+    nu, ng = up.size, gel.size
+    G = np.hstack([-Au, Ag, -b[act3][:, None]])
+    G = np.vstack([G, np.concatenate([np.ones(nu + ng), [0.0]])[None, :]])
+    h = np.concatenate([np.zeros(act.size), [1.0]])
+    c = np.concatenate([np.ones(nu), -lp.lower[gel3], [B_z[z]]])
+    res = linprog(c, A_ub=G, b_ub=h, bounds=[(0, None)] * (nu + ng + 1), method="highs")
+    assert res.status == 0
+    lu = np.zeros(lp.labels.size)
+    ll = np.zeros(lp.labels.size)
+    lu[up3] = res.x[:nu]
+    ll[gel3] = res.x[nu:nu + ng]
+    return -res.fun, lu, ll
+
+
+def test_per_slice_certificate_is_sound_and_names_the_slice():
+    """Without a z-extent PSF the LP is feasible iff every slice is (HiGHS per
+    slice).  The best per-slice candidate of each feasible slice cannot pass the
+    slice test; the infeasible slice's passes it.  Add a small uniform lam_lo
+    on the gel rows of every other slice (the residue an iteration leaves on
+    feasible slices): the slice test still accepts, the whole-volume test,
+    whose kappa is a maximum over all slices and whose B sums them, does not."""
+    nz, bad_z = 8, 4
+    lp, ops = _slice_stack(nz, bad_z)
+    assert pdhg.slices_decoupled(ops)
+    feasible = [_slice_feasible(lp, ops, z) for z in range(nz)]
+    assert feasible == [z != bad_z for z in range(nz)]
+    data = pdhg.certificate_data(lp, ops)
+    for z in range(nz):
+        val, lu, ll = _slice_best_certificate(lp, ops, z)
+        if z == bad_z:
+            assert val > 1e-3
+            assert pdhg.certificate(lp, ops, lu, ll, *data)
+            other = lp.gel & (np.arange(lp.labels.size) % nz != z)
+            ll2 = ll + 1e-4 * other
+            assert pdhg.certificate(lp, ops, lu, ll2, *data)
+            assert not pdhg.certificate(lp, ops, lu, ll2, *data, per_slice=False)
+        else:
+            assert val <= 1e-9
+            assert not pdhg.certificate(lp, ops, lu, ll, *data)
+
+
+def test_per_slice_certificate_ends_the_solve_sooner(monkeypatch):
+    """The oracle PDHG on the 16-slice stack with one infeasible slice: with the
+    l_inf ray test switched off, the slice test proves infeasibility within
+    5120 iterations; the whole-volume test alone needs more."""
+    lp, ops = _slice_stack(16, 8)
+    monkeypatch.setattr(pdhg, "_farkas", lambda *a, **k: False)
+    res = pdhg.solve(lp, ops, kkt_tol=1e-7, max_iter=5120)
+    assert res["status"] == pdhg.PRIMAL_INFEASIBLE
+    whole = pdhg.certificate
+    monkeypatch.setattr(pdhg, "certificate", lambda *a, **k: whole(*a, per_slice=False))
+    res = pdhg.solve(lp, ops, kkt_tol=1e-7, max_iter=5120)
+    assert res["status"] == pdhg.ITER_LIMIT
