@@ -37,16 +37,27 @@ if ROOT not in sys.path:
 
 METRIC = "PDHG iter/s and time-to-1e-4 KKT at 256³×360 views; projector GB/s vs HBM"
 FP32_LANES_PER_SM = 128
-SM_COUNT = 152
-SM_MAX_MHZ = 2070.0
+
+
+def sm_count(device=None) -> int:
+    """Streaming multiprocessors of the device (cudaDeviceProp.multiProcessorCount)."""
+    import torch
+    return int(torch.cuda.get_device_properties(device if device is not None else 0).multi_processor_count)
+
+
+def sm_max_mhz(peaks: dict) -> float:
+    """Maximum SM clock: the measured value, else the GB300 specification (2070 MHz)."""
+    try:
+        return float(peaks.get("sm_max_mhz", 2070.0))
+    except (TypeError, ValueError):
+        return 2070.0
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# two fused operator kernels, from one ncu capture of this workload
-# (profiles/k_project_csg256_f32.md, profiles/k_backproject_csg256_f32.md).
-# It is reported only while the kernel sources (code, comments aside) still
-# hash to the value they had at the capture; after any change to the code it
-# is null until re-captured.
+# two fused operator kernels, from one single-pass ncu capture of this
+# workload.  It is reported only while the kernel sources (code, comments
+# aside) still hash to the value they had at the capture; after any change to
+# the code it is null until re-captured.
 KERNEL_SOURCES = ["sipo_device.cuh", "sipo_solver.cuh", "sipo_ops.cuh", "sipo_launch.h",
                   "sipo_project.cu", "sipo_backproject.cu"]
 TRAFFIC = {("csg256", "f32"): {"sources_sha256_16": "adc961dbddc52893",
@@ -333,22 +344,23 @@ def run_gpu(args, dist, rank, world, device):
     bytes_bp = S * el + need_cols * wl.nz * (4 * el + 2 * cw + 1 + 2 * el + cw + el)
     bytes_fp = wl.n * wl.n * wl.nz * el + act_cols * wl.nz * (cw + 2 * el + 2 * el)
     clk = clocks.summary()
-    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = 2.0 * taps / (dom_ms * 1e-3) / 1e12
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
+    n_sm, mhz = sm_count(device), sm_max_mhz(peaks)
+    peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    achieved = 2.0 * taps / (dom_ms * 1e-3) / 1e12
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops,
                 "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
-                "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x "
-                               f"{SM_MAX_MHZ:.0f} MHz (no measured FP32 peak exists)",
+                "peak_source": f"derived: {n_sm} SMs (cudaDeviceProp) x {FP32_LANES_PER_SM} FP32 lanes x "
+                               f"2 FLOP x {mhz:.0f} MHz (no measured FP32 peak exists)",
                 "units": "taps (one FMA = 2 FLOP per tap per z value)", "units_per_launch": taps,
                 "avg_launch_ms": dom_ms,
-                "l1_roof_frac": (taps / (dom_ms * 1e-3)) / (SM_COUNT * 32 * SM_MAX_MHZ * 1e6),
+                "l1_roof_frac": (taps / (dom_ms * 1e-3)) / (n_sm * 32 * mhz * 1e6),
                 "backproject": {"ms": bp_ms, "taps": bp_taps,
                                 "tflops": 2.0 * bp_taps / (bp_ms * 1e-3) / 1e12,
                                 "alg_bytes": bytes_bp, "gbs": bytes_bp / (bp_ms * 1e-3) / 1e9,

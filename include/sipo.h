@@ -144,6 +144,9 @@ typedef struct sipo_result {
   double solve_ms;
   long long kernel_launches;
   int tile_cfg; /* backprojector tile table entry in use */
+  int cert_slice; /* PRIMAL_INFEASIBLE proved by the bound-based test on one
+                     z-slice (operators without z coupling): that slice's
+                     index; -1 otherwise */
 } sipo_result;
 
 /* Creates a solver context: copies the geometry and the target dose f_T
@@ -220,7 +223,11 @@ int sipo_response_metrics(sipo_ctx *ctx, const sipo_response *M, const float *m_
 
 /* Runs the restarted Halpern PDHG (Sec. 2.8) from a zero start until the
  * KKT tolerance, a primal-infeasibility certificate or max_iter, then the
- * post-solve metrics.  y_out (nullable) receives y*, the normalised
+ * post-solve metrics of f~* = A^T y* (recomputed by one operator application
+ * at the returned point).  Without a PSF extent along z the bound-based
+ * certificate is tested slice by slice (the forward model is slice-separable,
+ * Sec. 2.3: one infeasible slice makes the LP infeasible), and
+ * res->cert_slice names the slice.  y_out (nullable) receives y*, the normalised
  * projection of Eq. 18, as [n_angles][n_det][nz] in FP32 (FP64 when storage
  * is SIPO_F64), host or device per y_location.  Blocks until done.  Errors:
  * INVALID_ARG, CUDA, TIMEOUT. */
@@ -280,6 +287,19 @@ int sipo_set_state(sipo_ctx *ctx, const void *y, const void *lam_up, const void 
  * INVALID_ARG (null, bad location), CUDA. */
 int sipo_set_primal(sipo_ctx *ctx, const void *y, int y_location, double u, double v);
 
+/* Primal start taken from another context on the device, for the two-stage
+ * design of Sec. 3.2 without a host round trip: the point y that src's most
+ * recent sipo_solve returned (its last check's T(z), in src's storage type),
+ * multiplied by `scale` (finite, > 0), becomes dst's primal start exactly as
+ * sipo_set_primal would make it (projected onto the primal domain; u, v as
+ * there; duals zero).  The Case-1 -> Case-2 transfer passes scale = 1 / r,
+ * the stage-1 dose over (1 - d_lo) in stage-2 normalised units.  Both
+ * contexts must have the same geometry (sizes, angles, vial, attenuation,
+ * PSF) and device; their LP cases may differ.  Synchronises both streams.
+ * Errors: INVALID_ARG (null, same context, scale, geometry mismatch, src not
+ * solved), CUDA. */
+int sipo_set_primal_from(sipo_ctx *dst, const sipo_ctx *src, double scale, double u, double v);
+
 /* Solves n independent contexts as one batch (a parameter sweep): one CUDA
  * graph holds one check period of every context as parallel branches (each on
  * its context's stream), so small LPs share the device and the host waits
@@ -338,7 +358,10 @@ const char *sipo_phase_name(int i);
 
 /* Number of entries in the backprojector tile table (for sipo_tolerances.tile_cfg):
  * 0 = 8 voxel columns per warp at 2 blocks/SM, 1 = 4 columns at 2 blocks/SM,
- * 2 = 4 columns at 3 blocks/SM. */
+ * 2 = 4 columns at 3 blocks/SM, 3 and 4 = the single-precision row-pattern
+ * kernel (4 columns, the rows of each angle in registers, packed FP32
+ * multiply-adds) at 2 and 3 blocks/SM; FP64 contexts run entry 2 for 3 and 4.
+ * Every entry gives the same sums bit for bit within one precision. */
 int sipo_tile_count(void);
 
 /* Total kernels this library has launched in this process (graph nodes count

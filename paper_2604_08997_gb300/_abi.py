@@ -49,7 +49,8 @@ class sipo_result(Structure):
                 ("gap", c_double), ("pobj", c_double), ("dobj", c_double), ("u", c_double),
                 ("v", c_double), ("omega", c_double), ("f_crit", c_double), ("alpha", c_double),
                 ("dtvr_f", c_double), ("dsr", c_double), ("psr_f", c_double), ("s", c_double),
-                ("solve_ms", c_double), ("kernel_launches", c_longlong), ("tile_cfg", c_int)]
+                ("solve_ms", c_double), ("kernel_launches", c_longlong), ("tile_cfg", c_int),
+                ("cert_slice", c_int)]
 
     def as_dict(self) -> dict:
         d = {name: getattr(self, name) for name, _ in self._fields_}
@@ -94,6 +95,7 @@ SIGNATURES = {
                                       POINTER(sipo_response_result)]),
     "sipo_warm_start": (c_int, [c_void_p, c_void_p]),
     "sipo_set_primal": (c_int, [c_void_p, c_void_p, c_int, c_double, c_double]),
+    "sipo_set_primal_from": (c_int, [c_void_p, c_void_p, c_double, c_double, c_double]),
     "sipo_get_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, POINTER(c_double)]),
     "sipo_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, POINTER(c_double)]),
     "sipo_project": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
@@ -342,6 +344,13 @@ def sipo_set_primal(ctx: Context, y, u: float = -1.0, v: float = -1.0) -> None:
     _check(load().sipo_set_primal(ctx.handle, c_void_p(p), loc, float(u), float(v)))
 
 
+def sipo_set_primal_from(dst: Context, src: Context, scale: float = 1.0, u: float = -1.0,
+                         v: float = -1.0) -> None:
+    """sipo_set_primal_from(dst, src, scale, u, v): dst's next solve starts from
+    scale times the point src's last solve returned, without leaving the device."""
+    _check(load().sipo_set_primal_from(dst.handle, src.handle, float(scale), float(u), float(v)))
+
+
 def sipo_get_state(ctx: Context, y, lam_up, lam_lo) -> dict:
     """Checkpoint: T(z) of ctx's last check into y [n_angles*n_det*nz], lam_up, lam_lo
     [ny*nx*nz] (compute dtype, all host or all CUDA); returns u, v, omega, iters."""
@@ -446,6 +455,11 @@ def sipo_profile(ctx: Context, iters: int) -> dict:
 
 def sipo_kernel_launch_count() -> int:
     return int(load().sipo_kernel_launch_count())
+
+
+def sipo_tile_count() -> int:
+    """Entries of the backprojector tile table (values of tolerances["tile_cfg"])."""
+    return int(load().sipo_tile_count())
 
 
 def sipo_set_tolerances(ctx: Context, kkt_tol: float, max_iter: int, check_every: int = 64,

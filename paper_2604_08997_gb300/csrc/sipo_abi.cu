@@ -49,7 +49,7 @@ void ck(cudaError_t e, const char* what) {
 
 int grid_for(long long n) {
   long long g = (n + kThreads - 1) / kThreads;
-  return int(std::max<long long>(1, std::min<long long>(g, 152LL * 16)));
+  return int(std::max<long long>(1, std::min<long long>(g, (long long)device_sms() * 16)));
 }
 
 struct SolverBase {
@@ -94,6 +94,9 @@ struct SolverBase {
   // start from a caller's point (y, lam_up, lam_lo, u~, v~, omega); null duals: zero
   virtual void state_from(const void* y, const void* lam_up, const void* lam_lo, int loc, double u, double v,
                           double omega) = 0;
+  // start from src's last returned primal point times `scale` (same geometry)
+  virtual void primal_from(const SolverBase& src, double scale, double u, double v) = 0;
+  virtual std::vector<double> geometry_fingerprint() const = 0;
   // the point T(z) of the last check: y, lam_up, lam_lo (compute type) and u~, v~, omega, k
   virtual void state_to(void* y, void* lam_up, void* lam_lo, int loc, double* scalars) = 0;
   // response-domain post-scaling and metrics of the last solve's dose
@@ -169,6 +172,11 @@ struct Solver final : SolverBase {
   C *cert_b = nullptr, *cert_q = nullptr;  // bound-based certificate: A 1_rows, candidate
   bool cert_on = false;
   double cert_B = 0.0;
+  // the certificate slice by slice (no PSF extent along z): B_z, the block
+  // partials of obj_z and the per-slice maxima kappa_z
+  bool cert_slices = false;
+  double *cert_Bz = nullptr, *cert_pz = nullptr;
+  unsigned long long* cert_kz = nullptr;
   Scal* st = nullptr;
   double* part = nullptr;
   double* trace = nullptr;
@@ -343,14 +351,48 @@ struct Solver final : SolverBase {
   // anchor, as after a restart; A^T y and A (lam_up - lam_lo) are recomputed.
   void state_from(const void* y_in, const void* up_in, const void* lo_in, int loc, double u, double v,
                   double omega) override {
-    init_state();
-    const Geo<C> g = geo();
-    const Bufs<S, C> B = bufs();
     const cudaMemcpyKind kind = loc == SIPO_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    init_state();
     C* ts = nullptr;
     ck(cudaMallocAsync(reinterpret_cast<void**>(&ts), SN * sizeof(C), stream), "state tmp");
     ck(cudaMemcpyAsync(ts, y_in, SN * sizeof(C), kind, stream), "state y");
-    k_import_primal<S, C><<<grid_for((long long)SN), kThreads, 0, stream>>>(ts, col, yp, (long long)SN);
+    start_from(ts, 1.0, up_in, lo_in, loc, u, v, omega);
+  }
+
+  std::vector<double> geometry_fingerprint() const override {
+    std::vector<double> f = {double(device), double(nx), double(ny), double(nz), double(na), double(nd),
+                             vial_r, mu, sigma[0], sigma[1], sigma[2], trunc};
+    f.insert(f.end(), angles.begin(), angles.end());
+    return f;
+  }
+
+  // The two-stage transfer on the device: src's returned point y (its last
+  // T(z), in src's storage type) times `scale` becomes this context's primal
+  // start, as sipo_set_primal would make it from a copy of it.
+  void primal_from(const SolverBase& src, double scale, double u, double v) override {
+    if (src.geometry_fingerprint() != geometry_fingerprint())
+      fail(SIPO_ERR_INVALID_ARG, "primal transfer: the contexts differ in geometry or device");
+    ck(cudaStreamSynchronize(src.strm()), "primal transfer: source");
+    const Point pt = src.point();
+    if (pt.st.k <= 0 && pt.st.done == 0)
+      fail(SIPO_ERR_INVALID_ARG, "primal transfer: the source context has not been solved");
+    init_state();
+    C* ts = nullptr;
+    ck(cudaMallocAsync(reinterpret_cast<void**>(&ts), SN * sizeof(C), stream), "state tmp");
+    convert_from<C>(pt.yp, pt.s_dtype, ts, (long long)SN, stream);
+    count(1);
+    start_from(ts, scale, nullptr, nullptr, SIPO_DEVICE, u, v, -1.0);
+  }
+
+  // Shared tail of the starts: ts (device, compute type, SN values, freed
+  // here) scaled and projected onto the primal domain becomes y; the duals
+  // as in state_from.
+  void start_from(C* ts, double scale, const void* up_in, const void* lo_in, int loc, double u, double v,
+                  double omega) {
+    const Geo<C> g = geo();
+    const Bufs<S, C> B = bufs();
+    const cudaMemcpyKind kind = loc == SIPO_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    k_import_primal<S, C><<<grid_for((long long)SN), kThreads, 0, stream>>>(ts, col, yp, C(scale), (long long)SN);
     ck(cudaFreeAsync(ts, stream), "free");
     // d = A^T y with the operator of a check step's plain backprojection
     launch_backproject<S, S, C, kBpStore, C>(g, yp, B, psf ? braw : dp, need, zl, stream, bp_nv);
@@ -569,7 +611,7 @@ struct Solver final : SolverBase {
     b.d = d; b.d0 = d0; b.dp = dp; b.row = row; b.ft = ft_is_const ? nullptr : ft; b.lab = lab;
     b.ft_const = ft_const; b.up_ratio = C(up_ratio); b.fu = fu; b.has_u = has_u; b.has_v = has_v;
     b.band_rhs = C(band_rhs); b.st = st; b.part = part;
-    b.cert_b = cert_b; b.cert_q = cert_q;
+    b.cert_b = cert_b; b.cert_q = cert_q; b.cert_kz = cert_kz;
     return b;
   }
 
@@ -699,7 +741,7 @@ struct Solver final : SolverBase {
       const int lpb = kThreads / std::min(nzg, kThreads);
       nb = ((long long)nx * ny + lpb - 1) / lpb;
     }
-    const int grid = int(std::max<long long>(1, std::min<long long>(nb, 152LL * 16)));
+    const int grid = int(std::max<long long>(1, std::min<long long>(nb, (long long)device_sms() * 16)));
     if (axis < 2) {
       if (vg == 4)
         k_conv_xy<TI, TO, C, 4><<<grid, kThreads, 0, s>>>(in, out, tp, r, nx, ny, nz, axis);
@@ -965,6 +1007,18 @@ struct Solver final : SolverBase {
       }
       cert_B = cp.kase == SIPO_CASE2 ? double(n_band) * band_rhs : (fu ? sums[7] : up_ratio * sums[2]);
       count(3);
+      // slice by slice when the operator does not couple z-slices
+      cert_slices = R[2] == 0 && nz > 1 && nz <= kCertMaxZ;
+      if (cert_slices) {
+        cert_Bz = dalloc<double>(size_t(nz));
+        cert_pz = dalloc<double>(size_t(kCertBlocks) * nz);
+        cert_kz = dalloc<unsigned long long>(size_t(nz));
+        k_cert_bz<C><<<kCertBlocks, kThreads, 0, stream>>>(lab, ft_is_const ? nullptr : ft, ft_const, fu,
+                                                            up_ratio, cp.kase, (long long)nx * ny, nz, cert_pz);
+        k_cert_zsum<<<(nz + kThreads - 1) / kThreads, kThreads, 0, stream>>>(cert_pz, kCertBlocks, nz, cert_Bz);
+        zero(cert_kz, size_t(nz));
+        count(2);
+      }
     }
     count(16);
     choose_tiles();
@@ -1003,6 +1057,9 @@ struct Solver final : SolverBase {
     h.cert_B = cert_B;
     h.cert_on = cert_on ? 1 : 0;
     h.cert = 0;
+    h.cert_slices = cert_slices ? 1 : 0;
+    h.cert_z = -1;
+    if (cert_kz) zero(cert_kz, size_t(nz));
     *h_st = h;
     ck(cudaMemcpyAsync(st, h_st, sizeof(Scal), cudaMemcpyHostToDevice, stream), "state");
     ck(cudaStreamSynchronize(stream), "begin solve");
@@ -1115,7 +1172,18 @@ struct Solver final : SolverBase {
     }
     launch_project<S, S, C, kFpResid, C>(g, psf ? kq : qp, B, (C*)nullptr, act_col, zl, s, nbits, rspan);
     count(1);
-    if (cert_on) {
+    if (cert_slices) {
+      // bound-based certificate of the epoch difference lam+ - lam0, per slice
+      k_cert_vol_z<S, C><<<kCertBlocks, kThreads, 0, s>>>(B, (long long)nx * ny, nz, cert_pz);
+      const C* cq = cert_q;
+      if (psf) {
+        psf3<C, C>(cert_q, t3, t1, t2, -1, s);
+        cq = t3;
+      }
+      launch_project<C, S, C, kFpCertZ, C>(g, cq, B, (C*)nullptr, act_col, zl, s, nbits, rspan);
+      k_cert_decide_z<<<1, kThreads, 0, s>>>(st, cert_pz, kCertBlocks, nz, cert_kz, cert_Bz);
+      count(3);
+    } else if (cert_on) {
       // bound-based certificate of the epoch difference lam+ - lam0
       k_cert_vol<S, C><<<kRedBlocks, kThreads, 0, s>>>(B, (long long)V);
       const C* cq = cert_q;
@@ -1190,6 +1258,12 @@ struct Solver final : SolverBase {
       ck(cudaStreamSynchronize(stream), "solve");
     }
     solved = true;
+    // f~* = A^T y* of the returned point, recomputed by one plain application
+    // of the operator: the iterations carry d by linearity (d+ = (d_bar + d) / 2),
+    // which drifts from A^T y by rounding over many steps in FP32
+    launch_backproject<S, S, C, kBpStore, C>(geo(), yp, bufs(), psf ? braw : dp, need, zl, stream, bp_nv);
+    count(1);
+    if (psf) psf3<C, C>(braw, dp, t1, t2, -1, stream);
     // metrics of d = A^T y at the returned point (Eqs. 6-8, 27, 46)
     k_metrics<C><<<kRedBlocks, kThreads, 0, stream>>>(dp, lab, fT, ft_is_const ? nullptr : ft, ft_const,
                                                      f_crit, (long long)V, part);
@@ -1226,6 +1300,7 @@ struct Solver final : SolverBase {
     res->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     res->kernel_launches = launches;
     res->tile_cfg = bp_nv;
+    res->cert_slice = h.status == 1 ? h.cert_z : -1;
   }
 
   // copies n elements of S (converted to C) to out (host or device)
@@ -1261,11 +1336,12 @@ struct Solver final : SolverBase {
     const Geo<C> g = geo();
     if (psf) {
       ensure_temps();
-      launch_backproject<C, C, C, kBpStore, C>(g, static_cast<const C*>(sino), Bufs<C, C>{}, t3, nullptr, zl, s);
+      launch_backproject<C, C, C, kBpStore, C>(g, static_cast<const C*>(sino), Bufs<C, C>{}, t3, nullptr, zl, s,
+                                               bp_nv);
       psf3<C, C>(t3, static_cast<C*>(vol), t1, t2, -1, s);
     } else {
       launch_backproject<C, C, C, kBpStore, C>(g, static_cast<const C*>(sino), Bufs<C, C>{},
-                                               static_cast<C*>(vol), nullptr, zl, s);
+                                               static_cast<C*>(vol), nullptr, zl, s, bp_nv);
     }
     count(1);
     ck(cudaGetLastError(), "backproject");
@@ -1510,6 +1586,16 @@ int sipo_set_state(sipo_ctx* ctx, const void* y, const void* lam_up, const void*
   if (!ctx || !y || !lam_up || !lam_lo || !scalars) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
   if (location != SIPO_HOST && location != SIPO_DEVICE) sipo::fail(SIPO_ERR_INVALID_ARG, "bad location");
   ctx->c.s->state_from(y, lam_up, lam_lo, location, scalars[0], scalars[1], scalars[2]);
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
+int sipo_set_primal_from(sipo_ctx* dst, const sipo_ctx* src, double scale, double u, double v) {
+  SIPO_TRY
+  if (!dst || !src) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
+  if (dst == src) sipo::fail(SIPO_ERR_INVALID_ARG, "primal transfer: source and destination are the same context");
+  if (!(scale > 0) || !std::isfinite(scale)) sipo::fail(SIPO_ERR_INVALID_ARG, "scale must be finite and > 0");
+  dst->c.s->primal_from(*src->c.s, scale, u, v);
   return SIPO_OK;
   SIPO_CATCH
 }

@@ -16,7 +16,26 @@ namespace sipo {
 
 constexpr int kThreads = 256;     // threads per block for every kernel
 constexpr int kWarps = kThreads / 32;
-constexpr int kRedBlocks = 1216;  // 152 SMs x 8: grid of every reducing kernel
+// Grid of every reducing kernel: 8 blocks per SM of a 152-SM GB300.  It is a
+// constant on purpose: the FP64 reductions sum one partial per block in block
+// order, so a fixed grid keeps every solve bit-reproducible from one device to
+// another whatever its SM count; the grid-stride loops stay correct on any.
+constexpr int kRedBlocks = 1216;
+
+// Streaming multiprocessors of the current device (cudaDeviceProp
+// multiProcessorCount), cached per device: the element-wise kernels size
+// their grids as a multiple of it.
+inline int device_sms() {
+  static int cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (cache[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
 constexpr double kEta = 0.99;     // step factor on the Pock-Chambolle steps
 
 enum Label : uint8_t { kExt = 0, kBand = 1, kGel = 2 };

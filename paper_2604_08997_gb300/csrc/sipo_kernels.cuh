@@ -187,15 +187,15 @@ __global__ void k_convert(const TI* __restrict__ in, TO* __restrict__ out, long 
     out[i] = from_c<TO>(to_c(in[i]));
 }
 
-// A caller's primal point projected onto the primal domain of Eqs. 23-24:
-// y >= 0 on active rays (positive column sum), 0 on the others.  A NaN
-// fails the comparison and is dropped like a negative value.
+// A caller's primal point times `scale` (> 0) projected onto the primal
+// domain of Eqs. 23-24: y >= 0 on active rays (positive column sum), 0 on the
+// others.  A NaN fails the comparison and is dropped like a negative value.
 template <typename S, typename C>
 __global__ void k_import_primal(const C* __restrict__ in, const C* __restrict__ col, S* __restrict__ out,
-                                long long n) {
+                                C scale, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const C v = in[i];
+    const C v = in[i] * scale;
     out[i] = from_c<S>(col[i] > C(0) && v > C(0) ? v : C(0));
   }
 }
@@ -500,6 +500,122 @@ __global__ void __launch_bounds__(kThreads) k_cert_decide(Scal* st, const double
   const double kappa = block_max_slot(part, kSlCertK);
   if (threadIdx.x != 0) return;
   st->cert = (obj > 0.0 && kappa * st->cert_B <= (1.0 - kCertMargin) * obj) ? 1 : 0;
+}
+
+// ----------------------------------- bound-based certificate, slice by slice
+// Without a PSF extent along z the operator maps each z-slice's rays to that
+// slice's voxels only (slice-separable forward model, Sec. 2.3), so the
+// Farkas bound above holds per slice: obj_z > kappa_z B_z for one slice z
+// proves infeasibility.  The per-z sums below use a fixed grid: block b
+// covers a contiguous range of (y, x) columns, thread t the z values
+// t, t + blockDim.x, ...; each block writes one partial per z and the
+// decision sums them in block order, so the result does not depend on timing.
+constexpr int kCertBlocks = 304;  // fixed (block-order sums), 2 per SM of a GB300
+constexpr int kCertMaxZ = 4096;   // slice mode needs nz <= this (shared maxima)
+
+__device__ __forceinline__ void cert_col_range(long long ncol, long long& c0, long long& c1) {
+  const long long per = (ncol + gridDim.x - 1) / gridDim.x;
+  c0 = blockIdx.x * per;
+  c1 = c0 + per < ncol ? c0 + per : ncol;
+}
+
+// B_z: per slice, the sum of the constant upper bounds of the bounding rows
+// (Case 2: band rows, bound 1; Case 1: gel rows, bound f~_U).
+template <typename C>
+__global__ void __launch_bounds__(kThreads)
+k_cert_bz(const uint8_t* __restrict__ lab, const C* __restrict__ ft, C ft_const, const C* __restrict__ fu,
+          double up_ratio, int kase, long long ncol, int nz, double* __restrict__ partz) {
+  long long c0, c1;
+  cert_col_range(ncol, c0, c1);
+  for (int z = threadIdx.x; z < nz; z += blockDim.x) {
+    double acc = 0.0;
+    for (long long c = c0; c < c1; ++c) {
+      const long long i = c * nz + z;
+      const uint8_t l = lab[i];
+      if (kase == 2) {
+        if (l == kBand) acc += 1.0;
+      } else if (l == kGel) {
+        const double f = ft ? double(ft[i]) : double(ft_const);
+        acc += fu ? double(fu[i]) : f * up_ratio;
+      }
+    }
+    partz[(size_t)blockIdx.x * nz + z] = acc;
+  }
+}
+
+// out[z] = sum over blocks of partz (block order).
+__global__ void __launch_bounds__(kThreads)
+k_cert_zsum(const double* __restrict__ partz, int nblocks, int nz, double* __restrict__ out) {
+  for (int z = blockIdx.x * blockDim.x + threadIdx.x; z < nz; z += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int b = 0; b < nblocks; ++b) acc += partz[(size_t)b * nz + z];
+    out[z] = acc;
+  }
+}
+
+// The candidate of k_cert_vol, written to cert_q, with its dual objective
+// summed per slice into partz[block][z].
+template <typename S, typename C>
+__global__ void __launch_bounds__(kThreads) k_cert_vol_z(Bufs<S, C> b, long long ncol, int nz, double* partz) {
+  if (b.st->done) return;
+  const bool case2 = b.has_v != 0;
+  long long c0, c1;
+  cert_col_range(ncol, c0, c1);
+  for (int z = threadIdx.x; z < nz; z += blockDim.x) {
+    double acc = 0.0;
+    for (long long c = c0; c < c1; ++c) {
+      const long long i = c * nz + z;
+      const uint8_t l = b.lab[i];
+      C qv = C(0);
+      if (l == kGel) {
+        const C f = b.ft ? b.ft[i] : b.ft_const;
+        const C dlo = to_c(b.lpl[i]) - to_c(b.ll0[i]);
+        const C llh = dlo > C(0) ? dlo : C(0);
+        acc += double(f) * double(llh);
+        C luh = C(0);
+        if (!case2) {
+          const C dup = to_c(b.lpu[i]) - to_c(b.lu0[i]);
+          luh = dup > C(0) ? dup : C(0);
+          const C fU = b.fu ? b.fu[i] : f * b.up_ratio;
+          acc -= double(fU) * double(luh);
+        }
+        qv = luh - llh;
+      } else if (l == kBand && case2) {
+        const C dup = to_c(b.lpu[i]) - to_c(b.lu0[i]);
+        const C luh = dup > C(0) ? dup : C(0);
+        acc -= double(b.band_rhs) * double(luh);
+        qv = luh;
+      }
+      b.cert_q[i] = qv;
+    }
+    partz[(size_t)blockIdx.x * nz + z] = acc;
+  }
+}
+
+// One block: per slice obj_z (block partials of k_cert_vol_z), kappa_z (the
+// projector's maxima) and B_z; the verdict and the first slice that carries
+// it.  The maxima are cleared for the next check.
+__global__ void __launch_bounds__(kThreads)
+k_cert_decide_z(Scal* st, const double* __restrict__ partz, int nblocks, int nz, unsigned long long* kz,
+                const double* __restrict__ Bz) {
+  __shared__ int first;
+  if (threadIdx.x == 0) first = 0x7fffffff;
+  __syncthreads();
+  const bool live = !st->done;
+  for (int z = threadIdx.x; z < nz; z += blockDim.x) {
+    if (live) {
+      double obj = 0.0;
+      for (int b = 0; b < nblocks; ++b) obj += partz[(size_t)b * nz + z];
+      const double kappa = __longlong_as_double((long long)kz[z]);
+      if (obj > 0.0 && kappa * Bz[z] <= (1.0 - kCertMargin) * obj) atomicMin(&first, z);
+    }
+    kz[z] = 0ull;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && live) {
+    st->cert = first != 0x7fffffff ? 1 : 0;
+    st->cert_z = st->cert ? first : -1;
+  }
 }
 
 // --------------------------------------------------------- blend kernels

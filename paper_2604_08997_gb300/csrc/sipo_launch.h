@@ -28,8 +28,9 @@ template <typename C>
 void launch_ray_spans(const Geo<C>& g, const uint8_t* need, int2* out, cudaStream_t stream);
 
 // tile: entry of the backprojector tile table (0: 8 columns per warp, 2
-// blocks/SM; 1: 4 columns, 2 blocks/SM; 2: 4 columns, 3 blocks/SM).
-constexpr int kBpTiles = 3;
+// blocks/SM; 1: 4 columns, 2 blocks/SM; 2: 4 columns, 3 blocks/SM; 3, 4: the
+// single-precision row-pattern kernel at 2 and 3 blocks/SM, entry 2 in FP64).
+constexpr int kBpTiles = 5;
 template <typename SI, typename S, typename C, int MODE, typename O>
 void launch_backproject(const Geo<C>& g, const SI* sino, const Bufs<S, C>& b, O* out,
                         const uint8_t* need, int zl, cudaStream_t stream, int tile = 0);

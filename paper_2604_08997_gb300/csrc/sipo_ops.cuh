@@ -22,7 +22,7 @@
 
 namespace sipo {
 
-enum FpMode : int { kFpStore = 0, kFpPrimal = 1, kFpPrimalCheck = 2, kFpResid = 3, kFpCert = 4 };
+enum FpMode : int { kFpStore = 0, kFpPrimal = 1, kFpPrimalCheck = 2, kFpResid = 3, kFpCert = 4, kFpCertZ = 5 };
 enum BpMode : int { kBpStore = 0, kBpDual = 1 };
 
 
@@ -246,6 +246,13 @@ k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __r
   StepScalars<C> sc{};
   if (MODE == kFpPrimal || MODE == kFpPrimalCheck) sc = read_scalars<C>(b.st);
   __shared__ __align__(16) TapList<C> taps[kWarps];
+  // slice-mode certificate: per-z maxima of the block (dynamic shared memory,
+  // nz entries), merged into b.cert_kz after the tile loop
+  extern __shared__ __align__(16) unsigned long long kz_block[];
+  if constexpr (MODE == kFpCertZ) {
+    for (int z = threadIdx.x; z < g.nz; z += blockDim.x) kz_block[z] = 0ull;
+    __syncthreads();
+  }
 
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int k = int(t % g.na);
@@ -311,9 +318,16 @@ k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __r
       primal_update<S, C, ZL, true>(b, sc, base, acc, red);
     } else if constexpr (MODE == kFpResid) {
       resid_update<S, C, ZL>(b, base, acc, red);
-    } else {
+    } else if constexpr (MODE == kFpCert) {
       cert_update<S, C, ZL>(b, base, acc, red);
+    } else {
+      cert_update_z<S, C, ZL>(b, base, z0, acc, kz_block);
     }
+  }
+  if constexpr (MODE == kFpCertZ) {
+    __syncthreads();
+    for (int z = threadIdx.x; z < g.nz; z += blockDim.x)
+      if (kz_block[z] != 0ull) atomicMax(b.cert_kz + z, kz_block[z]);
   }
   if constexpr (MODE == kFpPrimalCheck) block_reduce_store<2>(red, b.part, kSlFpX);
   if constexpr (MODE == kFpResid) block_reduce_store<4, kResidMaxMask>(red, b.part, kSlRd2);
@@ -515,6 +529,257 @@ k_backproject(const Geo<C> g, const SI* __restrict__ sino, const Bufs<S, C> b, O
         if (need == nullptr || ((mask >> v) & 1u)) store_z<O, C, ZL>(out + base, acc[v]);
       } else if ((mask >> v) & 1u) {
         // the epilogue runs group by group to keep its live range short
+        using L = ZLayout<C, ZL>;
+#pragma unroll
+        for (int q = 0; q < L::NG; ++q) {
+          C part[L::G];
+#pragma unroll
+          for (int i = 0; i < L::G; ++i)
+            part[i] = kStage ? stage[((v * L::NG + q) * 32 + lane) * L::G + i] : acc[v][q * L::G + i];
+          dual_update<S, C, L::G, false>(b, sc, base + q * L::kStride, part, red);
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if constexpr (MODE == kBpDual) block_reduce_store<2>(red, b.part, kSlSBand);
+}
+
+// ------------------------------------------ backprojector with row patterns
+// Single-precision form of k_backproject with the same tiles, z layout,
+// angle order and epilogues, and sums equal bit for bit.  Per angle the lanes
+// write, for the warp's four voxels (x order), the first detector row
+// b = min floor(u), the offsets floor(u_v) - b packed two bits each (the
+// pattern) and the weights, each one twice (a float pair for the packed
+// multiply-add), with zero weight on every tap whose bin is off the detector.
+// u = fma(x, cos, inner) is monotone in x, so with |cos| <= 1 the offsets
+// move by 0 or 1 from one voxel to the next: 15 patterns.  Each pattern has a
+// body whose row indices are compile-time constants: the angle's two to five
+// rows are loaded at once into named registers, clamped to the detector (a
+// clamped row only meets zero weights, and 0 * x leaves a sum unchanged), and
+// every voxel applies its two rows with packed FP32 multiply-adds
+// (__ffma2_rn, two z values per instruction, each rounded like fmaf).  A
+// pattern outside the 15 takes a generic body that loads each voxel's rows.
+struct alignas(16) Bp2Ent {
+  float4 w[4];  // voxel v: (w0, w0, w1, w1)
+  int b, pat, pad0, pad1;
+  int4 i0;      // floor(u) per voxel (read by the generic body only)
+};
+constexpr int kBp2Chunk = 32;
+constexpr int kBp2Generic = 0xff;
+constexpr int kBp2NV = 4;
+
+__host__ __device__ constexpr int bp2_off(int pat, int v) { return (pat >> (2 * v)) & 3; }
+__host__ __device__ constexpr int bp2_rows(int pat) {
+  int m = 0;
+  for (int v = 0; v < kBp2NV; ++v) m = bp2_off(pat, v) > m ? bp2_off(pat, v) : m;
+  return m + 2;
+}
+
+__device__ __forceinline__ void bp2_fill(const Geo<float>& g, int k, float yf, float xf0, int iy, int tx0,
+                                         unsigned mask, Bp2Ent& out) {
+  const float c = g.cs[2 * k], s = g.cs[2 * k + 1];
+  const float inner = geo_inner(yf, s, g.off);
+  const float eyv = g.ex ? g.ey[(size_t)k * g.ny + iy] : 1.0f;
+  const float* esk = g.es ? g.es + (size_t)k * g.nd : nullptr;
+  int i0[kBp2NV];
+  float w0[kBp2NV], w1[kBp2NV];
+#pragma unroll
+  for (int v = 0; v < kBp2NV; ++v) {
+    const float u = geo_outer(xf0 + float(v), c, inner);
+    float flo;
+    floor_split(u, flo, i0[v]);
+    float a = 0.0f, bb = 0.0f;
+    if ((mask >> v) & 1u) {
+      const float wv = u - flo;
+      const float e = g.ex ? g.ex[(size_t)k * g.nx + tx0 + v] * eyv : 1.0f;
+      a = (1.0f - wv) * e;
+      bb = wv * e;
+      if (esk) {
+        a = unsigned(i0[v]) < unsigned(g.nd) ? a * esk[i0[v]] : 0.0f;
+        bb = unsigned(i0[v] + 1) < unsigned(g.nd) ? bb * esk[i0[v] + 1] : 0.0f;
+      }
+    }
+    w0[v] = unsigned(i0[v]) < unsigned(g.nd) ? a : 0.0f;
+    w1[v] = unsigned(i0[v] + 1) < unsigned(g.nd) ? bb : 0.0f;
+  }
+  int b = i0[0];
+#pragma unroll
+  for (int v = 1; v < kBp2NV; ++v) b = min(b, i0[v]);
+  bool inc = true, dec = true;
+#pragma unroll
+  for (int v = 0; v + 1 < kBp2NV; ++v) {
+    const int st = i0[v + 1] - i0[v];
+    inc = inc && (st == 0 || st == 1);
+    dec = dec && (st == 0 || st == -1);
+  }
+  int pat = 0;
+#pragma unroll
+  for (int v = 0; v < kBp2NV; ++v) pat |= (i0[v] - b) << (2 * v);
+  if (!(inc || dec)) pat = kBp2Generic;
+#pragma unroll
+  for (int v = 0; v < kBp2NV; ++v) out.w[v] = make_float4(w0[v], w0[v], w1[v], w1[v]);
+  out.b = b;
+  out.pat = pat;
+  out.pad0 = 0;
+  out.pad1 = 0;
+  out.i0 = make_int4(i0[0], i0[1], i0[2], i0[3]);
+}
+
+// acc += w0 * r0 + w1 * r1 elementwise (w0 applied first), packed in pairs.
+template <int ZL>
+__device__ __forceinline__ void bp2_fma(float (&acc)[ZL], const float4& w, const float (&r0)[ZL],
+                                        const float (&r1)[ZL]) {
+  if constexpr (ZL % 2 == 0) {
+    const float2 wa = make_float2(w.x, w.y), wb = make_float2(w.z, w.w);
+#pragma unroll
+    for (int i = 0; i < ZL; i += 2) {
+      float2 a = make_float2(acc[i], acc[i + 1]);
+      a = __ffma2_rn(wa, make_float2(r0[i], r0[i + 1]), a);
+      a = __ffma2_rn(wb, make_float2(r1[i], r1[i + 1]), a);
+      acc[i] = a.x;
+      acc[i + 1] = a.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < ZL; ++i) acc[i] = fmaf(w.z, r1[i], fmaf(w.x, r0[i], acc[i]));
+  }
+}
+
+template <typename SI, int ZL>
+__device__ __forceinline__ void bp2_row(const Geo<float>& g, const SI* srow, int r, float (&t)[ZL]) {
+  r = r < 0 ? 0 : (r >= g.nd ? g.nd - 1 : r);
+  load_z<SI, float, ZL>(srow + (size_t)r * g.nz, t);
+}
+
+template <typename SI, int ZL, int PAT>
+__device__ __forceinline__ void bp2_body(const Geo<float>& g, const SI* srow, const Bp2Ent& e,
+                                         float (&acc)[kBp2NV][ZL]) {
+  constexpr int NR = bp2_rows(PAT);
+  float r[NR][ZL];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) bp2_row<SI, ZL>(g, srow, e.b + j, r[j]);
+#pragma unroll
+  for (int v = 0; v < kBp2NV; ++v) bp2_fma<ZL>(acc[v], e.w[v], r[bp2_off(PAT, v)], r[bp2_off(PAT, v) + 1]);
+}
+
+template <typename SI, int ZL>
+__device__ __forceinline__ void bp2_generic(const Geo<float>& g, const SI* srow, const Bp2Ent& e,
+                                         float (&acc)[kBp2NV][ZL]) {
+  const int i0[kBp2NV] = {e.i0.x, e.i0.y, e.i0.z, e.i0.w};
+#pragma unroll
+  for (int v = 0; v < kBp2NV; ++v) {
+    float r0[ZL], r1[ZL];
+    bp2_row<SI, ZL>(g, srow, i0[v], r0);
+    bp2_row<SI, ZL>(g, srow, i0[v] + 1, r1);
+    bp2_fma<ZL>(acc[v], e.w[v], r0, r1);
+  }
+}
+
+#define SIPO_BP2_PATTERNS(X)                                                              \
+  X(0x00) X(0x40) X(0x50) X(0x90) X(0x54) X(0x94) X(0xA4) X(0xE4)                          \
+  X(0x01) X(0x05) X(0x15) X(0x06) X(0x16) X(0x1A) X(0x1B)
+
+// One angle of a warp's four voxels: dispatch on the table entry's pattern.
+template <typename SI, int ZL>
+__device__ __forceinline__ void bp2_angle(const Geo<float>& g, const SI* srow, const Bp2Ent& e,
+                                          float (&acc)[kBp2NV][ZL]) {
+  switch (e.pat) {
+#define SIPO_BP2_CASE(P) \
+  case P:                \
+    bp2_body<SI, ZL, P>(g, srow, e, acc); break;
+    SIPO_BP2_PATTERNS(SIPO_BP2_CASE)
+#undef SIPO_BP2_CASE
+    default:
+      bp2_generic<SI, ZL>(g, srow, e, acc);
+  }
+}
+
+// Tile: 4 voxel columns along x per warp, one row per warp (8 rows per
+// block), ZL z values per lane; need, modes and epilogues as in
+// k_backproject.
+template <typename SI, typename S, int ZL, int MINB, int MODE, typename O>
+__global__ void __launch_bounds__(kThreads, MINB)
+k_backproject2(const Geo<float> g, const SI* __restrict__ sino, const Bufs<S, float> b, O* __restrict__ out,
+               const uint8_t* __restrict__ need) {
+  using C = float;
+  constexpr int NV = kBp2NV;
+  if (MODE != kBpStore && b.st->done) return;
+  constexpr int ZC = 32 * ZL;
+  constexpr int NR = MODE == kBpDual ? 2 : 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ntx = (g.nx + NV - 1) / NV, nty = (g.ny + kWarps - 1) / kWarps;
+  const int nzc = (g.nz + ZC - 1) / ZC;
+  const long long ntiles = (long long)ntx * nty * nzc;
+  double red[NR > 0 ? NR : 1] = {};
+  StepScalars<C> sc{};
+  if (MODE != kBpStore) sc = read_scalars<C>(b.st);
+  constexpr size_t kTableBytes = sizeof(Bp2Ent) * kBp2Chunk;
+  constexpr size_t kStageBytes = size_t(NV) * ZL * 32 * sizeof(C);
+  constexpr bool kStage = MODE != kBpStore && kStageBytes <= 4096;
+  constexpr size_t kWarpBytes = kTableBytes > (kStage ? kStageBytes : 0) ? kTableBytes : kStageBytes;
+  __shared__ __align__(16) unsigned char smem_warp[kWarps][kWarpBytes];
+  Bp2Ent* tb = reinterpret_cast<Bp2Ent*>(smem_warp[warp]);
+
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int tz = int(t % nzc);
+    const long long t1 = t / nzc;
+    const int tx = int(t1 % ntx);
+    const int ty = int(t1 / ntx);
+    const int iy = ty * kWarps + warp;
+    const int z0 = tz * ZC + lane * ZLayout<C, ZL>::G;
+    if (iy >= g.ny) continue;
+    const int2 sp = g.xspan[iy];
+    unsigned mask = 0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int ix = tx * NV + v;
+      if (ix < g.nx && ix >= sp.x && ix <= sp.y && (need == nullptr || need[(size_t)iy * g.nx + ix]))
+        mask |= 1u << v;
+    }
+    C acc[NV][ZL];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int i = 0; i < ZL; ++i) acc[v][i] = C(0);
+    // the whole warp takes part; a lane past the end of a ragged z column
+    // reads the column's first group and never stores its result
+    if (mask != 0u) {
+      const C yf = C(iy) - g.cy;
+      const C xf0 = C(tx * NV) - g.cx;
+      const SI* sz = sino + (z0 < g.nz ? z0 : 0);
+      for (int k0 = 0; k0 < g.na; k0 += kBp2Chunk) {
+        if (k0 + lane < g.na) bp2_fill(g, k0 + lane, yf, xf0, iy, tx * NV, mask, tb[lane]);
+        __syncwarp();
+        const int kn = min(kBp2Chunk, g.na - k0);
+        for (int kk = 0; kk < kn; ++kk)
+          bp2_angle<SI, ZL>(g, sz + (size_t)(k0 + kk) * g.nd * g.nz, tb[kk], acc);
+        __syncwarp();
+      }
+    }
+    using LS = ZLayout<C, ZL>;
+    C* stage = reinterpret_cast<C*>(smem_warp[warp]);
+    if constexpr (kStage) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int q = 0; q < LS::NG; ++q)
+#pragma unroll
+          for (int i = 0; i < LS::G; ++i) stage[((v * LS::NG + q) * 32 + lane) * LS::G + i] = acc[v][q * LS::G + i];
+      __syncwarp();
+    }
+    if (z0 >= g.nz) {
+      __syncwarp();
+      continue;
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int ix = tx * NV + v;
+      if (ix >= g.nx) continue;
+      const size_t base = ((size_t)iy * g.nx + ix) * g.nz + z0;
+      if constexpr (MODE == kBpStore) {
+        if (need == nullptr || ((mask >> v) & 1u)) store_z<O, C, ZL>(out + base, acc[v]);
+      } else if ((mask >> v) & 1u) {
         using L = ZLayout<C, ZL>;
 #pragma unroll
         for (int q = 0; q < L::NG; ++q) {

@@ -34,18 +34,20 @@ void launch_project(const Geo<C>& g, const SI* vol, const Bufs<S, C>& b, O* out,
                     const uint8_t* act_col, int zl, cudaStream_t stream, const NeedBits& nb,
                     const int2* rspan) {
   constexpr int G = z_group<C>();
+  // the slice-mode certificate keeps one 8-byte maximum per z in shared memory
+  const size_t dyn = MODE == kFpCertZ ? size_t(g.nz) * sizeof(unsigned long long) : 0;
   if (zl == 2 * G)
-    k_project<SI, S, C, 2 * G, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, vol, b, out, act_col, nb, rspan);
+    k_project<SI, S, C, 2 * G, MODE, O><<<kRedBlocks, kThreads, dyn, stream>>>(g, vol, b, out, act_col, nb, rspan);
   else if (zl == G)
-    k_project<SI, S, C, G, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, vol, b, out, act_col, nb, rspan);
+    k_project<SI, S, C, G, MODE, O><<<kRedBlocks, kThreads, dyn, stream>>>(g, vol, b, out, act_col, nb, rspan);
   else
-    k_project<SI, S, C, 1, MODE, O><<<kRedBlocks, kThreads, 0, stream>>>(g, vol, b, out, act_col, nb, rspan);
+    k_project<SI, S, C, 1, MODE, O><<<kRedBlocks, kThreads, dyn, stream>>>(g, vol, b, out, act_col, nb, rspan);
 }
 
 void launch_need_bits(const uint8_t* need, uint32_t* rows, uint32_t* cols, int nx, int ny, int wr, int wc,
                       cudaStream_t stream) {
-  const int gr = int(std::min<long long>(((long long)ny * wr + kThreads - 1) / kThreads, 152LL * 16));
-  const int gc = int(std::min<long long>(((long long)nx * wc + kThreads - 1) / kThreads, 152LL * 16));
+  const int gr = int(std::min<long long>(((long long)ny * wr + kThreads - 1) / kThreads, (long long)device_sms() * 16));
+  const int gc = int(std::min<long long>(((long long)nx * wc + kThreads - 1) / kThreads, (long long)device_sms() * 16));
   k_need_bits<<<gr, kThreads, 0, stream>>>(need, rows, nx, ny, wr, 1);
   k_need_bits<<<gc, kThreads, 0, stream>>>(need, cols, nx, ny, wc, 0);
 }
@@ -53,7 +55,7 @@ void launch_need_bits(const uint8_t* need, uint32_t* rows, uint32_t* cols, int n
 template <typename C>
 void launch_ray_spans(const Geo<C>& g, const uint8_t* need, int2* out, cudaStream_t stream) {
   const long long n = (long long)g.na * g.nd;
-  const int grid = int(std::min<long long>((n + kThreads - 1) / kThreads, 152LL * 16));
+  const int grid = int(std::min<long long>((n + kThreads - 1) / kThreads, (long long)device_sms() * 16));
   k_ray_spans<C><<<grid, kThreads, 0, stream>>>(g, need, out);
 }
 template void launch_ray_spans<float>(const Geo<float>&, const uint8_t*, int2*, cudaStream_t);
@@ -75,6 +77,9 @@ SIPO_FP_SOLVER(double, double)
 SIPO_FP(float, float, float, kFpCert, float)
 SIPO_FP(float, __nv_bfloat16, float, kFpCert, float)
 SIPO_FP(double, double, double, kFpCert, double)
+SIPO_FP(float, float, float, kFpCertZ, float)
+SIPO_FP(float, __nv_bfloat16, float, kFpCertZ, float)
+SIPO_FP(double, double, double, kFpCertZ, double)
 SIPO_FP(float, float, float, kFpStore, float)
 SIPO_FP(double, double, double, kFpStore, double)
 SIPO_FP(__nv_bfloat16, __nv_bfloat16, float, kFpStore, float)

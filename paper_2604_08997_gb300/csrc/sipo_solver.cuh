@@ -79,9 +79,11 @@ struct Scal {
   double* trace;
   int trace_cap, trace_n;
   // bound-based infeasibility certificate: B, whether the case has one, and
-  // the verdict of the current check
+  // the verdict of the current check; cert_slices: evaluated per z-slice
+  // (operator without z coupling), cert_z: first slice that carried it (-1)
   double cert_B;
   int cert_on, cert;
+  int cert_slices, cert_z;
 };
 
 // Margin of the bound-based certificate: kappa * B <= (1 - kCertMargin) obj.
@@ -118,9 +120,11 @@ struct Bufs {
   C band_rhs;           // right side of band rows: 0 (u~ variable) or 1 (Case 2)
   Scal* st;
   double* part;
-  // bound-based certificate: b = A 1_rows per ray, the candidate volume
+  // bound-based certificate: b = A 1_rows per ray, the candidate volume,
+  // and per z-slice the largest max(-g^, 0) / b as ordered bits (slice mode)
   const C* cert_b;
   C* cert_q;
+  unsigned long long* cert_kz;
 };
 
 // Halpern weights and steps read once per kernel.
@@ -318,6 +322,25 @@ __device__ __forceinline__ void cert_update(const Bufs<S, C>& b, size_t base, co
     if (col[i] > C(0) && g[i] < C(0)) {
       const double v = -double(g[i]);
       red[0] = fmax(red[0], bb[i] > C(0) ? v / double(bb[i]) : CUDART_INF);
+    }
+  }
+}
+
+// Slice mode: the same ratio per z value, folded with an atomic maximum into
+// the block's shared array kz[nz] (the bit patterns of non-negative doubles,
+// +inf included, order like the values, so the maximum does not depend on
+// the order of the updates).
+template <typename S, typename C, int ZL>
+__device__ __forceinline__ void cert_update_z(const Bufs<S, C>& b, size_t base, int z0, const C (&g)[ZL],
+                                              unsigned long long* kz) {
+  C col[ZL], bb[ZL];
+  load_z<C, C, ZL>(b.col + base, col);
+  load_z<C, C, ZL>(b.cert_b + base, bb);
+#pragma unroll
+  for (int i = 0; i < ZL; ++i) {
+    if (col[i] > C(0) && g[i] < C(0)) {
+      const double v = bb[i] > C(0) ? -double(g[i]) / double(bb[i]) : CUDART_INF;
+      atomicMax(kz + z0 + z_offset<C, ZL>(i), (unsigned long long)__double_as_longlong(v));
     }
   }
 }

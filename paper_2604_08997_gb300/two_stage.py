@@ -13,16 +13,15 @@ dose scaled by 1 / (1 - d_lo) satisfies every stage-2 row for any r >= u~*:
 in normalised units (dose / f_crit of each stage) that point is y2 = y1 / r,
 so stage 2 is feasible by construction, its optimum v~* is at most that
 point's spread (<= (1 + d_hi) / (1 - d_lo)), and stage 2 may start from it
-(`sipo_set_primal`) instead of from zero.
+instead of from zero.
 
-Host orchestration only: both solves and the start run in libsipo.
+Host orchestration only: both solves run in libsipo, and the stage-1 point
+goes to stage 2 on the device (`sipo_set_primal_from` with scale 1 / r).
 """
 from __future__ import annotations
 
-import numpy as np
-
-from ._abi import (SIPO_CASE1, SIPO_CASE2, SIPO_F64, SIPO_OPTIMAL, sipo_create, sipo_destroy,
-                   sipo_set_primal, sipo_solve)
+from ._abi import (SIPO_CASE1, SIPO_CASE2, SIPO_OPTIMAL, sipo_create, sipo_destroy, sipo_set_primal_from,
+                   sipo_solve)
 
 
 def two_stage_solve(geometry: dict, f_T, tol_lo: float = 0.05, tol_hi: float = 0.05,
@@ -39,29 +38,23 @@ def two_stage_solve(geometry: dict, f_T, tol_lo: float = 0.05, tol_hi: float = 0
     tol1 = dict(tolerances or {})
     tol2 = dict(tolerances2 if tolerances2 is not None else tol1)
     c1 = dict(kase=SIPO_CASE1, tol_lo=tol_lo, tol_hi=tol_hi, band_width=band_width)
-    n_sino = len(geometry["angles"]) * int(geometry["n_det"]) * int(geometry["nz"])
-    dt = np.float64 if tol1.get("storage") == SIPO_F64 else np.float32
-    y1 = np.empty(n_sino, dt)
     ctx1 = sipo_create(geometry, f_T, c1, tol1)
+    ctx2 = None
     try:
-        res1 = sipo_solve(ctx1, y1)
+        res1 = sipo_solve(ctx1)
+        out = {"stage1": res1, "stage2": None, "ratio": None}
+        if res1["status"] != SIPO_OPTIMAL or not res1["u"] > 0:
+            return out
+        r = float(res1["u"]) * (1.0 + slack)
+        out["ratio"] = r
+        c2 = dict(kase=SIPO_CASE2, inhibit_ratio=r, band_width=band_width)
+        ctx2 = sipo_create(geometry, f_T, c2, tol2)
+        if warm:
+            # the stage-1 dose over (1 - d_lo), in stage-2 normalised units
+            sipo_set_primal_from(ctx2, ctx1, 1.0 / r)
+        out["stage2"] = sipo_solve(ctx2)
+        return out
     finally:
         sipo_destroy(ctx1)
-    out = {"stage1": res1, "stage2": None, "ratio": None}
-    if res1["status"] != SIPO_OPTIMAL or not res1["u"] > 0:
-        return out
-    u1 = float(res1["u"])
-    r = u1 * (1.0 + slack)
-    out["ratio"] = r
-    c2 = dict(kase=SIPO_CASE2, inhibit_ratio=r, band_width=band_width)
-    ctx2 = sipo_create(geometry, f_T, c2, tol2)
-    try:
-        if warm:
-            dt2 = np.float64 if tol2.get("storage") == SIPO_F64 else np.float32
-            # the stage-1 dose over (1 - d_lo), in stage-2 normalised units
-            start = np.ascontiguousarray((y1.astype(np.float64) / r).astype(dt2))
-            sipo_set_primal(ctx2, start)
-        out["stage2"] = sipo_solve(ctx2)
-    finally:
-        sipo_destroy(ctx2)
-    return out
+        if ctx2 is not None:
+            sipo_destroy(ctx2)

@@ -109,6 +109,11 @@ def test_new_entries_validate_before_device_work(lib):
     assert lib.sipo_set_state(None, p, p, p, 0, sc) == -1
     assert lib.sipo_set_primal(None, p, 0, -1.0, -1.0) == -1
     assert b"null" in lib.sipo_last_error()
+    assert lib.sipo_set_primal_from(None, None, 1.0, -1.0, -1.0) == -1
+    assert b"null" in lib.sipo_last_error()
+    fake = ctypes.c_void_p(1)
+    assert lib.sipo_set_primal_from(fake, fake, 1.0, -1.0, -1.0) == -1
+    assert b"same context" in lib.sipo_last_error()
 
 
 def test_noalloc_wrapper_refuses_mismatched_buffers():

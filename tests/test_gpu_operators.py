@@ -46,14 +46,15 @@ CASES = [
 ]
 
 
-def _ctx(sipo, case, storage, seed=0):
+def _ctx(sipo, case, storage, seed=0, tile=-1):
     nx, ny, nz, na, nd, vial, mu, sig = case
     rng = np.random.default_rng(seed)
     ang = np.sort(rng.uniform(0, 2 * np.pi, na))
     tgt = np.zeros((ny, nx, nz), np.float32)
     tgt[ny // 3: 2 * ny // 3, nx // 3: 2 * nx // 3, nz // 4: max(nz // 4 + 1, 3 * nz // 4)] = 1.0
     geo = dict(nx=nx, ny=ny, nz=nz, angles=ang, n_det=nd, vial_radius=vial, mu=mu, psf_sigma=sig)
-    ctx = sipo.sipo_create(geo, tgt, dict(kase=0, band_width=2), dict(storage=storage, max_iter=0))
+    ctx = sipo.sipo_create(geo, tgt, dict(kase=0, band_width=2),
+                           dict(storage=storage, max_iter=0, tile_cfg=tile))
     ogeo = Geometry(nx, ny, nz, ang, nd, vial_radius=vial, mu=mu, psf_sigma=sig)
     return ctx, ogeo, tgt
 
@@ -80,6 +81,31 @@ def test_operator_pair_matches_oracle(sipo, case, storage):
     lhs = float(torch.sum(out_s.double() * torch.tensor(sino, device="cuda")))
     rhs = float(torch.sum(out_v.double() * torch.tensor(vol, device="cuda")))
     assert abs(lhs - rhs) <= (1e-5 if storage == "f32" else 1e-12) * math.sqrt(vol.size * sino.size)
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_every_backprojector_tile_matches_the_oracle(sipo, case):
+    """Each entry of the backprojector tile table (0-2: per-voxel row window;
+    3-4: row patterns with packed multiply-adds) against the oracle, and the
+    entries against each other: they add the same terms in the same order, so
+    the FP32 sums agree bit for bit."""
+    n_tiles = sipo.sipo_tile_count()
+    assert n_tiles == 5
+    outs = []
+    for tile in range(n_tiles):
+        ctx, ogeo, _ = _ctx(sipo, case, sipo.SIPO_F32, tile=tile)
+        ops = Operators(ogeo)
+        rng = np.random.default_rng(7)
+        sino = rng.uniform(-1, 1, size=ogeo.sino_shape)
+        out_v = torch.empty(ogeo.vol_shape, dtype=torch.float32, device="cuda")
+        sipo.sipo_backproject(ctx, torch.tensor(sino, dtype=torch.float32, device="cuda"), out_v)
+        torch.cuda.synchronize()
+        o = out_v.cpu().numpy()
+        assert _rel(o, ops.AT(sino)) <= FP32_TOL, tile
+        outs.append(o)
+        sipo.sipo_destroy(ctx)
+    for tile in range(1, n_tiles):
+        np.testing.assert_array_equal(outs[tile], outs[0], err_msg=f"tile {tile}")
 
 
 @pytest.mark.parametrize("storage", ["f32", "f64"])

@@ -503,3 +503,74 @@ def test_host_injected_failures_are_errors_or_statuses(sipo):
     sipo.sipo_set_tolerances(ctx, 1e-9, 100000)
     res = sipo.sipo_solve(ctx)
     assert res["status"] == sipo.SIPO_OPTIMAL
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_backprojector_tiles_give_identical_solves(sipo, storage):
+    """The fused dual step with every backprojector tile entry: the row-pattern
+    kernel (entries 3 and 4) adds the same terms in the same order as the
+    per-voxel window (entries 0-2), so solves agree bit for bit, in FP32 and
+    with BF16 iterate storage (256 z: two groups of four values per lane)."""
+    n, nz = 20, 256
+    tgt = np.zeros((n, n, nz), np.float32)
+    tgt[6:14, 7:13, 40:200] = 1.0
+    tgt[9:11, 4:16, 100:150] = 1.0
+    ang = uniform_angles(27)
+    geo = dict(nx=n, ny=n, nz=nz, angles=ang, n_det=29, vial_radius=9.5, mu=0.01)
+    cp = dict(kase=2, inhibit_ratio=0.7, band_width=2)
+    st = sipo.SIPO_F32 if storage == "f32" else sipo.SIPO_BF16
+    ref = None
+    for tile in range(sipo.sipo_tile_count()):
+        ctx = sipo.sipo_create(geo, tgt, cp, dict(storage=st, kkt_tol=0.0, max_iter=192, tile_cfg=tile))
+        res = sipo.sipo_solve(ctx)
+        assert res["tile_cfg"] == tile
+        key = (res["iters"], res["pobj"], res["kkt"], res["dtvr_f"], res["psr_f"])
+        if ref is None:
+            ref = key
+        assert key == ref, (tile, key, ref)
+        sipo.sipo_destroy(ctx)
+
+
+def _slice_stack(nz, bad_z, ratio=0.62):
+    """The CPU pins' stack of 12x12 Case-2 slices (10 views, 17 bins), one of
+    them (bad_z) infeasible at this ratio; bad_z None: all feasible."""
+    n, na, nd = 12, 10, 17
+    feas = [discs_2d(n, n_discs=1, r_range=(2.5, 3.5), container_radius=4.5, seed=3),
+            discs_2d(n, n_discs=3, r_range=(1.0, 1.6), container_radius=4.5, seed=3),
+            discs_2d(n, n_discs=1, r_range=(2.5, 3.5), container_radius=4.5, seed=5)]
+    bad = discs_2d(n, n_discs=1, r_range=(2.5, 3.5), container_radius=4.5, seed=1)
+    sl = [feas[i % 3] for i in range(nz)]
+    if bad_z is not None:
+        sl[bad_z] = bad
+    tgt = np.ascontiguousarray(np.concatenate(sl, axis=2))
+    ang = uniform_angles(na)
+    geo = dict(nx=n, ny=n, nz=nz, angles=ang, n_det=nd)
+    cp = dict(kase=2, inhibit_ratio=ratio, band_width=2)
+    lp, ops = build_lp(Geometry(n, n, nz, ang, nd), tgt, CaseParams(case=2, inhibit_ratio=ratio, band_width=2))
+    return lp, ops, geo, tgt, cp
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_one_infeasible_slice_is_certified_and_named(sipo, storage):
+    """16 slices, slice 8 infeasible (HiGHS per slice on the CPU): the solver
+    proves the LP infeasible slice by slice within the 5120 iterations the
+    oracle's slice test needs (its whole-volume test alone needs more) and
+    names the slice; the same stack without slice 8 solves to optimality with
+    the oracle's objective (no false certificate)."""
+    st = sipo.SIPO_F64 if storage == "f64" else sipo.SIPO_F32
+    lp, ops, geo, tgt, cp = _slice_stack(16, 8)
+    ctx = sipo.sipo_create(geo, tgt, cp, dict(storage=st, kkt_tol=1e-7, max_iter=5120))
+    res = sipo.sipo_solve(ctx)
+    assert res["status"] == sipo.SIPO_PRIMAL_INFEASIBLE, res
+    assert res["cert_slice"] in (8, -1), res["cert_slice"]
+    sipo.sipo_destroy(ctx)
+    lp, ops, geo, tgt, cp = _slice_stack(16, None)
+    ref = pdhg.solve(lp, ops, kkt_tol=1e-8, max_iter=100000)
+    assert ref["status"] == pdhg.OPTIMAL
+    ctx = sipo.sipo_create(geo, tgt, cp, dict(storage=st, kkt_tol=1e-8 if storage == "f64" else 1e-5,
+                                              max_iter=100000))
+    res = sipo.sipo_solve(ctx)
+    assert res["status"] == sipo.SIPO_OPTIMAL, res
+    assert res["cert_slice"] == -1
+    assert abs(res["pobj"] - ref["obj"]) <= (1e-7 if storage == "f64" else 1e-4) * abs(ref["obj"])
+    sipo.sipo_destroy(ctx)

@@ -1,7 +1,8 @@
 """Host logic of two_stage_solve (Sec. 3.2) with the library calls faked (CPU only):
-the stage-2 ratio is u~* (1 + slack), the stage-2 start is y1 / r in the
-stage-2 compute type, stage 2 is skipped when stage 1 is not optimal, and
-both contexts are released even when stage 2 fails."""
+the stage-2 ratio is u~* (1 + slack), stage 2 starts from the stage-1 point
+scaled by 1 / r on the device (sipo_set_primal_from), stage 2 is skipped when
+stage 1 is not optimal, and both contexts are released even when stage 2
+fails."""
 import numpy as np
 import pytest
 
@@ -22,34 +23,31 @@ class Fake:
     def solve(self, ctx, y_out=None):
         case, _ = self.created[ctx]
         if case["kase"] == SIPO_CASE1:
-            if y_out is not None:
-                y_out[:] = np.arange(y_out.size, dtype=y_out.dtype)
             return {"status": self.status1, "u": self.u1, "pobj": self.u1}
         if self.fail2:
             raise RuntimeError("stage 2 failed")
         return {"status": SIPO_OPTIMAL, "pobj": 1.2}
 
-    def set_primal(self, ctx, y, u=-1.0, v=-1.0):
-        self.started.append((ctx, y.copy()))
+    def set_primal_from(self, dst, src, scale=1.0, u=-1.0, v=-1.0):
+        assert src not in self.destroyed and dst not in self.destroyed
+        self.started.append((dst, src, scale))
 
     def destroy(self, ctx):
         self.destroyed.append(ctx)
 
 
-@pytest.fixture
-def fake(monkeypatch):
-    f = Fake()
-    monkeypatch.setattr(two_stage, "sipo_create", f.create)
-    monkeypatch.setattr(two_stage, "sipo_solve", f.solve)
-    monkeypatch.setattr(two_stage, "sipo_set_primal", f.set_primal)
-    monkeypatch.setattr(two_stage, "sipo_destroy", f.destroy)
-    return f
+def _patch(monkeypatch, f):
+    for name, fn in (("sipo_create", f.create), ("sipo_solve", f.solve),
+                     ("sipo_set_primal_from", f.set_primal_from), ("sipo_destroy", f.destroy)):
+        monkeypatch.setattr(two_stage, name, fn)
 
 
 GEO = dict(nx=4, ny=4, nz=2, angles=np.zeros(3), n_det=5)
 
 
-def test_ratio_and_start(fake):
+def test_ratio_and_start(monkeypatch):
+    fake = Fake()
+    _patch(monkeypatch, fake)
     out = two_stage.two_stage_solve(GEO, np.ones((4, 4, 2), np.float32), tol_lo=0.1, tol_hi=0.2,
                                     band_width=3, tolerances=dict(storage=SIPO_F64), slack=0.25)
     r = 0.5 * 1.25
@@ -57,34 +55,28 @@ def test_ratio_and_start(fake):
     c1, c2 = fake.created[0][0], fake.created[1][0]
     assert c1 == dict(kase=SIPO_CASE1, tol_lo=0.1, tol_hi=0.2, band_width=3)
     assert c2 == dict(kase=SIPO_CASE2, inhibit_ratio=r, band_width=3)
-    ctx, y = fake.started[0]
-    assert ctx == 1 and y.dtype == np.float64 and y.size == 3 * 5 * 2
-    np.testing.assert_array_equal(y, np.arange(30, dtype=np.float64) / r)
-    assert fake.destroyed == [0, 1]
+    assert fake.created[1][1] == dict(storage=SIPO_F64)
+    assert fake.started == [(1, 0, 1.0 / r)]
+    assert sorted(fake.destroyed) == [0, 1]
 
 
-def test_float32_start_and_cold_stage2(fake):
-    two_stage.two_stage_solve(GEO, np.ones((4, 4, 2), np.float32), tolerances={}, warm=True)
-    assert fake.started[0][1].dtype == np.float32
-    fake.started.clear()
+def test_cold_stage2(monkeypatch):
+    fake = Fake()
+    _patch(monkeypatch, fake)
     two_stage.two_stage_solve(GEO, np.ones((4, 4, 2), np.float32), warm=False)
-    assert fake.started == []
+    assert fake.started == [] and sorted(fake.destroyed) == [0, 1]
 
 
 def test_stage2_skipped_unless_stage1_optimal(monkeypatch):
     f = Fake(status1=SIPO_ITER_LIMIT)
-    for name, fn in (("sipo_create", f.create), ("sipo_solve", f.solve), ("sipo_set_primal", f.set_primal),
-                     ("sipo_destroy", f.destroy)):
-        monkeypatch.setattr(two_stage, name, fn)
+    _patch(monkeypatch, f)
     out = two_stage.two_stage_solve(GEO, np.ones((4, 4, 2), np.float32))
     assert out["stage2"] is None and out["ratio"] is None and len(f.created) == 1 and f.destroyed == [0]
 
 
 def test_contexts_released_when_stage2_fails(monkeypatch):
     f = Fake(fail2=True)
-    for name, fn in (("sipo_create", f.create), ("sipo_solve", f.solve), ("sipo_set_primal", f.set_primal),
-                     ("sipo_destroy", f.destroy)):
-        monkeypatch.setattr(two_stage, name, fn)
+    _patch(monkeypatch, f)
     with pytest.raises(RuntimeError):
         two_stage.two_stage_solve(GEO, np.ones((4, 4, 2), np.float32))
-    assert f.destroyed == [0, 1]
+    assert sorted(f.destroyed) == [0, 1]
