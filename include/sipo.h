@@ -230,7 +230,9 @@ int sipo_response_metrics(sipo_ctx *ctx, const sipo_response *M, const float *m_
  * res->cert_slice names the slice.  y_out (nullable) receives y*, the normalised
  * projection of Eq. 18, as [n_angles][n_det][nz] in FP32 (FP64 when storage
  * is SIPO_F64), host or device per y_location.  Blocks until done.  Errors:
- * INVALID_ARG, CUDA, TIMEOUT. */
+ * INVALID_ARG, CUDA, TIMEOUT (a bounded device-side wait of the staged
+ * backprojector gave up), NUMERIC (its rows did not fit the staged box; the
+ * geometry cannot produce this). */
 int sipo_solve(sipo_ctx *ctx, void *y_out, int y_location, sipo_result *res);
 
 /* Warm start, for precision escalation (a reading of the mixed-precision
@@ -360,8 +362,11 @@ const char *sipo_phase_name(int i);
  * 0 = 8 voxel columns per warp at 2 blocks/SM, 1 = 4 columns at 2 blocks/SM,
  * 2 = 4 columns at 3 blocks/SM, 3 and 4 = the single-precision row-pattern
  * kernel (4 columns, the rows of each angle in registers, packed FP32
- * multiply-adds) at 2 and 3 blocks/SM; FP64 contexts run entry 2 for 3 and 4.
- * Every entry gives the same sums bit for bit within one precision. */
+ * multiply-adds) at 2 and 3 blocks/SM, 5 and 6 = the row-pattern kernel fed
+ * by tensor-memory (TMA) copies of each angle's detector rows into shared
+ * memory, at 3 and 2 blocks/SM, when nz is a multiple of 256 (else entry 4).
+ * FP64 contexts run entry 2 for 3-6.  Every entry gives the same sums bit for
+ * bit within one precision. */
 int sipo_tile_count(void);
 
 /* Total kernels this library has launched in this process (graph nodes count

@@ -1252,6 +1252,7 @@ struct Solver final : SolverBase {
   void finish_solve(void* y_out, int loc, sipo_result* res) override {
     ck(cudaMemcpyAsync(h_st, st, sizeof(Scal), cudaMemcpyDeviceToHost, stream), "read state");
     ck(cudaStreamSynchronize(stream), "solve");
+    check_bp_fault();
     if (!h_st->done) {
       final_check();
       ck(cudaMemcpyAsync(h_st, st, sizeof(Scal), cudaMemcpyDeviceToHost, stream), "read state");
@@ -1301,6 +1302,15 @@ struct Solver final : SolverBase {
     res->kernel_launches = launches;
     res->tile_cfg = bp_nv;
     res->cert_slice = h.status == 1 ? h.cert_z : -1;
+  }
+
+  // A bounded wait inside the staged backprojector gave up (bit 0), or an
+  // angle's rows did not fit its box (bit 1): the sums of that launch are not
+  // valid, so the solve is an error.
+  void check_bp_fault() {
+    const unsigned int f = bp3_fault_take();
+    if (f & 1u) fail(SIPO_ERR_TIMEOUT, "backprojector: a wait on a tensor-memory copy timed out");
+    if (f) fail(SIPO_ERR_NUMERIC, "backprojector: detector rows outside the staged box");
   }
 
   // copies n elements of S (converted to C) to out (host or device)

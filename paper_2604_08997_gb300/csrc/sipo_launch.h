@@ -29,8 +29,15 @@ void launch_ray_spans(const Geo<C>& g, const uint8_t* need, int2* out, cudaStrea
 
 // tile: entry of the backprojector tile table (0: 8 columns per warp, 2
 // blocks/SM; 1: 4 columns, 2 blocks/SM; 2: 4 columns, 3 blocks/SM; 3, 4: the
-// single-precision row-pattern kernel at 2 and 3 blocks/SM, entry 2 in FP64).
-constexpr int kBpTiles = 5;
+// single-precision row-pattern kernel at 2 and 3 blocks/SM, entry 2 in FP64;
+// 5, 6: the row-pattern kernel with rows staged by tensor-memory copies, at 3
+// and 2 blocks/SM, for nz a multiple of 256, else entry 4).
+constexpr int kBpTiles = 7;
+
+// Reads and clears the fault flag of the staged backprojector (nonzero: a
+// bounded wait on a tensor-memory copy gave up; the launch's sums are not
+// valid).  Synchronous: call outside stream capture.
+unsigned int bp3_fault_take();
 template <typename SI, typename S, typename C, int MODE, typename O>
 void launch_backproject(const Geo<C>& g, const SI* sino, const Bufs<S, C>& b, O* out,
                         const uint8_t* need, int zl, cudaStream_t stream, int tile = 0);

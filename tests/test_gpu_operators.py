@@ -86,11 +86,12 @@ def test_operator_pair_matches_oracle(sipo, case, storage):
 @pytest.mark.parametrize("case", CASES)
 def test_every_backprojector_tile_matches_the_oracle(sipo, case):
     """Each entry of the backprojector tile table (0-2: per-voxel row window;
-    3-4: row patterns with packed multiply-adds) against the oracle, and the
-    entries against each other: they add the same terms in the same order, so
-    the FP32 sums agree bit for bit."""
+    3-4: row patterns with packed multiply-adds; 5-6: the same fed by
+    tensor-memory copies into shared memory, on the z = 256 case) against the
+    oracle, and the entries against each other: they add the same terms in the
+    same order, so the FP32 sums agree bit for bit."""
     n_tiles = sipo.sipo_tile_count()
-    assert n_tiles == 5
+    assert n_tiles == 7
     outs = []
     for tile in range(n_tiles):
         ctx, ogeo, _ = _ctx(sipo, case, sipo.SIPO_F32, tile=tile)
