@@ -302,6 +302,24 @@ int sipo_set_primal(sipo_ctx *ctx, const void *y, int y_location, double u, doub
  * solved), CUDA. */
 int sipo_set_primal_from(sipo_ctx *dst, const sipo_ctx *src, double scale, double u, double v);
 
+/* Farkas test with a dual point from another context, for the infeasibility
+ * diagnostic of Secs. 2.7.1-2.7.2.  The dual point (lam_up, lam_lo) of src's
+ * most recent solve (its last check's T(z)) is tested once as a ray proving
+ * ctx's LP (Case 1 or Case 2) primal infeasible, with the bound-based test
+ * that sipo_solve runs at every check (slice by slice when the PSF has no z
+ * extent).  The test is homogeneous in the ray, so src may normalise the same
+ * part differently: the general form with w1 = 1, w2 = 0 on the same target
+ * and band minimises the band-to-gel dose ratio, and when its optimum u~*
+ * exceeds a Case-2 ratio r its optimal dual is a Farkas ray of Case 2 at r
+ * (Eqs. 40-45: band d <= 1 and gel d >= f_T / (r min f_T) cannot both hold).
+ * *certified = 1 if the test proves infeasibility (then *slice, if non-null,
+ * receives the slice that carries it, or -1 for a whole-volume proof), else
+ * 0.  Both contexts must have the same geometry, device and region labels.
+ * Resets ctx's solver state (a later sipo_solve starts from zero).
+ * Synchronises both streams.  Errors: INVALID_ARG (null, same context,
+ * mismatch, general-form ctx, src not solved), CUDA, TIMEOUT. */
+int sipo_farkas_from(sipo_ctx *ctx, const sipo_ctx *src, int *certified, int *slice);
+
 /* Solves n independent contexts as one batch (a parameter sweep): one CUDA
  * graph holds one check period of every context as parallel branches (each on
  * its context's stream), so small LPs share the device and the host waits

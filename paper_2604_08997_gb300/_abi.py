@@ -96,6 +96,7 @@ SIGNATURES = {
     "sipo_warm_start": (c_int, [c_void_p, c_void_p]),
     "sipo_set_primal": (c_int, [c_void_p, c_void_p, c_int, c_double, c_double]),
     "sipo_set_primal_from": (c_int, [c_void_p, c_void_p, c_double, c_double, c_double]),
+    "sipo_farkas_from": (c_int, [c_void_p, c_void_p, POINTER(c_int), POINTER(c_int)]),
     "sipo_get_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, POINTER(c_double)]),
     "sipo_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, POINTER(c_double)]),
     "sipo_project": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
@@ -349,6 +350,14 @@ def sipo_set_primal_from(dst: Context, src: Context, scale: float = 1.0, u: floa
     """sipo_set_primal_from(dst, src, scale, u, v): dst's next solve starts from
     scale times the point src's last solve returned, without leaving the device."""
     _check(load().sipo_set_primal_from(dst.handle, src.handle, float(scale), float(u), float(v)))
+
+
+def sipo_farkas_from(ctx: Context, src: Context) -> tuple[bool, int]:
+    """sipo_farkas_from(ctx, src): does src's last dual point prove ctx's LP
+    infeasible?  Returns (certified, slice or -1)."""
+    cert, sl = c_int(0), c_int(-1)
+    _check(load().sipo_farkas_from(ctx.handle, src.handle, ctypes.byref(cert), ctypes.byref(sl)))
+    return bool(cert.value), int(sl.value)
 
 
 def sipo_get_state(ctx: Context, y, lam_up, lam_lo) -> dict:

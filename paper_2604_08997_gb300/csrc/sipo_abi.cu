@@ -96,6 +96,10 @@ struct SolverBase {
                           double omega) = 0;
   // start from src's last returned primal point times `scale` (same geometry)
   virtual void primal_from(const SolverBase& src, double scale, double u, double v) = 0;
+  // tests src's last returned dual point as a Farkas ray of this LP (bound-based
+  // test); returns 1 if it proves infeasibility, with the slice in *slice
+  virtual int farkas_from(const SolverBase& src, int* slice) = 0;
+  virtual std::vector<double> label_counts() const = 0;
   virtual std::vector<double> geometry_fingerprint() const = 0;
   // the point T(z) of the last check: y, lam_up, lam_lo (compute type) and u~, v~, omega, k
   virtual void state_to(void* y, void* lam_up, void* lam_lo, int loc, double* scalars) = 0;
@@ -382,6 +386,39 @@ struct Solver final : SolverBase {
     convert_from<C>(pt.yp, pt.s_dtype, ts, (long long)SN, stream);
     count(1);
     start_from(ts, scale, nullptr, nullptr, SIPO_DEVICE, u, v, -1.0);
+  }
+
+  std::vector<double> label_counts() const override { return {double(n_band), double(n_gel)}; }
+
+  // The dual point T(z) of src's last check (lam_up, lam_lo) becomes the
+  // candidate of the bound-based certificate of this context's LP (the epoch
+  // difference with a zero anchor) and is tested once, slice by slice where
+  // the operator allows.  The candidate's scale does not matter (the test is
+  // homogeneous), so src may hold another normalisation of the same part, e.g.
+  // the general form with w2 = 0 whose optimum u~* is the best achievable
+  // band-to-gel ratio: its optimal dual, tested in Case 2 at a ratio below u~*,
+  // is a Farkas ray.  Resets this context's solver state.
+  int farkas_from(const SolverBase& src, int* slice) override {
+    if (src.geometry_fingerprint() != geometry_fingerprint() || src.label_counts() != label_counts())
+      fail(SIPO_ERR_INVALID_ARG, "Farkas test: the contexts differ in geometry, device or labels");
+    if (!cert_on) fail(SIPO_ERR_INVALID_ARG, "Farkas test: the general form has no bound-based certificate");
+    ck(cudaStreamSynchronize(src.strm()), "Farkas test: source");
+    const Point pt = src.point();
+    if (pt.st.k <= 0 && pt.st.done == 0)
+      fail(SIPO_ERR_INVALID_ARG, "Farkas test: the source context has not been solved");
+    init_state();  // zero anchors lu0, ll0: the candidate is lam itself
+    convert_from<S>(pt.lpu, pt.s_dtype, lpu, (long long)V, stream);
+    convert_from<S>(pt.lpl, pt.s_dtype, lpl, (long long)V, stream);
+    count(2);
+    enqueue_certificate(stream);
+    ck(cudaGetLastError(), "Farkas test");
+    ck(cudaMemcpyAsync(h_st, st, sizeof(Scal), cudaMemcpyDeviceToHost, stream), "read state");
+    ck(cudaStreamSynchronize(stream), "Farkas test");
+    check_bp_fault();
+    const int cert = h_st->cert;
+    if (slice) *slice = cert ? h_st->cert_z : -1;
+    init_state();
+    return cert;
   }
 
   // Shared tail of the starts: ts (device, compute type, SN values, freed
@@ -1172,29 +1209,7 @@ struct Solver final : SolverBase {
     }
     launch_project<S, S, C, kFpResid, C>(g, psf ? kq : qp, B, (C*)nullptr, act_col, zl, s, nbits, rspan);
     count(1);
-    if (cert_slices) {
-      // bound-based certificate of the epoch difference lam+ - lam0, per slice
-      k_cert_vol_z<S, C><<<kCertBlocks, kThreads, 0, s>>>(B, (long long)nx * ny, nz, cert_pz);
-      const C* cq = cert_q;
-      if (psf) {
-        psf3<C, C>(cert_q, t3, t1, t2, -1, s);
-        cq = t3;
-      }
-      launch_project<C, S, C, kFpCertZ, C>(g, cq, B, (C*)nullptr, act_col, zl, s, nbits, rspan);
-      k_cert_decide_z<<<1, kThreads, 0, s>>>(st, cert_pz, kCertBlocks, nz, cert_kz, cert_Bz);
-      count(3);
-    } else if (cert_on) {
-      // bound-based certificate of the epoch difference lam+ - lam0
-      k_cert_vol<S, C><<<kRedBlocks, kThreads, 0, s>>>(B, (long long)V);
-      const C* cq = cert_q;
-      if (psf) {
-        psf3<C, C>(cert_q, t3, t1, t2, -1, s);
-        cq = t3;
-      }
-      launch_project<C, S, C, kFpCert, C>(g, cq, B, (C*)nullptr, act_col, zl, s, nbits, rspan);
-      k_cert_decide<<<1, kThreads, 0, s>>>(st, part);
-      count(3);
-    }
+    enqueue_certificate(s);
     k_scalar_check<<<1, kThreads, 0, s>>>(st, part);
     count(1);
     if (ze > 1) {
@@ -1205,6 +1220,34 @@ struct Solver final : SolverBase {
       k_blend_vol<S, C, 1><<<kRedBlocks, kThreads, 0, s>>>(B, nvv);
     }
     count(2);
+  }
+
+  // Bound-based certificate of the epoch difference lam+ - lam0 (per slice when
+  // the operator does not couple z-slices): sets st->cert (and st->cert_z).
+  void enqueue_certificate(cudaStream_t s) {
+    const Geo<C> g = geo();
+    const Bufs<S, C> B = bufs();
+    if (cert_slices) {
+      k_cert_vol_z<S, C><<<kCertBlocks, kThreads, 0, s>>>(B, (long long)nx * ny, nz, cert_pz);
+      const C* cq = cert_q;
+      if (psf) {
+        psf3<C, C>(cert_q, t3, t1, t2, -1, s);
+        cq = t3;
+      }
+      launch_project<C, S, C, kFpCertZ, C>(g, cq, B, (C*)nullptr, act_col, zl, s, nbits, rspan);
+      k_cert_decide_z<<<1, kThreads, 0, s>>>(st, cert_pz, kCertBlocks, nz, cert_kz, cert_Bz);
+      count(3);
+    } else if (cert_on) {
+      k_cert_vol<S, C><<<kRedBlocks, kThreads, 0, s>>>(B, (long long)V);
+      const C* cq = cert_q;
+      if (psf) {
+        psf3<C, C>(cert_q, t3, t1, t2, -1, s);
+        cq = t3;
+      }
+      launch_project<C, S, C, kFpCert, C>(g, cq, B, (C*)nullptr, act_col, zl, s, nbits, rspan);
+      k_cert_decide<<<1, kThreads, 0, s>>>(st, part);
+      count(3);
+    }
   }
 
   void build_graph() {
@@ -1606,6 +1649,15 @@ int sipo_set_primal_from(sipo_ctx* dst, const sipo_ctx* src, double scale, doubl
   if (dst == src) sipo::fail(SIPO_ERR_INVALID_ARG, "primal transfer: source and destination are the same context");
   if (!(scale > 0) || !std::isfinite(scale)) sipo::fail(SIPO_ERR_INVALID_ARG, "scale must be finite and > 0");
   dst->c.s->primal_from(*src->c.s, scale, u, v);
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
+int sipo_farkas_from(sipo_ctx* ctx, const sipo_ctx* src, int* certified, int* slice) {
+  SIPO_TRY
+  if (!ctx || !src || !certified) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
+  if (ctx == src) sipo::fail(SIPO_ERR_INVALID_ARG, "Farkas test: source and destination are the same context");
+  *certified = ctx->c.s->farkas_from(*src->c.s, slice);
   return SIPO_OK;
   SIPO_CATCH
 }

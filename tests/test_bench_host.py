@@ -59,3 +59,21 @@ def test_reference_arm_prints_the_contract_line(capsys):
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_uses_every_host_core(capsys):
+    """On a multi-slice workload the reference arm runs one spawned oracle
+    process per host core (each on its own z-slices) and reports that rate
+    with the core count, plus the single-process rate."""
+    import json
+    import os
+    if (os.cpu_count() or 1) < 2:
+        pytest.skip("one host core")
+    rc = bench.main(["--impl", "reference", "--workload", "csg32", "--cpu-seconds", "1",
+                     "--steps", "2", "--warmup", "3"])
+    assert rc == 0
+    d = json.loads([l for l in capsys.readouterr().out.splitlines() if l.strip()][0])
+    cb = d["cpu_baseline"]
+    assert 1 < cb["cores"] <= os.cpu_count()
+    assert cb["single_thread"]["cores"] == 1 and cb["single_thread"]["value"] > 0
+    assert cb["value"] == d["value"] > cb["single_thread"]["value"]

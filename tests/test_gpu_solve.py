@@ -578,3 +578,62 @@ def test_one_infeasible_slice_is_certified_and_named(sipo, storage):
     assert res["cert_slice"] == -1
     assert abs(res["pobj"] - ref["obj"]) <= (1e-7 if storage == "f64" else 1e-4) * abs(ref["obj"])
     sipo.sipo_destroy(ctx)
+
+
+def test_batched_sweep_invariants(sipo):
+    """A tolerance and inhibition sweep solved as one batch (FP64): Case-1
+    optima u~*(delta) cannot increase as delta widens the feasible set
+    (Sec. 2.7.1), Case-2 feasibility is monotone in the ratio r and v~*(r)
+    cannot increase where feasible (Sec. 2.7.2: a larger r lowers the gel
+    rows' bound f~ = f_T / (r min f_T)); every status agrees with the dense
+    simplex on the same LP."""
+    deltas = (0.02, 0.05, 0.1, 0.2)
+    ratios = (0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9)
+    specs = [(1, dict(tol_lo=d, tol_hi=d)) for d in deltas] + [(2, dict(inhibit_ratio=r)) for r in ratios]
+    ctxs, simplex_status = [], []
+    for case, extra in specs:
+        lp, ops, geo, tgt, cp = _tiny(case, extra)
+        simplex_status.append(simplex.solve_dense(lp, ops)[0])
+        ctxs.append(sipo.sipo_create(geo, tgt, cp, dict(storage=sipo.SIPO_F64, kkt_tol=1e-9, max_iter=64 * 800)))
+    res = sipo.sipo_solve_batched(ctxs)
+    for r, st in zip(res, simplex_status):
+        want = sipo.SIPO_OPTIMAL if st == "optimal" else sipo.SIPO_PRIMAL_INFEASIBLE
+        assert r["status"] == want, (r["status_name"], st)
+    u = [r["pobj"] for r in res[:len(deltas)]]
+    assert all(a >= b - 1e-7 for a, b in zip(u, u[1:])), u
+    c2 = res[len(deltas):]
+    feas = [r["status"] == sipo.SIPO_OPTIMAL for r in c2]
+    assert feas == sorted(feas) and any(feas) and not all(feas), feas
+    v = [r["pobj"] for r in c2 if r["status"] == sipo.SIPO_OPTIMAL]
+    assert all(a >= b - 1e-7 for a, b in zip(v, v[1:])), v
+    for c in ctxs:
+        sipo.sipo_destroy(c)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_case2_with_separation_certifies_or_starts(sipo, storage):
+    """The separation LP (general form, w1 = 1, w2 = 0) on the 16-slice stack
+    gives the best band-to-gel ratio u~*, equal to HiGHS's optimum of the same
+    LP; at r = 0.62 the stack with its infeasible slice has u~* > r and the
+    separation dual proves Case 2 infeasible on slice 8 at once; without that
+    slice u~* < r and Case 2 started from the scaled separation point reaches
+    the oracle optimum."""
+    from paper_2604_08997_gb300 import case2_with_separation
+    from test_oracle_lp import _highs
+    st = sipo.SIPO_F64 if storage == "f64" else sipo.SIPO_F32
+    tol = dict(storage=st, kkt_tol=1e-8 if storage == "f64" else 1e-5, max_iter=100000)
+    for bad, expect in ((8, sipo.SIPO_PRIMAL_INFEASIBLE), (None, sipo.SIPO_OPTIMAL)):
+        lp, ops, geo, tgt, cp = _slice_stack(16, bad)
+        lp0, ops0 = build_lp(Geometry(12, 12, 16, uniform_angles(10), 17), tgt,
+                             CaseParams(case=0, w1=1.0, w2=0.0, band_width=2))
+        ref = _highs(lp0, ops0, method="highs-ipm")
+        assert ref.status == 0
+        out = case2_with_separation(geo, tgt, 0.62, band_width=2, tolerances=tol)
+        assert out["ratio_bound"] == pytest.approx(ref.fun, rel=1e-7 if storage == "f64" else 1e-4)
+        assert out["status"] == expect, out
+        if bad is not None:
+            assert out["certified"] and out["cert_slice"] == bad and ref.fun > 0.62
+        else:
+            ref2 = pdhg.solve(lp, ops, kkt_tol=1e-8, max_iter=100000)
+            assert ref2["status"] == pdhg.OPTIMAL and ref.fun < 0.62
+            assert out["case2"]["pobj"] == pytest.approx(ref2["obj"], rel=1e-7 if storage == "f64" else 1e-4)

@@ -109,8 +109,12 @@ def test_infeasible_case2_reported_by_both():
 
 
 def _highs(lp, ops, method="highs"):
+    """The LP of `lp` for scipy's HiGHS (no PSF): the slice operator P^T on
+    every z-slice, i.e. P^T (x) I_nz in the [y][x][z] / [angle][bin][z] order."""
+    assert not any(s > 0 for s in ops.geo.psf_sigma)
     act = np.flatnonzero(lp.active)
-    M = ops.PT[:, act]
+    PT = ops.PT if ops.geo.nz == 1 else sp.kron(ops.PT, sp.identity(ops.geo.nz), format="csr")
+    M = PT[:, act]
     band, gel = np.flatnonzero(lp.band), np.flatnonzero(lp.gel)
     nb, ng, ny = band.size, gel.size, act.size
     ucol = sp.csr_matrix((-np.ones(nb) if lp.has_u else np.zeros(nb),
@@ -663,3 +667,27 @@ def test_per_slice_certificate_ends_the_solve_sooner(monkeypatch):
     monkeypatch.setattr(pdhg, "certificate", lambda *a, **k: whole(*a, per_slice=False))
     res = pdhg.solve(lp, ops, kkt_tol=1e-7, max_iter=5120)
     assert res["status"] == pdhg.ITER_LIMIT
+
+
+def test_separation_lp_settles_case2_feasibility():
+    """The general form with w1 = 1, w2 = 0 minimises the band-to-gel dose ratio
+    (its optimum u~* equals HiGHS's).  Case 2 at ratio r is feasible iff
+    u~* <= r: above it the separation LP's optimal dual passes the bound-based
+    Farkas test of the Case-2 LP; below it the separation point over r
+    satisfies every Case-2 row (Eqs. 40-45)."""
+    r = 0.62
+    for bad in (8, None):
+        lp2, ops2 = _slice_stack(16, bad, ratio=r)
+        tgt = np.concatenate([lp2.f_T.reshape(12, 12, 16)], axis=2)
+        lp0, ops0 = build_lp(ops2.geo, tgt, CaseParams(case=GENERAL, w1=1.0, w2=0.0, band_width=2))
+        ref = _highs(lp0, ops0, method="highs-ipm")
+        res = pdhg.solve(lp0, ops0, kkt_tol=1e-6, max_iter=100000)
+        assert res["status"] == pdhg.OPTIMAL and abs(res["obj"] - ref.fun) <= 1e-5 * ref.fun
+        cert = pdhg.certificate(lp2, ops2, res["lam_up"], res["lam_lo"], *pdhg.certificate_data(lp2, ops2))
+        if bad is not None:
+            assert ref.fun > r and cert
+        else:
+            assert ref.fun < r and not cert
+            y = res["y"] / r
+            d = ops2.AT(y.reshape(ops2.geo.sino_shape)).ravel()
+            assert np.all(d[lp2.band] <= 1.0 + 1e-5) and np.all(d[lp2.gel] >= lp2.lower[lp2.gel] * (1 - 1e-5))
