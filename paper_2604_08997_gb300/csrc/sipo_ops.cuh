@@ -166,6 +166,24 @@ __device__ __forceinline__ int fp_line_taps(const Geo<C>& g, const NeedBits& nb,
   return nt;
 }
 
+// acc += w * v elementwise; single precision in packed pairs (__ffma2_rn:
+// two z values per instruction, each rounded like fmaf).
+template <typename C, int ZL>
+__device__ __forceinline__ void fma_z(C (&acc)[ZL], C w, const C (&v)[ZL]) {
+  if constexpr (sizeof(C) == 4 && ZL % 2 == 0) {
+    const float2 ww = make_float2(w, w);
+#pragma unroll
+    for (int i = 0; i < ZL; i += 2) {
+      const float2 a = __ffma2_rn(ww, make_float2(v[i], v[i + 1]), make_float2(acc[i], acc[i + 1]));
+      acc[i] = a.x;
+      acc[i + 1] = a.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < ZL; ++i) acc[i] = fma(w, v[i], acc[i]);
+  }
+}
+
 template <bool ROWS, bool FAST, typename SI, typename C, int ZL>
 __device__ __forceinline__ void fp_walk(const Geo<C>& g, const SI* vz, const NeedBits& nb, bool use_bits, int k,
                                         C jf, C c, C s, int lo, int hi, TapList<C>& tl, C (&acc)[ZL]) {
@@ -203,18 +221,12 @@ __device__ __forceinline__ void fp_walk(const Geo<C>& g, const SI* vz, const Nee
 #pragma unroll
       for (int u = 0; u < 4; ++u) load_z<SI, C, ZL>(vz + (size_t)tl.col[t + u] * g.nz, v[u]);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const C w = tl.w[t + u];
-#pragma unroll
-        for (int i = 0; i < ZL; ++i) acc[i] = fma(w, v[u][i], acc[i]);
-      }
+      for (int u = 0; u < 4; ++u) fma_z<C, ZL>(acc, tl.w[t + u], v[u]);
     }
     for (; t < total; ++t) {
       C v[ZL];
       load_z<SI, C, ZL>(vz + (size_t)tl.col[t] * g.nz, v);
-      const C w = tl.w[t];
-#pragma unroll
-      for (int i = 0; i < ZL; ++i) acc[i] = fma(w, v[i], acc[i]);
+      fma_z<C, ZL>(acc, tl.w[t], v);
     }
     __syncwarp();
   }
