@@ -209,6 +209,17 @@ typedef struct sipo_response_result {
 int sipo_response_map(const sipo_response *M, const float *in, float *out, long long n, double scale,
                       int inverse, void *stream);
 
+/* The inhibition ratio of Case 2 for a threshold given as a response
+ * (Sec. 2.7.2 mapped through Eq. 5): r = M^-1(m_crit) / M^-1(min m_T), the
+ * minimum over the device float32 array m_T (n values) of the responses above
+ * the lower asymptote alpha (the part; M is increasing, so this is the
+ * part's smallest prescribed dose).  *ratio receives r, *gel_min (nullable)
+ * that minimum response.  Synchronises `stream`.  Errors: INVALID_ARG (bad
+ * model, null, n <= 0, m_crit outside (alpha, k), no response inside
+ * (alpha, k)), CUDA. */
+int sipo_response_inhibit_ratio(const sipo_response *M, const float *m_T, long long n, double m_crit,
+                                double *ratio, double *gel_min, void *stream);
+
 /* Response-domain back end of ctx's last solve: m_T ([ny][nx][nz] float32,
  * host or device per `location`, positive on gel) is the target response.
  * alpha > 0 is used as the post-scaling factor; otherwise (0, negative or

@@ -91,6 +91,8 @@ SIGNATURES = {
                                     POINTER(c_void_p)]),
     "sipo_response_map": (c_int, [POINTER(sipo_response), c_void_p, c_void_p, c_longlong, c_double, c_int,
                                   c_void_p]),
+    "sipo_response_inhibit_ratio": (c_int, [c_void_p, c_void_p, c_longlong, c_double, POINTER(c_double),
+                                            POINTER(c_double), c_void_p]),
     "sipo_response_metrics": (c_int, [c_void_p, POINTER(sipo_response), c_void_p, c_int, c_double,
                                       POINTER(sipo_response_result)]),
     "sipo_warm_start": (c_int, [c_void_p, c_void_p]),
@@ -306,6 +308,21 @@ def sipo_response_map(M, src, dst, inverse: bool, scale: float = 1.0, stream=Non
     _check(load().sipo_response_map(ctypes.byref(r), c_void_p(ps), c_void_p(pd), int(src.numel()),
                                     float(scale), 1 if inverse else 0, _stream(stream)))
     return dst
+
+
+def sipo_response_inhibit_ratio(M, m_T, m_crit: float, stream=None) -> tuple[float, float]:
+    """Case-2 ratio M^-1(m_crit) / M^-1(min_gel m_T) computed on the device
+    (see include/sipo.h); returns (ratio, smallest prescribed response)."""
+    if str(m_T.dtype) not in ("torch.float32", "float32"):
+        raise ValueError("m_T must be float32")
+    p, loc = _ptr(m_T)
+    if loc == SIPO_HOST:
+        raise ValueError("m_T must be a device tensor")
+    r = sipo_response(*M)
+    ratio, gmin = c_double(0.0), c_double(0.0)
+    _check(load().sipo_response_inhibit_ratio(ctypes.byref(r), c_void_p(p), int(m_T.numel()), float(m_crit),
+                                              ctypes.byref(ratio), ctypes.byref(gmin), _stream(stream)))
+    return float(ratio.value), float(gmin.value)
 
 
 def sipo_response_metrics(ctx: Context, M, m_T, alpha: float = 0.0) -> dict:

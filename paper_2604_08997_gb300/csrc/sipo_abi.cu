@@ -1702,6 +1702,34 @@ int sipo_response_map(const sipo_response* M, const float* in, float* out, long 
   SIPO_CATCH
 }
 
+int sipo_response_inhibit_ratio(const sipo_response* M, const float* m_T, long long n, double m_crit,
+                                double* ratio, double* gel_min, void* stream) {
+  SIPO_TRY
+  const sipo::Richards r = richards_of(M);
+  if (!m_T || !ratio || n <= 0) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument or empty target");
+  if (!(m_crit > M->alpha && m_crit < M->k)) sipo::fail(SIPO_ERR_INVALID_ARG, "m_crit must lie in (alpha, k)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned int* d_min = nullptr;
+  double* d_out = nullptr;
+  sipo::ck(cudaMallocAsync(reinterpret_cast<void**>(&d_min), sizeof(unsigned int), s), "response ratio");
+  sipo::ck(cudaMallocAsync(reinterpret_cast<void**>(&d_out), 2 * sizeof(double), s), "response ratio");
+  sipo::ck(cudaMemsetAsync(d_min, 0xff, sizeof(unsigned int), s), "response ratio");
+  sipo::k_response_gel_min<<<sipo::grid_for(n), sipo::kThreads, 0, s>>>(m_T, n, M->alpha, d_min);
+  sipo::k_response_case2_ratio<<<1, 32, 0, s>>>(d_min, r, m_crit, d_out, d_out + 1);
+  sipo::ck(cudaGetLastError(), "response ratio");
+  sipo::g_launches += 2;
+  double h[2];
+  sipo::ck(cudaMemcpyAsync(h, d_out, sizeof(h), cudaMemcpyDeviceToHost, s), "response ratio");
+  sipo::ck(cudaFreeAsync(d_min, s), "response ratio");
+  sipo::ck(cudaFreeAsync(d_out, s), "response ratio");
+  sipo::ck(cudaStreamSynchronize(s), "response ratio");
+  if (!std::isfinite(h[0])) sipo::fail(SIPO_ERR_INVALID_ARG, "no prescribed response inside (alpha, k)");
+  *ratio = h[0];
+  if (gel_min) *gel_min = h[1];
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
 int sipo_response_metrics(sipo_ctx* ctx, const sipo_response* M, const float* m_T, int location, double alpha,
                           sipo_response_result* out) {
   SIPO_TRY

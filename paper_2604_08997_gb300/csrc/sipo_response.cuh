@@ -3,6 +3,8 @@
 // inverse, and the response-domain post-scaling and metrics of a solved dose.
 #pragma once
 
+#include <math_constants.h>
+
 #include "sipo_device.cuh"
 
 namespace sipo {
@@ -122,6 +124,39 @@ __global__ void __launch_bounds__(kThreads) k_response_ratio(const C* __restrict
     if (threadIdx.x == 0) part[j * gridDim.x + blockIdx.x] = sh[0];
     __syncthreads();
   }
+}
+
+// Case 2 with a response threshold (Sec. 2.7.2 through Eq. 5): the smallest
+// prescribed response over the part (values above the lower asymptote alpha),
+// as ordered bits of a float, then the ratio M^-1(m_crit) / M^-1(min m_T).
+__device__ __forceinline__ unsigned int ordered_bits(float x) {
+  const unsigned int b = __float_as_uint(x);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float from_ordered_bits(unsigned int k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+__global__ void k_response_gel_min(const float* __restrict__ mT, long long n, double alpha,
+                                   unsigned int* __restrict__ out) {
+  unsigned int best = 0xffffffffu;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float m = mT[i];
+    if (double(m) > alpha) best = min(best, ordered_bits(m));  // NaN fails the test
+  }
+  atomicMin(out, best);
+}
+
+// One thread: ratio = M^-1(m_crit) / M^-1(gel minimum), NaN when either is
+// outside (alpha, k) or no response lies above alpha.
+__global__ void k_response_case2_ratio(const unsigned int* __restrict__ mn, Richards r, double m_crit,
+                                       double* __restrict__ ratio, double* __restrict__ gel_min) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double g = *mn == 0xffffffffu ? CUDART_NAN : double(from_ordered_bits(*mn));
+  *gel_min = g;
+  const bool ok = g > r.alpha && g < r.k && m_crit > r.alpha && m_crit < r.k;
+  *ratio = ok ? richards_inverse(r, m_crit) / richards_inverse(r, g) : CUDART_NAN;
 }
 
 }  // namespace sipo

@@ -21,8 +21,8 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from ._abi import (SIPO_CASE2, SIPO_GENERAL, sipo_create, sipo_create_bounded, sipo_response_map,
-                   sipo_response_metrics)
+from ._abi import (SIPO_CASE2, SIPO_GENERAL, sipo_create, sipo_create_bounded, sipo_response_inhibit_ratio,
+                   sipo_response_map, sipo_response_metrics)
 
 
 @dataclass(frozen=True)
@@ -75,13 +75,9 @@ def response_case1(geometry: dict, m_T, M: Richards, eps_lo: float = 0.05, eps_h
 def response_case2(geometry: dict, m_T, M: Richards, m_crit: float, band_width: int = 10,
                    tolerances: dict | None = None):
     """Case 2 with the inhibition threshold given as a response m_crit (f_crit = M^-1(m_crit))."""
-    import torch
     m = _device(m_T)
     f_T = response_to_dose(M, m)
-    gel_min = m[m > M.alpha].min().reshape(1)
-    ends = response_to_dose(M, torch.cat([torch.tensor([m_crit], dtype=torch.float32, device=m.device),
-                                          gel_min]))
-    ratio = float(ends[0]) / float(ends[1])
+    ratio, _ = sipo_response_inhibit_ratio(M.as_tuple(), m, m_crit)
     return sipo_create(geometry, f_T, dict(kase=SIPO_CASE2, inhibit_ratio=ratio, band_width=band_width),
                        tolerances or {})
 

@@ -121,3 +121,21 @@ def test_response_case2_threshold_is_the_response_threshold(sipo):
     res = sipo.sipo_solve(ctx)
     want = float(response_inverse(ORichards(*MP), np.array([0.33]))[0])
     assert abs(res["f_crit"] - want) <= 1e-6 * want
+
+
+def test_response_inhibit_ratio_on_the_device(sipo):
+    """sipo_response_inhibit_ratio: the part's smallest prescribed response and
+    r = M^-1(m_crit) / M^-1(min m_T) against the oracle's inverse in FP64; a
+    threshold outside (alpha, k) and a target without a part are refused."""
+    from paper_2604_08997_gb300._abi import sipo_response_inhibit_ratio
+    m_T, *_ = _response_target()
+    m = torch.from_numpy(np.ascontiguousarray(m_T)).cuda()
+    r, gmin = sipo_response_inhibit_ratio(MP, m, 0.33)
+    OM = ORichards(*MP)
+    assert gmin == pytest.approx(float(m_T[m_T > 0].min()), rel=0, abs=0)
+    want = float(response_inverse(OM, np.array([0.33]))[0] / response_inverse(OM, np.array([gmin]))[0])
+    assert r == pytest.approx(want, rel=1e-12)
+    with pytest.raises(sipo.SipoError):
+        sipo_response_inhibit_ratio(MP, m, 1.5)
+    with pytest.raises(sipo.SipoError):
+        sipo_response_inhibit_ratio(MP, torch.zeros(16, device="cuda"), 0.33)

@@ -1,7 +1,8 @@
 """Host logic of the response-domain front end (Sec. 2.1, Eq. 5; Sec. 2.7.1) with
 the device calls faked by the oracle's FP64 map on CPU tensors (CPU only):
 Case 1 passes M^-1 of m_T, (1 - eps_lo) m_T and (1 + eps_hi) m_T as target and
-bounds; Case 2 passes the ratio M^-1(m_crit) / M^-1(min_gel m_T)."""
+bounds; Case 2 passes the ratio M^-1(m_crit) / M^-1(min_gel m_T) that the
+library computes on the device (faked here by the oracle's map)."""
 import numpy as np
 import pytest
 
@@ -37,7 +38,14 @@ def fake(monkeypatch):
         calls["bounded"] = (f_T.clone(), f_L.clone(), f_U.clone(), case)
         return "ctx"
 
+    def ratio(M, m, m_crit, stream=None):
+        om = ORichards(*M)
+        v = m.double().numpy()
+        gmin = float(v[v > M[0]].min())
+        return float(response_inverse(om, np.array([m_crit]))[0] / response_inverse(om, np.array([gmin]))[0]), gmin
+
     monkeypatch.setattr(R, "_device", device)
+    monkeypatch.setattr(R, "sipo_response_inhibit_ratio", ratio)
     monkeypatch.setattr(R, "sipo_response_map", rmap)
     monkeypatch.setattr(R, "sipo_create", create)
     monkeypatch.setattr(R, "sipo_create_bounded", create_bounded)
