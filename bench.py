@@ -481,15 +481,17 @@ def run_gpu(args, dist, rank, world, device):
                 sipo.sipo_destroy(ctx_k)
         if wl.case == 2:
             # Case 2 with its feasibility settled first: the separation LP
-            # (general form, w1 = 1, w2 = 0) gives the best band-to-gel ratio;
-            # above the requested ratio its dual is tested as a Farkas ray,
-            # below it its point starts the Case-2 solve
+            # (Case 1 of the part, tol_lo = 0) gives the best band-to-gel
+            # ratio; its dual is probed as a Farkas ray of Case 2 during the
+            # solve, and a converged point below the ratio starts Case 2
             for label, cpk in runs:
                 tol_k = dict(tol, kkt_tol=1e-4, max_iter=args.kkt_iters)
+                tol_s = dict(tol, kkt_tol=1e-4, max_iter=args.separation_iters)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 ws = sipo.case2_with_separation(geo, tgt, cpk["inhibit_ratio"], band_width=cpk["band_width"],
-                                                tolerances=tol_k)
+                                                tolerances=tol_k, separation_tolerances=tol_s,
+                                                probe_every=args.probe_every)
                 torch.cuda.synchronize()
                 tk = time.perf_counter() - t0
                 sep, c2 = ws["separation"], ws["case2"]
@@ -503,7 +505,8 @@ def run_gpu(args, dist, rank, world, device):
                     "separation_dobj": sep["dobj"],
                     "case2_iters": c2["iters"] if c2 else 0, "case2_kkt": c2["kkt"] if c2 else None,
                     "objective": c2["pobj"] if c2 else None,
-                    "includes": "context creation of both LPs, separation solve, Farkas test or Case-2 solve"}
+                    "separation_form": "Case 1 with tol_lo = 0, tol_hi = 10 (minimum band dose over gel dose >= target)",
+                    "includes": "context creation of both LPs, separation solve with Farkas probes, Case-2 solve"}
         if args.escalate > 0:
             # precision escalation: BF16 storage for at most N iterations, then
             # FP32 warm-started from its last check (both contexts created first)
@@ -576,6 +579,10 @@ def main(argv=None):
     p.add_argument("--profile-iters", type=int, default=8)
     p.add_argument("--kkt-iters", type=int, default=2048)
     p.add_argument("--feasible-ratio", type=float, default=0.85)
+    p.add_argument("--separation-iters", type=int, default=16384,
+                   help="iteration cap of the separation LP that settles Case-2 feasibility")
+    p.add_argument("--probe-every", type=int, default=1024,
+                   help="iterations between Farkas probes of the Case-2 LP during the separation solve")
     p.add_argument("--escalate", type=int, default=0,
                    help="also time BF16 storage for N iterations, then FP32 warm-started from it")
     p.add_argument("--cpu-seconds", type=float, default=20.0)

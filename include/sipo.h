@@ -242,8 +242,10 @@ int sipo_response_metrics(sipo_ctx *ctx, const sipo_response *M, const float *m_
  * projection of Eq. 18, as [n_angles][n_det][nz] in FP32 (FP64 when storage
  * is SIPO_F64), host or device per y_location.  Blocks until done.  Errors:
  * INVALID_ARG, CUDA, TIMEOUT (a bounded device-side wait of the staged
- * backprojector gave up), NUMERIC (its rows did not fit the staged box; the
- * geometry cannot produce this). */
+ * backprojector gave up), NUMERIC (a check found NaN or infinite residuals,
+ * e.g. from an infinite imported start; or the staged backprojector's rows did
+ * not fit its box, which the geometry cannot produce); the context stays
+ * usable. */
 int sipo_solve(sipo_ctx *ctx, void *y_out, int y_location, sipo_result *res);
 
 /* Warm start, for precision escalation (a reading of the mixed-precision
@@ -331,6 +333,19 @@ int sipo_set_primal_from(sipo_ctx *dst, const sipo_ctx *src, double scale, doubl
  * mismatch, general-form ctx, src not solved), CUDA, TIMEOUT. */
 int sipo_farkas_from(sipo_ctx *ctx, const sipo_ctx *src, int *certified, int *slice);
 
+/* sipo_solve of ctx that probes target's infeasibility along the way: every
+ * probe_every iterations (rounded up to check periods) and when the solve
+ * stops, the dual point of ctx's last check is tested as a Farkas ray of
+ * target's LP (as sipo_farkas_from does); the solve stops at the first
+ * certificate, with *certified = 1 and *slice as in sipo_farkas_from, else
+ * *certified = 0.  res receives ctx's result as from sipo_solve (status
+ * ITER_LIMIT when a certificate ended it early).  For the separation solve of
+ * Case 2: ctx holds the same part as Case 1 with tol_lo = 0 (gel dose at least
+ * its target, band dose at most u~), target the Case-2 LP.  Errors: as
+ * sipo_solve and sipo_farkas_from. */
+int sipo_solve_probe(sipo_ctx *ctx, sipo_ctx *target, long long probe_every, sipo_result *res, int *certified,
+                     int *slice);
+
 /* Solves n independent contexts as one batch (a parameter sweep): one CUDA
  * graph holds one check period of every context as parallel branches (each on
  * its context's stream), so small LPs share the device and the host waits
@@ -397,6 +412,15 @@ const char *sipo_phase_name(int i);
  * FP64 contexts run entry 2 for 3-6.  Every entry gives the same sums bit for
  * bit within one precision. */
 int sipo_tile_count(void);
+
+/* Checked builds (compiled with -DSIPO_CHECKED, the library
+ * libsipo_checked.so): synchronises the device and returns the bits of the
+ * index and finiteness checks the kernels recorded since the last call (bit 0
+ * projector tap column or z offset, bit 1 backprojector detector or staged
+ * row, bit 2 epilogue z offset, bit 3 non-finite FP64 block sum), with bit 30
+ * set to mark a checked build, and clears them.  A plain build returns 0.
+ * The checks never trap: a violation is recorded and the kernel goes on. */
+unsigned int sipo_check_flags(void);
 
 /* Total kernels this library has launched in this process (graph nodes count
  * once per graph launch). */

@@ -14,7 +14,9 @@ from ctypes import POINTER, Structure, c_char_p, c_double, c_int, c_longlong, c_
 import numpy as np
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libsipo.so")
+# SIPO_LIBRARY=checked selects the checked build (libsipo_checked.so)
+LIB_PATH = os.path.join(PKG, "libsipo_checked.so" if os.environ.get("SIPO_LIBRARY") == "checked"
+                        else "libsipo.so")
 
 SIPO_OK = 0
 SIPO_F32, SIPO_F64, SIPO_BF16 = 0, 1, 2
@@ -99,6 +101,7 @@ SIGNATURES = {
     "sipo_set_primal": (c_int, [c_void_p, c_void_p, c_int, c_double, c_double]),
     "sipo_set_primal_from": (c_int, [c_void_p, c_void_p, c_double, c_double, c_double]),
     "sipo_farkas_from": (c_int, [c_void_p, c_void_p, POINTER(c_int), POINTER(c_int)]),
+    "sipo_solve_probe": (c_int, [c_void_p, c_void_p, c_longlong, c_void_p, POINTER(c_int), POINTER(c_int)]),
     "sipo_get_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, POINTER(c_double)]),
     "sipo_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, POINTER(c_double)]),
     "sipo_project": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
@@ -111,6 +114,7 @@ SIGNATURES = {
     "sipo_phase_count": (c_int, []),
     "sipo_phase_name": (c_char_p, [c_int]),
     "sipo_tile_count": (c_int, []),
+    "sipo_check_flags": (ctypes.c_uint, []),
     "sipo_kernel_launch_count": (c_longlong, []),
     "sipo_set_tolerances": (c_int, [c_void_p, POINTER(sipo_tolerances)]),
     "sipo_get_trace": (c_int, [c_void_p, POINTER(c_double), c_int]),
@@ -375,6 +379,16 @@ def sipo_farkas_from(ctx: Context, src: Context) -> tuple[bool, int]:
     cert, sl = c_int(0), c_int(-1)
     _check(load().sipo_farkas_from(ctx.handle, src.handle, ctypes.byref(cert), ctypes.byref(sl)))
     return bool(cert.value), int(sl.value)
+
+
+def sipo_solve_probe(ctx: Context, target: Context, probe_every: int = 1024) -> tuple[dict, bool, int]:
+    """sipo_solve of ctx, testing its dual point as a Farkas ray of target's LP
+    every probe_every iterations; returns (result, certified, slice or -1)."""
+    res = sipo_result()
+    cert, sl = c_int(0), c_int(-1)
+    _check(load().sipo_solve_probe(ctx.handle, target.handle, int(probe_every), ctypes.byref(res),
+                                   ctypes.byref(cert), ctypes.byref(sl)))
+    return res.as_dict(), bool(cert.value), int(sl.value)
 
 
 def sipo_get_state(ctx: Context, y, lam_up, lam_lo) -> dict:

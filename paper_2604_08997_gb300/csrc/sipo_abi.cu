@@ -1302,6 +1302,9 @@ struct Solver final : SolverBase {
       ck(cudaStreamSynchronize(stream), "solve");
     }
     solved = true;
+    if (h_st->numeric)
+      fail(SIPO_ERR_NUMERIC, "solve stopped at iteration " + std::to_string(h_st->k) +
+                                 ": non-finite residuals or objectives (NaN or infinite iterates)");
     // f~* = A^T y* of the returned point, recomputed by one plain application
     // of the operator: the iterations carry d by linearity (d+ = (d_bar + d) / 2),
     // which drifts from A^T y by rounding over many steps in FP32
@@ -1535,6 +1538,18 @@ const char* sipo_phase_name(int i) {
 
 int sipo_tile_count(void) { return sipo::kBpTiles; }
 
+unsigned int sipo_check_flags(void) {
+#ifdef SIPO_CHECKED
+  unsigned int v = 0, zero = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess) return 0x80000000u;
+  if (cudaMemcpyFromSymbol(&v, sipo::g_sipo_check, sizeof(v)) == cudaSuccess)
+    cudaMemcpyToSymbol(sipo::g_sipo_check, &zero, sizeof(zero));
+  return v | sipo::check_flags_project() | sipo::check_flags_backproject() | 0x40000000u;
+#else
+  return 0u;
+#endif
+}
+
 static void create_impl(const sipo_geometry* geo, const float* f_T, const float* f_L, const float* f_U,
                         const sipo_case_params* cp, const sipo_tolerances* tol, void* stream, sipo_ctx** out) {
   sipo::g_err.clear();
@@ -1604,6 +1619,47 @@ static void run_solve(sipo::SolverBase* s) {
     s->request_done();
     if (s->done_flag()) break;
   }
+}
+
+// run_solve that, every `probe_every` iterations (rounded up to check periods)
+// and when the solve stops, tests the last check's dual point as a Farkas ray
+// of `target`'s LP; stops at the first certificate.
+static void run_solve_probe(sipo::SolverBase* s, sipo::SolverBase* target, long long probe_every, int* certified,
+                            int* slice) {
+  s->begin_solve();
+  const long long P = s->period(), M = s->max_iter();
+  long long k = 0, next_probe = probe_every;
+  *certified = 0;
+  *slice = -1;
+  while (k < M) {
+    const long long n = std::min(P, M - k);
+    s->launch_block(n);
+    k += n;
+    s->request_done();
+    const bool done = s->done_flag();
+    if (k >= next_probe || done || k >= M) {
+      next_probe = k + probe_every;
+      int sl = -1;
+      if (target->farkas_from(*s, &sl)) {
+        *certified = 1;
+        *slice = sl;
+        break;
+      }
+    }
+    if (done) break;
+  }
+}
+
+int sipo_solve_probe(sipo_ctx* ctx, sipo_ctx* target, long long probe_every, sipo_result* res, int* certified,
+                     int* slice) {
+  SIPO_TRY
+  if (!ctx || !target || !res || !certified || !slice) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
+  if (ctx == target) sipo::fail(SIPO_ERR_INVALID_ARG, "probe: the solved and the tested context are the same");
+  if (probe_every <= 0) sipo::fail(SIPO_ERR_INVALID_ARG, "probe_every must be positive");
+  run_solve_probe(ctx->c.s.get(), target->c.s.get(), probe_every, certified, slice);
+  ctx->c.s->finish_solve(nullptr, SIPO_DEVICE, res);
+  return SIPO_OK;
+  SIPO_CATCH
 }
 
 int sipo_solve(sipo_ctx* ctx, void* y_out, int y_location, sipo_result* res) {

@@ -12,6 +12,20 @@
 
 namespace sipo {
 
+// Bits recorded by this translation unit's kernels in a checked build (0 in
+// plain builds); cleared by the read.
+unsigned int check_flags_backproject() {
+#ifdef SIPO_CHECKED
+  unsigned int v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_sipo_check, sizeof(v)) != cudaSuccess) return 0;
+  cudaMemcpyToSymbol(g_sipo_check, &zero, sizeof(zero));
+  return v;
+#else
+  return 0;
+#endif
+}
+
+
 unsigned int bp3_fault_take() {
   unsigned int v = 0;
   if (cudaMemcpyFromSymbol(&v, g_bp3_fault, sizeof(v)) != cudaSuccess) return 0;

@@ -125,9 +125,17 @@ __device__ __forceinline__ void bp3_generic(const SI* rows, int b0, const Bp2Ent
   }
 }
 
+// Highest bin (exclusive) a warp's entry reads: b + rows of the pattern, or
+// max floor(u) + 2 for the generic body.
+__device__ __forceinline__ int bp3_top(const Bp2Ent& e) {
+  if (e.pat != kBp2Generic) return e.b + bp2_rows(e.pat);
+  return max(max(e.i0.x, e.i0.y), max(e.i0.z, e.i0.w)) + 2;
+}
+
 // rows: the staged box of the angle (bin b0 first), lane offset included.
 template <typename SI, int ZL>
 __device__ __forceinline__ void bp3_angle(const SI* rows, int b0, const Bp2Ent& e, float (&acc)[kBp2NV][ZL]) {
+  SIPO_DCHECK(e.b >= b0 && bp3_top(e) - b0 <= kBp3Rows, 1);
   const SI* own = rows + (e.b - b0) * kBp3ZC;
   switch (e.pat) {
 #define SIPO_BP3_CASE(P) \
@@ -138,13 +146,6 @@ __device__ __forceinline__ void bp3_angle(const SI* rows, int b0, const Bp2Ent& 
     default:
       bp3_generic<SI, ZL>(rows, b0, e, acc);
   }
-}
-
-// Highest bin (exclusive) a warp's entry reads: b + rows of the pattern, or
-// max floor(u) + 2 for the generic body.
-__device__ __forceinline__ int bp3_top(const Bp2Ent& e) {
-  if (e.pat != kBp2Generic) return e.b + bp2_rows(e.pat);
-  return max(max(e.i0.x, e.i0.y), max(e.i0.z, e.i0.w)) + 2;
 }
 
 // Shared-memory plan of the kernel (dynamic, one allocation, offsets from a

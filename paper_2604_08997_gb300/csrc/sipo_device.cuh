@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <math_constants.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -39,6 +40,28 @@ inline int device_sms() {
 constexpr double kEta = 0.99;     // step factor on the Pock-Chambolle steps
 
 enum Label : uint8_t { kExt = 0, kBand = 1, kGel = 2 };
+
+// ------------------------------------------------------------ checked build
+// Built with -DSIPO_CHECKED, the kernels test their computed indices (and the
+// finiteness of their FP64 block sums) and record a violated check as a bit of
+// a per-translation-unit device flag, read and cleared by sipo_check_flags();
+// they neither trap nor stop, and the access goes ahead as in the plain build
+// only when the check holds.  Plain builds compile the checks away.
+//   bit 0: projector tap column or z offset out of range
+//   bit 1: backprojector detector row or staged-box row out of range
+//   bit 2: element-wise update index out of its array
+//   bit 3: non-finite FP64 block sum
+#ifdef SIPO_CHECKED
+static __device__ unsigned int g_sipo_check = 0;
+#define SIPO_DCHECK(cond, bit)                                      \
+  do {                                                              \
+    if (!(cond)) atomicOr(&::sipo::g_sipo_check, 1u << (bit));      \
+  } while (0)
+#else
+#define SIPO_DCHECK(cond, bit) \
+  do {                         \
+  } while (0)
+#endif
 
 // ---------------------------------------------------------------- conversions
 __device__ __forceinline__ float to_c(float x) { return x; }
@@ -259,6 +282,7 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[N], double* part,
     double s = red[0][threadIdx.x];
 #pragma unroll
     for (int w = 1; w < kWarps; ++w) s = mx ? fmax(s, red[w][threadIdx.x]) : s + red[w][threadIdx.x];
+    SIPO_DCHECK(isfinite(s) || (mx && s == CUDART_INF), 3);
     part[(slot0 + threadIdx.x) * kRedBlocks + blockIdx.x] = s;
   }
 }

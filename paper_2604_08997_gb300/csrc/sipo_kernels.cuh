@@ -367,6 +367,13 @@ __global__ void __launch_bounds__(kThreads) k_scalar_check(Scal* st, const doubl
   st->rel_gap = rel_gap; st->pobj = pobj; st->dobj = dobj;
   st->kkt = fmax(rel_p, fmax(rel_d, rel_gap));
   st->sband_p = SbP; st->sgel_p = SgP;
+  if (!isfinite(rel_p) || !isfinite(rel_d) || !isfinite(rel_gap)) {
+    // NaN or infinity in the iterates: no status can be decided from them
+    st->numeric = 1;
+    st->status = 3;
+    st->done = 1;
+    return;
+  }
   // Farkas candidates (primal infeasibility, Secs. 2.7.1-2.7.2): the dual
   // difference since the last restart, and the dual part of the fixed-point
   // residual T(z) - z (which tends to the infimal displacement of PDHG).

@@ -38,6 +38,11 @@ constexpr int kBpTiles = 7;
 // bounded wait on a tensor-memory copy gave up; the launch's sums are not
 // valid).  Synchronous: call outside stream capture.
 unsigned int bp3_fault_take();
+
+// Checked builds (-DSIPO_CHECKED): the check bits recorded by the kernels of
+// each translation unit, read and cleared; 0 in plain builds.
+unsigned int check_flags_project();
+unsigned int check_flags_backproject();
 template <typename SI, typename S, typename C, int MODE, typename O>
 void launch_backproject(const Geo<C>& g, const SI* sino, const Bufs<S, C>& b, O* out,
                         const uint8_t* need, int zl, cudaStream_t stream, int tile = 0);

@@ -216,6 +216,9 @@ __device__ __forceinline__ void fp_walk(const Geo<C>& g, const SI* vz, const Nee
     }
     __syncwarp();
     int t = 0;
+#ifdef SIPO_CHECKED
+    for (int q = lane; q < total; q += 32) SIPO_DCHECK((unsigned(tl.col[q]) < unsigned(g.nx * g.ny)), 0);
+#endif
     for (; t + 4 <= total; t += 4) {
       C v[4][ZL];
 #pragma unroll
@@ -322,6 +325,7 @@ k_project(const Geo<C> g, const SI* __restrict__ vol, const Bufs<S, C> b, O* __r
     }
     if (z0 >= g.nz) continue;
     const size_t base = ((size_t)k * g.nd + j) * g.nz + z0;
+    SIPO_DCHECK((z0 + z_offset<C, ZL>(ZL - 1) < g.nz), 0);
     if constexpr (MODE == kFpStore) {
       store_z<O, C, ZL>(out + base, acc);
     } else if constexpr (MODE == kFpPrimal) {
@@ -532,6 +536,7 @@ k_backproject(const Geo<C> g, const SI* __restrict__ sino, const Bufs<S, C> b, O
       __syncwarp();
       continue;
     }
+    SIPO_DCHECK((z0 + z_offset<C, ZL>(ZL - 1) < g.nz), 2);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const int ix = tx * NV + v;
@@ -614,6 +619,9 @@ __device__ __forceinline__ void bp2_fill(const Geo<float>& g, int k, float yf, f
     }
     w0[v] = unsigned(i0[v]) < unsigned(g.nd) ? a : 0.0f;
     w1[v] = unsigned(i0[v] + 1) < unsigned(g.nd) ? bb : 0.0f;
+    // a clamped row is only ever met with a zero weight
+    SIPO_DCHECK(w0[v] == 0.0f || unsigned(i0[v]) < unsigned(g.nd), 1);
+    SIPO_DCHECK(w1[v] == 0.0f || unsigned(i0[v] + 1) < unsigned(g.nd), 1);
   }
   int b = i0[0];
 #pragma unroll
@@ -784,6 +792,7 @@ k_backproject2(const Geo<float> g, const SI* __restrict__ sino, const Bufs<S, fl
       __syncwarp();
       continue;
     }
+    SIPO_DCHECK((z0 + z_offset<C, ZL>(ZL - 1) < g.nz), 2);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const int ix = tx * NV + v;

@@ -7,6 +7,20 @@
 
 namespace sipo {
 
+// Bits recorded by this translation unit's kernels in a checked build (0 in
+// plain builds); cleared by the read.
+unsigned int check_flags_project() {
+#ifdef SIPO_CHECKED
+  unsigned int v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_sipo_check, sizeof(v)) != cudaSuccess) return 0;
+  cudaMemcpyToSymbol(g_sipo_check, &zero, sizeof(zero));
+  return v;
+#else
+  return 0;
+#endif
+}
+
+
 // bits[line][word] from flags need[y][x]; by_rows selects line = y (bits over
 // x) or line = x (bits over y).
 __global__ void k_need_bits(const uint8_t* __restrict__ need, uint32_t* __restrict__ bits, int nx, int ny,

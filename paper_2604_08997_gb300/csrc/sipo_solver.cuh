@@ -84,6 +84,8 @@ struct Scal {
   double cert_B;
   int cert_on, cert;
   int cert_slices, cert_z;
+  // a check found a non-finite residual or objective (the solve stops)
+  int numeric, pad2;
 };
 
 // Margin of the bound-based certificate: kappa * B <= (1 - kCertMargin) obj.

@@ -486,7 +486,8 @@ def test_host_injected_failures_are_errors_or_statuses(sipo):
     an infinite and a negative target value and an all-zero target are
     refused with INVALID_ARG (-1) and leave no context; an iteration limit
     is a status, not an error; changing a setting fixed at creation is
-    refused and leaves the context usable."""
+    refused and leaves the context usable; an infinite start is a NUMERIC
+    error and the context solves again afterwards."""
     case, extra = TINY[2]
     lp, ops, geo, tgt, cp = _tiny(case, extra)
     tol = dict(storage=sipo.SIPO_F64, kkt_tol=1e-9, max_iter=64)
@@ -507,14 +508,25 @@ def test_host_injected_failures_are_errors_or_statuses(sipo):
     sipo.sipo_set_tolerances(ctx, 1e-9, 100000)
     res = sipo.sipo_solve(ctx)
     assert res["status"] == sipo.SIPO_OPTIMAL
+    # an infinite primal start: the first check finds non-finite residuals and
+    # the solve is a NUMERIC error (-5); the next solve starts from zero again
+    y = np.zeros(lp.active.size)
+    y[np.flatnonzero(lp.active)[0]] = np.inf
+    sipo.sipo_set_primal(ctx, y)
+    with pytest.raises(sipo.SipoError) as e:
+        sipo.sipo_solve(ctx)
+    assert e.value.code == -5 and "non-finite" in str(e.value)
+    res = sipo.sipo_solve(ctx)
+    assert res["status"] == sipo.SIPO_OPTIMAL
 
 
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
 def test_backprojector_tiles_give_identical_solves(sipo, storage):
     """The fused dual step with every backprojector tile entry: the row-pattern
-    kernel (entries 3 and 4) adds the same terms in the same order as the
-    per-voxel window (entries 0-2), so solves agree bit for bit, in FP32 and
-    with BF16 iterate storage (256 z: two groups of four values per lane)."""
+    kernels (entries 3-6, global loads or tensor-memory staging) add the same
+    terms in the same order as the per-voxel window (entries 0-2), so solves
+    agree bit for bit, in FP32 and with BF16 iterate storage (256 z: two
+    groups of four values per lane)."""
     n, nz = 20, 256
     tgt = np.zeros((n, n, nz), np.float32)
     tgt[6:14, 7:13, 40:200] = 1.0
@@ -612,28 +624,28 @@ def test_batched_sweep_invariants(sipo):
 
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 def test_case2_with_separation_certifies_or_starts(sipo, storage):
-    """The separation LP (general form, w1 = 1, w2 = 0) on the 16-slice stack
-    gives the best band-to-gel ratio u~*, equal to HiGHS's optimum of the same
-    LP; at r = 0.62 the stack with its infeasible slice has u~* > r and the
-    separation dual proves Case 2 infeasible on slice 8 at once; without that
-    slice u~* < r and Case 2 started from the scaled separation point reaches
-    the oracle optimum."""
+    """The separation LP (Case 1 of the part with tol_lo = 0, tol_hi = 10) on
+    the 16-slice stack, probed as a Farkas ray of Case 2 at r = 0.62: with the
+    infeasible slice the probe proves Case 2 infeasible on slice 8; without it
+    the separation LP converges to HiGHS's optimum (below r) and Case 2 started
+    from its scaled point reaches the oracle optimum."""
     from paper_2604_08997_gb300 import case2_with_separation
     from test_oracle_lp import _highs
     st = sipo.SIPO_F64 if storage == "f64" else sipo.SIPO_F32
     tol = dict(storage=st, kkt_tol=1e-8 if storage == "f64" else 1e-5, max_iter=100000)
-    for bad, expect in ((8, sipo.SIPO_PRIMAL_INFEASIBLE), (None, sipo.SIPO_OPTIMAL)):
+    for bad in (8, None):
         lp, ops, geo, tgt, cp = _slice_stack(16, bad)
-        lp0, ops0 = build_lp(Geometry(12, 12, 16, uniform_angles(10), 17), tgt,
-                             CaseParams(case=0, w1=1.0, w2=0.0, band_width=2))
-        ref = _highs(lp0, ops0, method="highs-ipm")
-        assert ref.status == 0
-        out = case2_with_separation(geo, tgt, 0.62, band_width=2, tolerances=tol)
-        assert out["ratio_bound"] == pytest.approx(ref.fun, rel=1e-7 if storage == "f64" else 1e-4)
-        assert out["status"] == expect, out
+        out = case2_with_separation(geo, tgt, 0.62, band_width=2, tolerances=tol, probe_every=256)
         if bad is not None:
-            assert out["certified"] and out["cert_slice"] == bad and ref.fun > 0.62
+            assert out["status"] == sipo.SIPO_PRIMAL_INFEASIBLE and out["certified"], out
+            assert out["cert_slice"] == bad
         else:
+            lp1, ops1 = build_lp(Geometry(12, 12, 16, uniform_angles(10), 17), tgt,
+                                 CaseParams(case=1, tol_lo=0.0, tol_hi=10.0, band_width=2))
+            ref = _highs(lp1, ops1, method="highs-ipm")
+            assert ref.status == 0 and ref.fun < 0.62
+            assert out["separation"]["status"] == sipo.SIPO_OPTIMAL and not out["certified"]
+            assert out["ratio_bound"] == pytest.approx(ref.fun, rel=1e-7 if storage == "f64" else 1e-4)
             ref2 = pdhg.solve(lp, ops, kkt_tol=1e-8, max_iter=100000)
-            assert ref2["status"] == pdhg.OPTIMAL and ref.fun < 0.62
+            assert ref2["status"] == pdhg.OPTIMAL and out["status"] == sipo.SIPO_OPTIMAL
             assert out["case2"]["pobj"] == pytest.approx(ref2["obj"], rel=1e-7 if storage == "f64" else 1e-4)

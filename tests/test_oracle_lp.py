@@ -670,24 +670,30 @@ def test_per_slice_certificate_ends_the_solve_sooner(monkeypatch):
 
 
 def test_separation_lp_settles_case2_feasibility():
-    """The general form with w1 = 1, w2 = 0 minimises the band-to-gel dose ratio
-    (its optimum u~* equals HiGHS's).  Case 2 at ratio r is feasible iff
-    u~* <= r: above it the separation LP's optimal dual passes the bound-based
-    Farkas test of the Case-2 LP; below it the separation point over r
-    satisfies every Case-2 row (Eqs. 40-45)."""
+    """The separation LP minimises the band-to-gel dose ratio: in the general
+    form with w1 = 1, w2 = 0, or as Case 1 with tol_lo = 0 and tol_hi = 10 (the
+    gel upper rows are slack at the optimum here), both optima equal (HiGHS).
+    Case 2 at ratio r is feasible iff u~* <= r: above it the separation LP's
+    optimal dual (either form) passes the bound-based Farkas test of the
+    Case-2 LP; below it the separation point over r satisfies every Case-2 row
+    (Eqs. 40-45)."""
     r = 0.62
     for bad in (8, None):
         lp2, ops2 = _slice_stack(16, bad, ratio=r)
-        tgt = np.concatenate([lp2.f_T.reshape(12, 12, 16)], axis=2)
+        tgt = lp2.f_T.reshape(12, 12, 16)
         lp0, ops0 = build_lp(ops2.geo, tgt, CaseParams(case=GENERAL, w1=1.0, w2=0.0, band_width=2))
-        ref = _highs(lp0, ops0, method="highs-ipm")
-        res = pdhg.solve(lp0, ops0, kkt_tol=1e-6, max_iter=100000)
-        assert res["status"] == pdhg.OPTIMAL and abs(res["obj"] - ref.fun) <= 1e-5 * ref.fun
-        cert = pdhg.certificate(lp2, ops2, res["lam_up"], res["lam_lo"], *pdhg.certificate_data(lp2, ops2))
-        if bad is not None:
-            assert ref.fun > r and cert
-        else:
-            assert ref.fun < r and not cert
-            y = res["y"] / r
-            d = ops2.AT(y.reshape(ops2.geo.sino_shape)).ravel()
-            assert np.all(d[lp2.band] <= 1.0 + 1e-5) and np.all(d[lp2.gel] >= lp2.lower[lp2.gel] * (1 - 1e-5))
+        lp1, ops1 = build_lp(ops2.geo, tgt, CaseParams(case=CASE1, tol_lo=0.0, tol_hi=10.0, band_width=2))
+        ref0 = _highs(lp0, ops0, method="highs-ipm")
+        ref1 = _highs(lp1, ops1, method="highs-ipm")
+        assert abs(ref0.fun - ref1.fun) <= 1e-7 * ref0.fun
+        for lp, ops, ref in ((lp0, ops0, ref0), (lp1, ops1, ref1)):
+            res = pdhg.solve(lp, ops, kkt_tol=1e-6, max_iter=100000)
+            assert res["status"] == pdhg.OPTIMAL and abs(res["obj"] - ref.fun) <= 1e-5 * ref.fun
+            cert = pdhg.certificate(lp2, ops2, res["lam_up"], res["lam_lo"], *pdhg.certificate_data(lp2, ops2))
+            if bad is not None:
+                assert ref.fun > r and cert
+            else:
+                assert ref.fun < r and not cert
+                y = res["y"] / r
+                d = ops2.AT(y.reshape(ops2.geo.sino_shape)).ravel()
+                assert np.all(d[lp2.band] <= 1.0 + 1e-5) and np.all(d[lp2.gel] >= lp2.lower[lp2.gel] * (1 - 1e-5))
