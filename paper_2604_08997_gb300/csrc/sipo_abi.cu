@@ -1332,7 +1332,9 @@ struct Solver final : SolverBase {
     }
     const Scal& h = *h_st;
     std::memset(res, 0, sizeof(*res));
-    res->status = h.status;
+    // a solve stopped by its caller before a decision (a probe's certificate)
+    // reports the iteration limit
+    res->status = h.done ? h.status : SIPO_ITER_LIMIT;
     res->restarts = h.restarts;
     res->iters = h.k;
     res->kkt = h.kkt; res->rel_primal = h.rel_p; res->rel_dual = h.rel_d; res->rel_gap = h.rel_gap;

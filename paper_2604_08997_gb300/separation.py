@@ -16,10 +16,10 @@ current dual point as a Farkas ray of Case 2 at r (sipo_solve_probe runs the
 library's bound-based test, slice by slice where the PSF allows).  A ray is a
 certificate by itself, whatever the accuracy of the iterate that gave it, so
 the first one that passes ends the workflow with PRIMAL_INFEASIBLE.  If the
-separation LP converges instead with u~* <= r, its primal point over r
-satisfies every Case-2 row and starts the Case-2 solve (sipo_set_primal_from),
-as the two-stage design of Sec. 3.2 does with a Case-1 point; otherwise Case 2
-runs from zero.  Host orchestration only: every step runs in libsipo.
+separation LP ends instead with u~ <= r, its primal point over r satisfies
+every Case-2 row (up to its primal residual) and starts the Case-2 solve
+(sipo_set_primal_from), as the two-stage design of Sec. 3.2 does with a
+Case-1 point; otherwise Case 2 runs from zero.  Host orchestration only: every step runs in libsipo.
 """
 from __future__ import annotations
 
@@ -51,8 +51,9 @@ def case2_with_separation(geometry: dict, f_T, ratio: float, band_width: int = 1
         if cert:
             out["status"] = SIPO_PRIMAL_INFEASIBLE
             return out
-        if rs["status"] == SIPO_OPTIMAL and rs["pobj"] <= ratio:
-            # band d <= u~* <= r and gel d >= f_T / min f_T: over r, a Case-2 point
+        if rs["pobj"] <= ratio:
+            # band d <= u~ <= r and gel d >= f_T / min f_T: over r, a Case-2
+            # point (up to the separation's primal residual if it stopped early)
             sipo_set_primal_from(ctx2, sep, 1.0 / ratio)
         r2 = sipo_solve(ctx2)
         out.update(case2=r2, status=r2["status"])

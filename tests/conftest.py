@@ -10,6 +10,7 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device (GB300, sm_103a)")
+    config.addinivalue_line("markers", "slow: minutes of CPU work; runs only with SIPO_SLOW=1")
 
 
 @pytest.fixture(scope="session")
