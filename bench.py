@@ -349,6 +349,24 @@ def run_sweep(args, device):
         torch.cuda.synchronize()
         elapsed = time.perf_counter() - t0
     launches = sipo.sipo_kernel_launch_count() - n0
+    sequential = None
+    if args.sweep_sequential:
+        # the same LPs solved one after another (one graph per context), for
+        # the batched form's comparison with the plain form
+        for c in ctxs:
+            sipo.sipo_destroy(c)
+        ctxs = []
+        for wl in wls:
+            tol = dict(storage=storage, kkt_tol=1e-4, max_iter=args.kkt_iters, check_every=args.check_every)
+            ctxs.append(sipo.sipo_create(geometry_dict(wl), torch.from_numpy(wl.target).to(device),
+                                         case_dict(wl), tol))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        seq = [sipo.sipo_solve(c) for c in ctxs]
+        torch.cuda.synchronize()
+        seq_s = time.perf_counter() - t0
+        same = sum(1 for a, b in zip(res, seq) if a["status"] == b["status"] and a["iters"] == b["iters"])
+        sequential = {"seconds": seq_s, "same_status_and_iterations": same, "of": len(seq)}
     per_lp = [{"n": wl.n, "n_angles": wl.n_angles, "case": wl.case,
                "param": wl.tol_lo if wl.case == 1 else wl.inhibit_ratio,
                "status": r["status_name"], "iters": r["iters"], "kkt": r["kkt"], "objective": r["pobj"]}
@@ -369,7 +387,8 @@ def run_sweep(args, device):
                                    f"views, Case 1 delta 0.02-0.20 and Case 2 r 0.60-0.90, one batch",
                        "iteration_cap": args.kkt_iters, "storage": args.storage},
             "gpu_launches": int(launches), "create_seconds": t_create, "statuses": statuses,
-            "iterations_per_second": total_iters / elapsed, "per_lp": per_lp, "clocks": clocks.summary()}
+            "iterations_per_second": total_iters / elapsed, "sequential": sequential, "per_lp": per_lp,
+            "clocks": clocks.summary()}
 
 
 def run_gpu(args, dist, rank, world, device):
@@ -585,6 +604,8 @@ def main(argv=None):
                    help="iterations between Farkas probes of the Case-2 LP during the separation solve")
     p.add_argument("--escalate", type=int, default=0,
                    help="also time BF16 storage for N iterations, then FP32 warm-started from it")
+    p.add_argument("--sweep-sequential", action="store_true",
+                   help="--workload sweep: also solve the LPs one after another and time that")
     p.add_argument("--cpu-seconds", type=float, default=20.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     args = p.parse_args(argv)

@@ -422,6 +422,19 @@ int sipo_tile_count(void);
  * The checks never trap: a violation is recorded and the kernel goes on. */
 unsigned int sipo_check_flags(void);
 
+/* Self-test of the bounded waits of the staged backprojector (table entries 5
+ * and 6): one block of `threads` threads (1..1024) on the current device waits
+ * on an mbarrier's first phase with a budget of `budget_cycles` SM clock cycles
+ * (> 0).  With `arrive` != 0 thread 0 makes the one arrival the barrier expects
+ * and every wait ends at once; with `arrive` == 0 nothing completes the phase
+ * and every wait gives up after its budget, as a wait on a tensor-memory copy
+ * that never lands does in the kernel (where it sets the fault that makes the
+ * solve return SIPO_ERR_TIMEOUT).  *timed_out receives the number of threads
+ * whose wait gave up.  Returns SIPO_ERR_TIMEOUT when every wait gave up,
+ * SIPO_OK when none did, SIPO_ERR_CUDA on a CUDA error, SIPO_ERR_INVALID_ARG
+ * for bad arguments.  Synchronises the device; no solver state is touched. */
+int sipo_wait_selftest(long long budget_cycles, int arrive, int threads, unsigned int *timed_out);
+
 /* Total kernels this library has launched in this process (graph nodes count
  * once per graph launch). */
 long long sipo_kernel_launch_count(void);

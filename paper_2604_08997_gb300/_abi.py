@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(PKG, "libsipo_checked.so" if os.environ.get("SIPO_LIBRAR
                         else "libsipo.so")
 
 SIPO_OK = 0
+SIPO_ERR_INVALID_ARG, SIPO_ERR_CUDA, SIPO_ERR_TIMEOUT, SIPO_ERR_NUMERIC = -1, -2, -4, -5
 SIPO_F32, SIPO_F64, SIPO_BF16 = 0, 1, 2
 SIPO_HOST, SIPO_DEVICE = 0, 1
 SIPO_GENERAL, SIPO_CASE1, SIPO_CASE2 = 0, 1, 2
@@ -115,6 +116,7 @@ SIGNATURES = {
     "sipo_phase_name": (c_char_p, [c_int]),
     "sipo_tile_count": (c_int, []),
     "sipo_check_flags": (ctypes.c_uint, []),
+    "sipo_wait_selftest": (c_int, [c_longlong, c_int, c_int, POINTER(ctypes.c_uint)]),
     "sipo_kernel_launch_count": (c_longlong, []),
     "sipo_set_tolerances": (c_int, [c_void_p, POINTER(sipo_tolerances)]),
     "sipo_get_trace": (c_int, [c_void_p, POINTER(c_double), c_int]),
@@ -500,6 +502,17 @@ def sipo_kernel_launch_count() -> int:
 def sipo_tile_count() -> int:
     """Entries of the backprojector tile table (values of tolerances["tile_cfg"])."""
     return int(load().sipo_tile_count())
+
+
+def sipo_wait_selftest(budget_cycles: int, arrive: bool, threads: int = 128) -> tuple[int, int]:
+    """Runs the staged backprojector's bounded mbarrier wait on its own (see
+    include/sipo.h); returns (library return code, threads whose wait gave
+    up).  SIPO_ERR_TIMEOUT is the expected code when `arrive` is False."""
+    out = ctypes.c_uint(0)
+    rc = load().sipo_wait_selftest(int(budget_cycles), int(bool(arrive)), int(threads), ctypes.byref(out))
+    if rc not in (SIPO_OK, SIPO_ERR_TIMEOUT):
+        _check(rc)
+    return int(rc), int(out.value)
 
 
 def sipo_set_tolerances(ctx: Context, kkt_tol: float, max_iter: int, check_every: int = 64,

@@ -76,9 +76,12 @@ struct SolverBase {
   virtual int get_trace(double* out, int max_entries) = 0;
   // batched solves: zero start without a graph, one check period enqueued on
   // `s` (check step + period - 1 fused steps) followed by a copy of the state
-  // to the pinned host mirror, and that mirror
+  // to the pinned host mirror, and that mirror.  enqueue_period returns the
+  // kernels it enqueued without counting them (it is captured into a graph);
+  // add_launches counts one launch of that graph.
   virtual void init_for_batch() = 0;
-  virtual void enqueue_period(cudaStream_t s) = 0;
+  virtual long long enqueue_period(cudaStream_t s) = 0;
+  virtual void add_launches(long long n) = 0;
   virtual const Scal& host_state() const = 0;
   // warm start: the last check's T(z) of a finished solve (device arrays and
   // their element types), a problem fingerprint, and the import of such a point
@@ -271,11 +274,18 @@ struct Solver final : SolverBase {
     t_start = std::chrono::steady_clock::now();
   }
 
-  void enqueue_period(cudaStream_t s) override {
+  long long enqueue_period(cudaStream_t s) override {
+    const long long before = launches;
     enqueue_check(s);
     for (int i = 1; i < P; ++i) enqueue_normal(s);
     ck(cudaMemcpyAsync(h_st, st, sizeof(Scal), cudaMemcpyDeviceToHost, s), "state copy");
+    const long long k = launches - before;
+    launches = before;
+    g_launches -= k;
+    return k;
   }
+
+  void add_launches(long long n) override { count(n); }
 
   const Scal& host_state() const override { return *h_st; }
 
@@ -1552,6 +1562,22 @@ unsigned int sipo_check_flags(void) {
 #endif
 }
 
+int sipo_wait_selftest(long long budget_cycles, int arrive, int threads, unsigned int* timed_out) {
+  SIPO_TRY
+  if (!timed_out || budget_cycles <= 0 || threads < 1 || threads > 1024)
+    sipo::fail(SIPO_ERR_INVALID_ARG, "wait self-test: null output, budget <= 0 or threads outside 1..1024");
+  *timed_out = 0;
+  if (sipo::wait_selftest(budget_cycles, arrive, threads, timed_out) != 0)
+    sipo::fail(SIPO_ERR_CUDA, "wait self-test: CUDA error");
+  if (*timed_out == (unsigned int)threads) {
+    sipo::g_err = "wait self-test: every bounded wait gave up";
+    return SIPO_ERR_TIMEOUT;
+  }
+  if (*timed_out != 0) sipo::fail(SIPO_ERR_CUDA, "wait self-test: only some of the waits gave up");
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
 static void create_impl(const sipo_geometry* geo, const float* f_T, const float* f_L, const float* f_U,
                         const sipo_case_params* cp, const sipo_tolerances* tol, void* stream, sipo_ctx** out) {
   sipo::g_err.clear();
@@ -1813,46 +1839,60 @@ int sipo_solve_batched(sipo_ctx** ctxs, int n, void** y_outs, int y_location, si
       sipo::fail(SIPO_ERR_INVALID_ARG, "the contexts of a batch must have been created on one device");
   }
   for (auto* x : s) x->init_for_batch();
-  // One graph per check period of the whole batch: every context's period is
-  // a branch forked from, and joined back into, a master stream.
+  // One graph per check period of the unfinished contexts: every context's
+  // period is a branch forked from, and joined back into, a master stream.
+  // The graph is rebuilt without a context once it has finished, so finished
+  // contexts launch nothing.
   cudaStream_t master = nullptr;
   sipo::ck(cudaStreamCreateWithFlags(&master, cudaStreamNonBlocking), "stream");
   std::vector<cudaEvent_t> ev(n + 1, nullptr);
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  auto cleanup = [&]() {
+  auto drop_graph = [&]() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+  };
+  auto cleanup = [&]() {
+    drop_graph();
     for (auto e : ev)
       if (e) cudaEventDestroy(e);
     if (master) cudaStreamDestroy(master);
   };
   try {
     for (auto& e : ev) sipo::ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
-    sipo::ck(cudaStreamBeginCapture(master, cudaStreamCaptureModeThreadLocal), "begin capture");
-    sipo::ck(cudaEventRecord(ev[n], master), "fork");
-    for (int i = 0; i < n; ++i) {
-      cudaStream_t si = s[i]->strm();
-      sipo::ck(cudaStreamWaitEvent(si, ev[n], 0), "fork wait");
-      s[i]->enqueue_period(si);
-      sipo::ck(cudaEventRecord(ev[i], si), "join");
-      sipo::ck(cudaStreamWaitEvent(master, ev[i], 0), "join wait");
-    }
-    sipo::ck(cudaStreamEndCapture(master, &graph), "end capture");
-    sipo::ck(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
-    size_t nodes = 0;
-    sipo::ck(cudaGraphGetNodes(graph, nullptr, &nodes), "graph nodes");
     // iteration limits round up to whole check periods; a context whose limit
     // is reached stops at the check that opens its next period
     long long max_periods = 0;
     for (auto* x : s) max_periods = std::max(max_periods, (x->max_iter() + x->period() - 1) / x->period() + 1);
-    for (long long p = 0; p < max_periods; ++p) {
+    std::vector<int> live(n);
+    for (int i = 0; i < n; ++i) live[i] = i;
+    std::vector<long long> per(n, 0);
+    for (long long p = 0; p < max_periods && !live.empty(); ++p) {
+      if (!exec) {
+        sipo::ck(cudaStreamBeginCapture(master, cudaStreamCaptureModeThreadLocal), "begin capture");
+        sipo::ck(cudaEventRecord(ev[n], master), "fork");
+        for (int i : live) {
+          cudaStream_t si = s[i]->strm();
+          sipo::ck(cudaStreamWaitEvent(si, ev[n], 0), "fork wait");
+          per[i] = s[i]->enqueue_period(si);
+          sipo::ck(cudaEventRecord(ev[i], si), "join");
+          sipo::ck(cudaStreamWaitEvent(master, ev[i], 0), "join wait");
+        }
+        sipo::ck(cudaStreamEndCapture(master, &graph), "end capture");
+        sipo::ck(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
+      }
       sipo::ck(cudaGraphLaunch(exec, master), "graph launch");
-      sipo::g_launches += (long long)nodes;
+      for (int i : live) s[i]->add_launches(per[i]);
       sipo::ck(cudaStreamSynchronize(master), "batch period");
-      bool all = true;
-      for (auto* x : s) all = all && x->host_state().done != 0;
-      if (all) break;
+      std::vector<int> still;
+      for (int i : live)
+        if (s[i]->host_state().done == 0) still.push_back(i);
+      if (still.size() != live.size()) {
+        drop_graph();
+        live.swap(still);
+      }
     }
   } catch (...) {
     cleanup();

@@ -36,6 +36,20 @@ unsigned int bp3_fault_take() {
   return v;
 }
 
+int wait_selftest(long long budget, int arrive, int threads, unsigned int* timed_out) {
+  unsigned int* d = nullptr;
+  if (cudaMalloc(&d, sizeof(unsigned int)) != cudaSuccess) return -1;
+  cudaError_t e = cudaMemset(d, 0, sizeof(unsigned int));
+  if (e == cudaSuccess) {
+    k_wait_selftest<<<1, threads>>>(budget, arrive, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(timed_out, d, sizeof(unsigned int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? 0 : -1;
+}
+
 namespace {
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {

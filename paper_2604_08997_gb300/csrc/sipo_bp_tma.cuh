@@ -60,14 +60,33 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity; false once kBp3WaitCycles
-// SM clock cycles have passed without it.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the phase with the given parity; false once `budget` SM
+// clock cycles have passed without it.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget = kBp3WaitCycles) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > kBp3WaitCycles) return false;
+    if (clock64() - t0 > budget) return false;
   return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Self-test of the bounded wait: one mbarrier expecting one arrival, which
+// thread 0 makes only when `arrive` is set; every thread waits on the first
+// phase with a budget of `budget` cycles.  out[0] = number of threads whose wait
+// gave up (blockDim.x when nothing arrives, 0 otherwise).
+__global__ void k_wait_selftest(long long budget, int arrive, unsigned int* out) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && arrive) mbar_arrive(&bar);
+  if (!mbar_wait(&bar, 0u, budget)) atomicAdd(out, 1u);
 }
 
 // One box of the 3-D tensor map (z, bin, angle) into shared memory,
@@ -297,7 +316,17 @@ k_backproject3(const Geo<float> g, const SI* __restrict__ sino, const __grid_con
           }
         }
         __syncthreads();  // every warp is done with the slot
-        if (*abort_flag) break;
+        if (*abort_flag) {
+          // the copies still in flight write this block's shared memory: wait
+          // for them (bounded) before the block ends
+          if (threadIdx.x == 0)
+            for (int j = q; j < min(nst, q + kBp3Stages); ++j) {
+              const int sj = stage_seq + j;
+              mbar_wait(bars + sj % kBp3Stages, uint32_t((sj / kBp3Stages) & 1));
+            }
+          __syncthreads();
+          break;
+        }
         if (threadIdx.x == 0 && q + kBp3Stages < nst) issue(q + kBp3Stages);
       }
       stage_seq += nst;

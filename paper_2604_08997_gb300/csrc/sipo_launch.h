@@ -39,6 +39,12 @@ constexpr int kBpTiles = 7;
 // valid).  Synchronous: call outside stream capture.
 unsigned int bp3_fault_take();
 
+// Runs the bounded mbarrier wait of the staged backprojector on its own: one
+// block of `threads` threads waits `budget` cycles on a barrier that receives
+// its one arrival only if `arrive`; *timed_out = threads whose wait gave up.
+// 0 on success, -1 on a CUDA error.  Synchronous.
+int wait_selftest(long long budget, int arrive, int threads, unsigned int* timed_out);
+
 // Checked builds (-DSIPO_CHECKED): the check bits recorded by the kernels of
 // each translation unit, read and cleared; 0 in plain builds.
 unsigned int check_flags_project();

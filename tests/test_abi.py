@@ -114,6 +114,11 @@ def test_new_entries_validate_before_device_work(lib):
     fake = ctypes.c_void_p(1)
     assert lib.sipo_set_primal_from(fake, fake, 1.0, -1.0, -1.0) == -1
     assert b"same context" in lib.sipo_last_error()
+    n_out = ctypes.c_uint(7)
+    for budget, threads, outp in ((0, 32, ctypes.byref(n_out)), (1000, 0, ctypes.byref(n_out)),
+                                  (1000, 1025, ctypes.byref(n_out)), (1000, 32, None)):
+        assert lib.sipo_wait_selftest(budget, 0, threads, outp) == -1
+        assert b"wait self-test" in lib.sipo_last_error()
 
 
 def test_noalloc_wrapper_refuses_mismatched_buffers():

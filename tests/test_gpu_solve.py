@@ -221,6 +221,8 @@ def test_csg_case2_fp32_certificate_and_bf16(sipo):
     assert abs(res["pobj"] - ref["obj"]) <= 1e-3 * abs(ref["obj"])
     ctx16 = sipo.sipo_create(geo, tgt, cp, dict(storage=sipo.SIPO_BF16, kkt_tol=1e-4, max_iter=20000))
     r16 = sipo.sipo_solve(ctx16)
+    print("bf16", r16["status_name"], r16["iters"], r16["kkt"], r16["rel_primal"], r16["rel_gap"],
+          r16["pobj"], "f32", res["pobj"], "oracle", ref["obj"], flush=True)
     assert r16["status"] in (sipo.SIPO_OPTIMAL, sipo.SIPO_ITER_LIMIT)
     assert abs(r16["pobj"] - ref["obj"]) <= 2e-2 * abs(ref["obj"])
 
@@ -518,6 +520,25 @@ def test_host_injected_failures_are_errors_or_statuses(sipo):
     assert e.value.code == -5 and "non-finite" in str(e.value)
     res = sipo.sipo_solve(ctx)
     assert res["status"] == sipo.SIPO_OPTIMAL
+
+
+def test_bounded_wait_runs_out_and_reports_timeout(sipo):
+    """Failure detection on the device without a fault: the staged
+    backprojector's bounded mbarrier wait, run on a barrier that nothing
+    completes (its one expected arrival is never made), gives up after its
+    budget (2e6 cycles, about 1 ms) in every thread, and the library returns
+    SIPO_ERR_TIMEOUT; with the arrival made, every wait ends and the call
+    returns SIPO_OK.  The device stays usable: a solve runs afterwards."""
+    from paper_2604_08997_gb300._abi import SIPO_ERR_TIMEOUT, SIPO_OK, sipo_wait_selftest
+    rc, n = sipo_wait_selftest(2_000_000, arrive=False, threads=128)
+    assert rc == SIPO_ERR_TIMEOUT and n == 128
+    rc, n = sipo_wait_selftest(2_000_000, arrive=True, threads=128)
+    assert rc == SIPO_OK and n == 0
+    case, extra = TINY[0]
+    lp, ops, geo, tgt, cp = _tiny(case, extra)
+    ctx = sipo.sipo_create(geo, tgt, cp, dict(storage=sipo.SIPO_F64, kkt_tol=1e-9, max_iter=4096))
+    assert sipo.sipo_solve(ctx)["status"] == sipo.SIPO_OPTIMAL
+    sipo.sipo_destroy(ctx)
 
 
 @pytest.mark.parametrize("storage", ["f32", "bf16"])

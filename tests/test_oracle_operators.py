@@ -16,6 +16,7 @@ from scipy import ndimage
 from oracle.operators import (Geometry, Operators, apply_psf, backprojector_matrix,
                               detector_coordinate, psf_tap_derivative, psf_taps)
 from oracle import sample
+from synthetic.targets import discs_2d, uniform_angles
 
 
 def _disc_area(n, r, cx, cy, ss=8):
@@ -254,3 +255,24 @@ def test_single_output_samplers_agree_with_matrices():
         assert abs(sample.psf_voxel(geo, vol, iy, ix, iz) - kv[iy, ix, iz]) < 1e-12
         k, j = rng.integers(0, 9), rng.integers(0, 29)
         assert abs(sample.project_ray(geo, vol, k, j, iz) - pr[k, j, iz]) < 1e-12
+
+
+@pytest.mark.parametrize("n, n_angles, n_det", [(64, 96, 91), (64, 360, 64), (48, 180, 67)])
+def test_active_set_readings_differ_only_on_grazing_rays(n, n_angles, n_det):
+    """Sec. 2.2 defines the active rays as {[P f_T]_j > 0}.  The FP32 kernels
+    decide it with their own u (two fused multiply-adds in single precision),
+    the FP64 definition with u in double.  With f_T >= 0 and weights
+    max(0, 1 - |u - j|), a ray can change sides only through a tap whose
+    weight is within single-precision rounding of zero (u within ~1e-5 of
+    j -+ 1), so every ray on which the two readings differ carries an FP64
+    value of at most a few such weights; the test bounds that value and
+    reports how many rays differ."""
+    tgt = discs_2d(n, n_discs=3, r_range=(n / 10, n / 5), container_radius=n / 2 - 4, seed=4)
+    geo = Geometry(n, n, 1, uniform_angles(n_angles), n_det)
+    v64 = backprojector_matrix(geo, precision="f64").T @ tgt.ravel().astype(np.float64)
+    v32 = backprojector_matrix(geo, precision="f32").T @ tgt.ravel().astype(np.float64)
+    diff = (v64 > 0) != (v32 > 0)
+    print(f"active rays: {int((v64 > 0).sum())} (FP64), {int((v32 > 0).sum())} (FP32 u), "
+          f"{int(diff.sum())} differ of {diff.size}")
+    assert diff.sum() <= 1e-2 * diff.size
+    assert np.all(v64[diff] <= 4 * 2.0 ** -16 * n) and np.all(v32[diff] <= 4 * 2.0 ** -16 * n)
