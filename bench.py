@@ -433,10 +433,13 @@ def run_gpu(args, dist, rank, world, device):
     fp_ms = phases["project_primal"]
     tr_bp = captured_traffic(args.workload, args.storage, "backproject")
     tr_fp = captured_traffic(args.workload, args.storage, "project")
+    bp_name = {0: "k_backproject", 1: "k_backproject", 2: "k_backproject", 3: "k_backproject2",
+               4: "k_backproject2"}.get(res["tile_cfg"], "k_backproject3")
+    fp_name = "k_project"
     if bp_ms >= fp_ms:
-        dom, dom_ms, taps, traffic = "k_backproject (fused dual update)", bp_ms, bp_taps, tr_bp
+        dom, dom_ms, taps, traffic = f"{bp_name} (fused dual update)", bp_ms, bp_taps, tr_bp
     else:
-        dom, dom_ms, taps, traffic = "k_project (fused primal update)", fp_ms, fp_taps, tr_fp
+        dom, dom_ms, taps, traffic = f"{fp_name} (fused primal update)", fp_ms, fp_taps, tr_fp
     # algorithmic HBM bytes: every input element once, every output once
     el = 2 if args.storage == "bf16" else (8 if args.storage == "f64" else 4)
     cw = 8 if args.storage == "f64" else 4
@@ -505,7 +508,10 @@ def run_gpu(args, dist, rank, world, device):
             # solve, and a converged point below the ratio starts Case 2
             for label, cpk in [("requested", cp)]:
                 tol_k = dict(tol, kkt_tol=1e-4, max_iter=args.kkt_iters)
-                tol_s = dict(tol, kkt_tol=1e-4, max_iter=args.separation_iters)
+                # the separation LP runs in FP32 storage (BF16 iterates stall
+                # above the accuracy its certificate needs)
+                tol_s = dict(tol, kkt_tol=1e-4, max_iter=args.separation_iters,
+                             storage=sipo.SIPO_F64 if tol["storage"] == sipo.SIPO_F64 else sipo.SIPO_F32)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 ws = sipo.case2_with_separation(geo, tgt, cpk["inhibit_ratio"], band_width=cpk["band_width"],

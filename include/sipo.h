@@ -115,9 +115,10 @@ typedef struct sipo_case_params {
  * and restart checks (64 if <= 0).  storage: element type of the iterates
  * (SIPO_F32, SIPO_BF16 with FP32 arithmetic, or SIPO_F64); residuals, gap,
  * step sizes, restart logic and the u~/v~ scalars are FP64 in every mode.
- * tile_cfg: -1 lets the library choose tile shapes, otherwise an index into
- * its tile table (see sipo_tile_count).  primal_weight: initial primal weight
- * omega of the preconditioned PDHG (<= 0: the library's default rule). */
+ * tile_cfg: -1 lets the library choose the backprojector's tile shape,
+ * otherwise an index into its tile table (see sipo_tile_count).
+ * primal_weight: initial primal weight omega of the preconditioned PDHG (<= 0:
+ * the library's default rule). */
 typedef struct sipo_tolerances {
   double kkt_tol;
   long long max_iter;
@@ -349,7 +350,8 @@ int sipo_solve_probe(sipo_ctx *ctx, sipo_ctx *target, long long probe_every, sip
 /* Solves n independent contexts as one batch (a parameter sweep): one CUDA
  * graph holds one check period of every context as parallel branches (each on
  * its context's stream), so small LPs share the device and the host waits
- * once per period.  Contexts that finish keep their branch but exit at once.
+ * once per period.  When contexts finish, the graph is captured again without
+ * them.
  * In a batch the iteration limit of each context is rounded up to a whole
  * number of its check periods.  Each context must appear once, all must have
  * been created on one device; contexts created on the same stream run one

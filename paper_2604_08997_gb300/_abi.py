@@ -259,7 +259,8 @@ def sipo_create(geometry: dict, f_T, case: dict, tolerances: dict, stream=None) 
     geometry: nx, ny, nz, angles (radians), n_det, vial_radius, mu, psf_sigma
     (x, y, z), psf_trunc.  f_T: float32 [ny][nx][nz] numpy array or torch
     tensor (host or CUDA).  case: kase, w1, w2, tol_lo, tol_hi, inhibit_ratio,
-    band_width.  tolerances: kkt_tol, max_iter, check_every, storage, tile_cfg.
+    band_width.  tolerances: kkt_tol, max_iter, check_every, storage, tile_cfg,
+    primal_weight.
     `stream` None: the context creates its own stream.
     """
     lib = load()

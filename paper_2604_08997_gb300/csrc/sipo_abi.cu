@@ -25,6 +25,7 @@
 #include "sipo_kernels.cuh"
 #include "sipo_launch.h"
 #include "sipo_ops.cuh"
+#include "sipo_psf.cuh"
 #include "sipo_response.cuh"
 
 namespace sipo {
@@ -769,6 +770,28 @@ struct Solver final : SolverBase {
     const C* tp[3];
     for (int a = 0; a < 3; ++a) tp[a] = (deriv == a) ? dtaps[a] : taps[a];
     // an axis without blur runs the single tap 1 (R = 0): a copy
+    if constexpr (sizeof(C) == 4) {
+      // single precision, nz % 4 == 0: x and y in one pass through shared
+      // memory, then z from shared-memory chunks
+      const size_t smem = conv_xy_smem(R[0], R[1]);
+      if (nz % 4 == 0 && smem <= 227 * 1024 && R[2] <= kZMaxR) {
+        const float* tpx = reinterpret_cast<const float*>(tp[0] ? tp[0] : unit_tap());
+        const float* tpy = reinterpret_cast<const float*>(tp[1] ? tp[1] : unit_tap());
+        const float* tpz = reinterpret_cast<const float*>(tp[2] ? tp[2] : unit_tap());
+        const long long tiles = (long long)((ny + kXyT - 1) / kXyT) * ((nx + kXyT - 1) / kXyT) *
+                                ((nz / 4 + kXyZG - 1) / kXyZG);
+        const long long per_sm = std::max<long long>(1, std::min<long long>(8, (227LL * 1024) / (long long)smem));
+        const int gxy = int(std::max<long long>(1, std::min<long long>(tiles, device_sms() * per_sm)));
+        launch_conv_xy_fused<TI, C>(in, reinterpret_cast<float*>(tmp_a), tpx, R[0], tpy, R[1], nx, ny, nz, gxy, smem,
+                                    s);
+        const long long items = (long long)nx * ny * ((nz + kZChunk - 1) / kZChunk);
+        const int gz = int(std::max<long long>(1, std::min<long long>((items + kWarps - 1) / kWarps,
+                                                                      (long long)device_sms() * 8)));
+        launch_conv_z_chunk<C, TO>(reinterpret_cast<const float*>(tmp_a), out, tpz, R[2], nx, ny, nz, gz, s);
+        count(2);
+        return;
+      }
+    }
     conv_pass<TI, C>(in, tmp_a, tp[0] ? tp[0] : unit_tap(), R[0], 0, s);
     conv_pass<C, C>(tmp_a, tmp_b, tp[1] ? tp[1] : unit_tap(), R[1], 1, s);
     conv_pass<C, TO>(tmp_b, out, tp[2] ? tp[2] : unit_tap(), R[2], 2, s);

@@ -138,6 +138,34 @@ def test_psf_and_sigma_derivative(sipo, axis):
     assert _rel(out.cpu().numpy(), ref) <= FP64_TOL
 
 
+PSF_F32 = [
+    (21, 26, 24, 31, 37, 10.5, 0.02, (1.0, 0.7, 1.3)),    # z groups ragged in the 16-value tile
+    (37, 29, 132, 5, 41, 0.0, 0.0, (1.5, 1.5, 2.5)),      # radii 6, 6, 10; two z chunks, the last ragged
+    (20, 18, 256, 5, 23, 0.0, 0.0, (2.0, 0.0, 3.0)),      # radii 8, 0, 12
+    (19, 23, 13, 5, 25, 0.0, 0.0, (1.2, 0.9, 0.8)),       # nz % 4 != 0: the three-pass kernels
+]
+
+
+@pytest.mark.parametrize("case", PSF_F32)
+@pytest.mark.parametrize("axis", [-1, 0, 1, 2])
+def test_psf_fp32_matches_the_oracle(sipo, case, axis):
+    """Single-precision K (and its sigma derivative along one axis): the fused
+    x-y pass through shared memory and the chunked z pass (nz % 4 == 0), or
+    the three per-axis passes, against the oracle's direct convolution.  Three
+    FP32 passes of <= 25 taps each, taps rounded to FP32: relative L2 <= 2e-6
+    (about 3e-7 expected per pass for sums of random-sign terms)."""
+    ctx, ogeo, _ = _ctx(sipo, case, sipo.SIPO_F32)
+    if axis >= 0 and ogeo.psf_sigma[axis] == 0.0:
+        pytest.skip("no blur along this axis")
+    rng = np.random.default_rng(4)
+    vol = rng.normal(size=ogeo.vol_shape).astype(np.float32)
+    out = torch.empty(ogeo.vol_shape, dtype=torch.float32, device="cuda")
+    sipo.sipo_psf_apply(ctx, torch.tensor(vol, device="cuda"), out, axis)
+    torch.cuda.synchronize()
+    ref = apply_psf(ogeo, vol.astype(np.float64), deriv_axis=None if axis < 0 else axis)
+    assert _rel(out.cpu().numpy(), ref) <= 2e-6
+
+
 def test_full_size_sampled_outputs(sipo):
     """256^3 x 360 views (the solver's measured configuration): sampled outputs
     of the same launch configuration checked one by one against the oracle."""

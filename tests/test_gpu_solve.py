@@ -534,9 +534,9 @@ def test_bounded_wait_runs_out_and_reports_timeout(sipo):
     assert rc == SIPO_ERR_TIMEOUT and n == 128
     rc, n = sipo_wait_selftest(2_000_000, arrive=True, threads=128)
     assert rc == SIPO_OK and n == 0
-    case, extra = TINY[0]
+    case, extra = TINY[2]
     lp, ops, geo, tgt, cp = _tiny(case, extra)
-    ctx = sipo.sipo_create(geo, tgt, cp, dict(storage=sipo.SIPO_F64, kkt_tol=1e-9, max_iter=4096))
+    ctx = sipo.sipo_create(geo, tgt, cp, dict(storage=sipo.SIPO_F64, kkt_tol=1e-9, max_iter=100000))
     assert sipo.sipo_solve(ctx)["status"] == sipo.SIPO_OPTIMAL
     sipo.sipo_destroy(ctx)
 
