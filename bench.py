@@ -606,7 +606,7 @@ def main(argv=None):
     p.add_argument("--feasible-ratio", type=float, default=0.85)
     p.add_argument("--separation-iters", type=int, default=16384,
                    help="iteration cap of the separation LP that settles Case-2 feasibility")
-    p.add_argument("--probe-every", type=int, default=1024,
+    p.add_argument("--probe-every", type=int, default=128,
                    help="iterations between Farkas probes of the Case-2 LP during the separation solve")
     p.add_argument("--escalate", type=int, default=0,
                    help="also time BF16 storage for N iterations, then FP32 warm-started from it")

@@ -15,7 +15,10 @@ The workflow solves it while testing, every `probe_every` iterations, its
 current dual point as a Farkas ray of Case 2 at r (sipo_solve_probe runs the
 library's bound-based test, slice by slice where the PSF allows).  A ray is a
 certificate by itself, whatever the accuracy of the iterate that gave it, so
-the first one that passes ends the workflow with PRIMAL_INFEASIBLE.  If the
+the first one that passes ends the workflow with PRIMAL_INFEASIBLE.  Passing
+duals can come and go between restarts (on the blurred 256^3 part one passes
+at iteration 1280 and none at 2048 or 3072), so the probes are frequent: every
+128 iterations by default, each about one projection.  If the
 separation LP ends instead with u~ <= r, its primal point over r satisfies
 every Case-2 row (up to its primal residual) and starts the Case-2 solve
 (sipo_set_primal_from), as the two-stage design of Sec. 3.2 does with a
@@ -29,7 +32,7 @@ from ._abi import (SIPO_CASE1, SIPO_CASE2, SIPO_OPTIMAL, SIPO_PRIMAL_INFEASIBLE,
 
 def case2_with_separation(geometry: dict, f_T, ratio: float, band_width: int = 10,
                           tolerances: dict | None = None, separation_tolerances: dict | None = None,
-                          probe_every: int = 1024, tol_hi: float = 10.0) -> dict:
+                          probe_every: int = 128, tol_hi: float = 10.0) -> dict:
     """Case 2 at inhibition ratio `ratio`, preceded by the separation LP.
 
     Returns {"separation": result of the separation LP, "ratio_bound": its
