@@ -60,8 +60,8 @@ def sm_max_mhz(peaks: dict) -> float:
 # the code it is null until re-captured.
 KERNEL_SOURCES = ["sipo_device.cuh", "sipo_solver.cuh", "sipo_ops.cuh", "sipo_launch.h",
                   "sipo_project.cu", "sipo_backproject.cu", "sipo_bp_tma.cuh"]
-TRAFFIC = {("csg256", "f32"): {"sources_sha256_16": "220cbddc0d1b9e55",
-                               "project": 279120896, "backproject": 222888832}}
+TRAFFIC = {("csg256", "f32"): {"sources_sha256_16": "d02153ed6aab633b",
+                               "project": 279118336, "backproject": 222976640}}
 
 
 def _code_only(text: str) -> str:
