@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(kThreads) k_cert_vol(Bufs<S, C> b, long long n
   block_reduce_store<1>(red, b.part, kSlCertObj);
 }
 
-// One block: the verdict from the partials of k_cert_vol and of the
+// One block: the decision from the partials of k_cert_vol and of the
 // projector's certificate mode.
 __global__ void __launch_bounds__(kThreads) k_cert_decide(Scal* st, const double* part) {
   if (st->done) return;
@@ -600,7 +600,7 @@ __global__ void __launch_bounds__(kThreads) k_cert_vol_z(Bufs<S, C> b, long long
 }
 
 // One block: per slice obj_z (block partials of k_cert_vol_z), kappa_z (the
-// projector's maxima) and B_z; the verdict and the first slice that carries
+// projector's maxima) and B_z; the decision and the first slice that carries
 // it.  The maxima are cleared for the next check.
 __global__ void __launch_bounds__(kThreads)
 k_cert_decide_z(Scal* st, const double* __restrict__ partz, int nblocks, int nz, unsigned long long* kz,

@@ -79,7 +79,7 @@ struct Scal {
   double* trace;
   int trace_cap, trace_n;
   // bound-based infeasibility certificate: B, whether the case has one, and
-  // the verdict of the current check; cert_slices: evaluated per z-slice
+  // the decision of the current check; cert_slices: evaluated per z-slice
   // (operator without z coupling), cert_z: first slice that carried it (-1)
   double cert_B;
   int cert_on, cert;
