@@ -19,6 +19,9 @@
 // consecutive outputs (R is a template parameter, up to kZMaxR).
 #pragma once
 
+#include <algorithm>
+#include <type_traits>
+
 #include "sipo_device.cuh"
 
 namespace sipo {
@@ -42,11 +45,34 @@ __host__ __device__ constexpr size_t conv_xy_smem(int rx, int ry) {
          size_t(2 * rx + 1 + 2 * ry + 1) * sizeof(float);
 }
 
+// acc += t * v, as two packed FP32 multiply-adds (each lane rounded like fmaf)
 __device__ __forceinline__ void f4_fma(float4& acc, float t, const float4& v) {
-  acc.x = fmaf(t, v.x, acc.x);
-  acc.y = fmaf(t, v.y, acc.y);
-  acc.z = fmaf(t, v.z, acc.z);
-  acc.w = fmaf(t, v.w, acc.w);
+  const float2 tt = make_float2(t, t);
+  const float2 lo = __ffma2_rn(tt, make_float2(v.x, v.y), make_float2(acc.x, acc.y));
+  const float2 hi = __ffma2_rn(tt, make_float2(v.z, v.w), make_float2(acc.z, acc.w));
+  acc = make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
+// A run of RUN outputs of one pass with a radius fixed at compile time:
+// acc[i] = sum over m of taps[m] * src[(i + m) * stride], terms added in
+// increasing m, each staged input read once and applied to every output it
+// reaches (no register window to shift).
+template <int RUN, int R>
+__device__ __forceinline__ void conv_run(const float4* src, int stride, const float* taps, float4 (&acc)[RUN]) {
+  float t[2 * R + 1];
+#pragma unroll
+  for (int m = 0; m <= 2 * R; ++m) t[m] = taps[m];
+#pragma unroll
+  for (int i = 0; i < RUN; ++i) acc[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+  for (int p = 0; p < RUN + 2 * R; ++p) {
+    const float4 v = src[p * stride];
+#pragma unroll
+    for (int i = 0; i < RUN; ++i) {
+      const int m = p - i;
+      if (m >= 0 && m <= 2 * R) f4_fma(acc[i], t[m], v);
+    }
+  }
 }
 
 // RC >= 0: both radii are RC, fixed at compile time (tap loops unrolled, tile
@@ -101,20 +127,24 @@ k_conv_xy_fused(const TI* __restrict__ in, TO* __restrict__ out, const float* __
       const int zg = it % kXyZG, r = it / kXyZG;
       const int run = r % kRunsX, yy = r / kRunsX;
       const float4* a = A + (size_t(yy) * pa + run * kXyRunX) * kXyZG + zg;
-      float4 acc[kXyRunX], win[kXyRunX];
+      float4 acc[kXyRunX];
+      if constexpr (RC >= 0) {
+        conv_run<kXyRunX, (RC >= 0 ? RC : 0)>(a, kXyZG, tx, acc);
+      } else {
+        float4 win[kXyRunX];
 #pragma unroll
-      for (int i = 0; i < kXyRunX; ++i) {
-        acc[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        win[i] = a[i * kXyZG];
-      }
+        for (int i = 0; i < kXyRunX; ++i) {
+          acc[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          win[i] = a[i * kXyZG];
+        }
+        for (int m = 0; m <= 2 * rx; ++m) {
+          const float tp = tx[m];
 #pragma unroll
-      for (int m = 0; m <= 2 * rx; ++m) {
-        const float tp = tx[m];
+          for (int i = 0; i < kXyRunX; ++i) f4_fma(acc[i], tp, win[i]);
 #pragma unroll
-        for (int i = 0; i < kXyRunX; ++i) f4_fma(acc[i], tp, win[i]);
-#pragma unroll
-        for (int i = 0; i + 1 < kXyRunX; ++i) win[i] = win[i + 1];
-        if (m < 2 * rx) win[kXyRunX - 1] = a[(m + kXyRunX) * kXyZG];
+          for (int i = 0; i + 1 < kXyRunX; ++i) win[i] = win[i + 1];
+          if (m < 2 * rx) win[kXyRunX - 1] = a[(m + kXyRunX) * kXyZG];
+        }
       }
       float4* b = B + (size_t(yy) * kXyPitchB + run * kXyRunX) * kXyZG + zg;
 #pragma unroll
@@ -128,20 +158,24 @@ k_conv_xy_fused(const TI* __restrict__ in, TO* __restrict__ out, const float* __
       const int x = r % kXyT, run = r / kXyT;
       const float4* b = B + (size_t(run * kXyRunY) * kXyPitchB + x) * kXyZG + zg;
       constexpr int kRow = kXyPitchB * kXyZG;  // float4 between rows of B
-      float4 acc[kXyRunY], win[kXyRunY];
+      float4 acc[kXyRunY];
+      if constexpr (RC >= 0) {
+        conv_run<kXyRunY, (RC >= 0 ? RC : 0)>(b, kRow, ty, acc);
+      } else {
+        float4 win[kXyRunY];
 #pragma unroll
-      for (int i = 0; i < kXyRunY; ++i) {
-        acc[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        win[i] = b[i * kRow];
-      }
+        for (int i = 0; i < kXyRunY; ++i) {
+          acc[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          win[i] = b[i * kRow];
+        }
+        for (int m = 0; m <= 2 * ry; ++m) {
+          const float tp = ty[m];
 #pragma unroll
-      for (int m = 0; m <= 2 * ry; ++m) {
-        const float tp = ty[m];
+          for (int i = 0; i < kXyRunY; ++i) f4_fma(acc[i], tp, win[i]);
 #pragma unroll
-        for (int i = 0; i < kXyRunY; ++i) f4_fma(acc[i], tp, win[i]);
-#pragma unroll
-        for (int i = 0; i + 1 < kXyRunY; ++i) win[i] = win[i + 1];
-        if (m < 2 * ry) win[kXyRunY - 1] = b[(m + kXyRunY) * kRow];
+          for (int i = 0; i + 1 < kXyRunY; ++i) win[i] = win[i + 1];
+          if (m < 2 * ry) win[kXyRunY - 1] = b[(m + kXyRunY) * kRow];
+        }
       }
       const int gx = txi * kXyT + x, gzg = zg0 + zg;
       if (gx >= nx || gzg >= nzg) continue;
@@ -218,13 +252,14 @@ k_conv_z_chunk(const TI* __restrict__ in, TO* __restrict__ out, const float* __r
       const float4 r4 = reinterpret_cast<const float4*>(w)[lane + q];
       v[4 * q] = r4.x; v[4 * q + 1] = r4.y; v[4 * q + 2] = r4.z; v[4 * q + 3] = r4.w;
     }
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float2 a01 = make_float2(0.0f, 0.0f), a23 = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int m = 0; m <= 2 * R; ++m) {
-      const float t = tp[m];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[j] = fmaf(t, v[RP - R + j + m], acc[j]);
+      const float2 t = make_float2(tp[m], tp[m]);
+      a01 = __ffma2_rn(t, make_float2(v[RP - R + m], v[RP - R + m + 1]), a01);
+      a23 = __ffma2_rn(t, make_float2(v[RP - R + m + 2], v[RP - R + m + 3]), a23);
     }
+    const float acc[4] = {a01.x, a01.y, a23.x, a23.y};
     store_group<TO, float, 4>(out + (size_t)col * nz + zo, acc);
   }
 }
