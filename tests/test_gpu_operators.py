@@ -166,6 +166,37 @@ def test_psf_fp32_matches_the_oracle(sipo, case, axis):
     assert _rel(out.cpu().numpy(), ref) <= 2e-6
 
 
+@pytest.mark.parametrize("n,sigma", [(256, (1.5, 1.5, 2.5)), (512, (2.0, 2.0, 3.0))])
+def test_full_size_psf_sampled(sipo, n, sigma):
+    """K at the sizes of the blurred workloads (256^3 with sigma (1.5, 1.5,
+    2.5), 512^3 with (2, 2, 3)), in the launch configuration the solver uses
+    (fused x-y pass, chunked z pass): sampled outputs, grid edges and corners
+    included, against the oracle's direct box sum one by one."""
+    geo = dict(nx=n, ny=n, nz=n, angles=uniform_angles(4), n_det=n, psf_sigma=sigma)
+    tgt = np.zeros((n, n, n), np.float32)
+    tgt[n // 3: n // 2, n // 3: n // 2, n // 3: n // 2] = 1.0
+    ctx = sipo.sipo_create(geo, tgt, dict(kase=0, band_width=2),
+                           dict(storage=sipo.SIPO_F32, max_iter=0, tile_cfg=4))
+    ogeo = Geometry(n, n, n, uniform_angles(4), n, psf_sigma=sigma)
+    g = torch.Generator(device="cuda").manual_seed(8)
+    vol = torch.rand((n, n, n), device="cuda", generator=g)
+    out = torch.empty_like(vol)
+    sipo.sipo_psf_apply(ctx, vol, out, -1)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(9)
+    pts = [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n - 1, 5), (n // 2, 0, n - 1)]
+    pts += [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(20)]
+    vol_h = None
+    errs = []
+    for iy, ix, iz in pts:
+        if vol_h is None:
+            vol_h = vol.cpu().numpy()
+        ref = sample.psf_voxel(ogeo, vol_h, iy, ix, iz)
+        errs.append(abs(float(out[iy, ix, iz]) - ref) / max(abs(ref), 1e-3))
+    assert max(errs) <= 2e-6, max(errs)
+    sipo.sipo_destroy(ctx)
+
+
 def test_full_size_sampled_outputs(sipo):
     """256^3 x 360 views (the solver's measured configuration): sampled outputs
     of the same launch configuration checked one by one against the oracle."""
