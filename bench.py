@@ -323,17 +323,49 @@ def tap_counts(wl, need, act_col):
     return bp * wl.nz, fp * wl.nz
 
 
-def run_sweep(args, device):
+def deal_lps(work, world: int, rank: int) -> list[int]:
+    """Indices of the independent LPs that `rank` solves: largest estimated
+    work first, each to the rank with the least work so far (ties to the
+    lower rank); the same on every rank, every LP to exactly one rank."""
+    load = [0.0] * world
+    owner = {}
+    for i in sorted(range(len(work)), key=lambda i: (-work[i], i)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        owner[i] = r
+        load[r] += work[i]
+    return [i for i in range(len(work)) if owner[i] == rank]
+
+
+def combine_sweep(elapsed: float, statuses: dict, iters: int, dist, device=None):
+    """Whole-sweep figures from one rank's share: the slowest rank's seconds,
+    the status counts and iteration totals summed over ranks."""
+    names = ["optimal", "primal_infeasible", "dual_infeasible", "iteration_limit"]
+    if dist is None:
+        return float(elapsed), {k: v for k, v in statuses.items() if v}, int(iters)
+    import torch
+    t = torch.tensor([float(statuses.get(k, 0)) for k in names] + [float(iters)], dtype=torch.float64,
+                     device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    counts = {k: int(v) for k, v in zip(names, t[:-1].tolist()) if v}
+    return max_over_ranks(elapsed, dist, device), counts, int(t[-1].item())
+
+
+def run_sweep(args, device, dist=None, rank=0, world=1):
     """The batched sweep (32 independent LPs, 64^3-192^3, 180-720 views, Case-1
     tolerances and Case-2 ratios): one sipo_solve_batched call to relative KKT
     1e-4 (or a certificate, or the iteration cap), timed on the host around the
-    call with the device synchronised; per-LP sizes, statuses and iterations."""
+    call with the device synchronised; per-LP sizes, statuses and iterations.
+    With several ranks the LPs are dealt out whole (deal_lps) and each rank
+    solves its share as one batch; nothing is exchanged but the timing and
+    the status counts (the slowest rank's time is the sweep's)."""
     import torch
     import paper_2604_08997_gb300 as sipo
     from synthetic.targets import sweep_workloads
     sipo.build()
     storage = {"f32": sipo.SIPO_F32, "bf16": sipo.SIPO_BF16, "f64": sipo.SIPO_F64}[args.storage]
-    wls = sweep_workloads()
+    wls_all = sweep_workloads()
+    mine = deal_lps([w.n ** 3 * w.n_angles for w in wls_all], world, rank)
+    wls = [wls_all[i] for i in mine]
     t0 = time.perf_counter()
     ctxs = []
     for wl in wls:
@@ -343,11 +375,15 @@ def run_sweep(args, device):
     t_create = time.perf_counter() - t0
     n0 = sipo.sipo_kernel_launch_count()
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clocks:
+        if dist is not None:
+            dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         res = sipo.sipo_solve_batched(ctxs)
         torch.cuda.synchronize()
         elapsed = time.perf_counter() - t0
+        if dist is not None:
+            dist.barrier()
     launches = sipo.sipo_kernel_launch_count() - n0
     sequential = None
     if args.sweep_sequential:
@@ -376,19 +412,22 @@ def run_sweep(args, device):
     statuses = {}
     for p in per_lp:
         statuses[p["status"]] = statuses.get(p["status"], 0) + 1
-    total_iters = sum(p["iters"] for p in per_lp)
+    local_iters = sum(p["iters"] for p in per_lp)
+    t_max, statuses, total_iters = combine_sweep(elapsed, statuses, local_iters, dist, device)
     return {"metric": "batched sweep: seconds until every LP of the sweep has a status (KKT 1e-4, "
                       "infeasibility certificate or iteration cap)",
-            "value": elapsed, "unit": "s", "n_gpus": 1, "steps": total_iters, "warmup": 0,
-            "ms_per_step": elapsed * 1e3 / max(1, total_iters), "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-            "config": {"workload": f"sweep: {len(wls)} LPs, {min(w.n for w in wls)}^3-{max(w.n for w in wls)}^3 "
-                                   f"voxels, {min(w.n_angles for w in wls)}-{max(w.n_angles for w in wls)} "
-                                   f"views, Case 1 delta 0.02-0.20 and Case 2 r 0.60-0.90, one batch",
-                       "iteration_cap": args.kkt_iters, "storage": args.storage},
+            "value": t_max, "unit": "s", "n_gpus": world, "steps": total_iters, "warmup": 0,
+            "ms_per_step": t_max * 1e3 / max(1, total_iters), "higher_is_better": False,
+            "scaling": "strong", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+            "config": {"workload": f"sweep: {len(wls_all)} LPs, {min(w.n for w in wls_all)}^3-"
+                                   f"{max(w.n for w in wls_all)}^3 voxels, {min(w.n_angles for w in wls_all)}-"
+                                   f"{max(w.n_angles for w in wls_all)} views, Case 1 delta 0.02-0.20 and Case 2 "
+                                   f"r 0.60-0.90, one batch per GPU",
+                       "iteration_cap": args.kkt_iters, "storage": args.storage,
+                       "parallelism": f"LPs dealt out whole over {world} GPU(s)"},
             "gpu_launches": int(launches), "create_seconds": t_create, "statuses": statuses,
-            "iterations_per_second": total_iters / elapsed, "sequential": sequential, "per_lp": per_lp,
-            "clocks": clocks.summary()}
+            "iterations_per_second": total_iters / t_max, "sequential": sequential,
+            "per_lp_rank0": per_lp, "clocks": clocks.summary()}
 
 
 def run_gpu(args, dist, rank, world, device):
@@ -650,9 +689,11 @@ def main(argv=None):
     torch.cuda.set_device(device)
     dist = init_dist(world, "nccl")
     if args.workload == "sweep":
-        out = run_sweep(args, device)
+        out = run_sweep(args, device, dist, rank, world)
         if rank == 0:
             print(json.dumps(out), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
         return 0
     out, wl = run_gpu(args, dist, rank, world, device)
     if rank == 0:
