@@ -55,6 +55,7 @@ def test_reference_arm_prints_the_contract_line(capsys):
                 "cpu_baseline", "e2e"):
         assert key in d, key
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["steps"] == 2 and d["warmup"] == 3    # K timed oracle steps after W untimed ones
     assert "workload" in d["config"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
@@ -64,7 +65,7 @@ def test_reference_arm_prints_the_contract_line(capsys):
 def test_reference_arm_uses_every_host_core(capsys):
     """On a multi-slice workload the reference arm runs one spawned oracle
     process per host core (each on its own z-slices) and reports that rate
-    with the core count, plus the single-process rate."""
+    with the core count, plus the rate of one process of the pool."""
     import json
     import os
     if (os.cpu_count() or 1) < 2:
@@ -75,5 +76,6 @@ def test_reference_arm_uses_every_host_core(capsys):
     d = json.loads([l for l in capsys.readouterr().out.splitlines() if l.strip()][0])
     cb = d["cpu_baseline"]
     assert 1 < cb["cores"] <= os.cpu_count()
-    assert cb["single_thread"]["cores"] == 1 and cb["single_thread"]["value"] > 0
-    assert cb["value"] == d["value"] > cb["single_thread"]["value"]
+    one = cb["single_process_in_pool"]
+    assert one["cores"] == 1 and one["value"] > 0
+    assert cb["value"] == d["value"] > one["value"]
