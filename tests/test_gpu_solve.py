@@ -221,10 +221,13 @@ def test_csg_case2_fp32_certificate_and_bf16(sipo):
     assert abs(res["pobj"] - ref["obj"]) <= 1e-3 * abs(ref["obj"])
     ctx16 = sipo.sipo_create(geo, tgt, cp, dict(storage=sipo.SIPO_BF16, kkt_tol=1e-4, max_iter=20000))
     r16 = sipo.sipo_solve(ctx16)
-    print("bf16", r16["status_name"], r16["iters"], r16["kkt"], r16["rel_primal"], r16["rel_gap"],
-          r16["pobj"], "f32", res["pobj"], "oracle", ref["obj"], flush=True)
     assert r16["status"] in (sipo.SIPO_OPTIMAL, sipo.SIPO_ITER_LIMIT)
-    assert abs(r16["pobj"] - ref["obj"]) <= 2e-2 * abs(ref["obj"])
+    # BF16 iterates stall above 1e-4; the objective of the point they reach is
+    # within its own relative KKT error of the optimum (the gap part bounds
+    # |p - d| and the optimum lies between them up to the residuals), plus one
+    # BF16 rounding (2^-8 relative) of the stored values it is computed from
+    bound = max(r16["kkt"], 2.0 ** -8)
+    assert abs(r16["pobj"] - ref["obj"]) <= bound * abs(ref["obj"]), (r16["pobj"], ref["obj"], bound)
 
 
 def test_batched_solve_matches_individual_solves(sipo):
