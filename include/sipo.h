@@ -340,7 +340,8 @@ int sipo_farkas_from(sipo_ctx *ctx, const sipo_ctx *src, int *certified, int *sl
  * target's LP (as sipo_farkas_from does); the solve stops at the first
  * certificate, with *certified = 1 and *slice as in sipo_farkas_from, else
  * *certified = 0.  res receives ctx's result as from sipo_solve (status
- * ITER_LIMIT when a certificate ended it early).  For the separation solve of
+ * ITER_LIMIT when a certificate ended it early; the returned point, and the
+ * state sipo_get_state exports, are then the check whose dual passed).  For the separation solve of
  * Case 2: ctx holds the same part as Case 1 with tol_lo = 0 (gel dose at least
  * its target, band dose at most u~), target the Case-2 LP.  Errors: as
  * sipo_solve and sipo_farkas_from. */

@@ -60,6 +60,9 @@ struct SolverBase {
   virtual void begin_solve() = 0;
   virtual void launch_block(long long n) = 0;
   virtual void request_done() = 0;
+  // ends the current solve at its last check (status ITER_LIMIT), so that the
+  // returned point and the exported state are that check's T(z)
+  virtual void stop_at_last_check() = 0;
   virtual bool done_flag() = 0;
   virtual void finish_solve(void* y_out, int loc, sipo_result* res) = 0;
   virtual void project(const void* vol, void* sino, cudaStream_t s) = 0;
@@ -1311,6 +1314,17 @@ struct Solver final : SolverBase {
     ck(cudaGetLastError(), "launch");
   }
 
+  void stop_at_last_check() override {
+    ck(cudaMemcpyAsync(h_st, st, sizeof(Scal), cudaMemcpyDeviceToHost, stream), "read state");
+    ck(cudaStreamSynchronize(stream), "stop");
+    if (!h_st->done) {
+      h_st->done = 1;
+      h_st->status = SIPO_ITER_LIMIT;
+      ck(cudaMemcpyAsync(st, h_st, sizeof(Scal), cudaMemcpyHostToDevice, stream), "state");
+      ck(cudaStreamSynchronize(stream), "stop");
+    }
+  }
+
   void request_done() override {
     ck(cudaMemcpyAsync(h_st, st, sizeof(Scal), cudaMemcpyDeviceToHost, stream), "read state");
   }
@@ -1694,6 +1708,7 @@ static void run_solve_probe(sipo::SolverBase* s, sipo::SolverBase* target, long 
       if (target->farkas_from(*s, &sl)) {
         *certified = 1;
         *slice = sl;
+        s->stop_at_last_check();  // the returned and exported point is the certified dual's check
         break;
       }
     }

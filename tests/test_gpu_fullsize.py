@@ -53,3 +53,44 @@ def test_csg256_fp32_solve_is_an_fp64_certificate(sipo):
     assert info["pobj"] == pytest.approx(res["pobj"], rel=1e-12)
     assert info["dobj"] == pytest.approx(res["dobj"], rel=1e-4)
     assert info["rel_primal"] <= 2e-4 and info["rel_dual"] <= 2e-4 and info["rel_gap"] <= 2e-4
+
+
+def test_csg256_ratio_08_gpu_certificate_holds_in_fp64(sipo):
+    """The headline status checked on the GPU's own certificate: the
+    separation LP of the measured part (Case 1 with tol_lo = 0, tol_hi = 10)
+    is solved in FP32 with Farkas probes of Case 2 at r = 0.8 until a probe
+    passes on some slice z; the dual point that passed (the separation
+    context's exported state) is then re-tested by the oracle in FP64 on that
+    slice alone, with the slice's rows of the 3-D LP (labels of the 3-D part)
+    and the bound-based test of Sec. 2.7 - one slice that cannot be met makes
+    the whole slice-separable LP infeasible."""
+    from oracle import pdhg
+    from oracle.lp import partition
+    wl = workload("csg256")
+    n, r = wl.n, 0.8
+    geo = dict(nx=n, ny=n, nz=wl.nz, angles=wl.angles, n_det=wl.n_det, vial_radius=wl.vial_radius)
+    tgt = torch.from_numpy(wl.target).cuda()
+    sep = sipo.sipo_create(geo, tgt, dict(kase=1, tol_lo=0.0, tol_hi=10.0, band_width=wl.band_width),
+                           dict(storage=sipo.SIPO_F32, kkt_tol=1e-4, max_iter=16384))
+    c2 = sipo.sipo_create(geo, tgt, dict(kase=2, inhibit_ratio=r, band_width=wl.band_width),
+                          dict(storage=sipo.SIPO_F32, kkt_tol=1e-4, max_iter=64))
+    res, certified, z = sipo.sipo_solve_probe(sep, c2, 128)
+    assert certified and 0 <= z < wl.nz, (res["status_name"], certified, z)
+    assert res["status"] == sipo.SIPO_ITER_LIMIT
+    lu = torch.empty((n, n, wl.nz), dtype=torch.float32, device="cuda")
+    ll = torch.empty_like(lu)
+    y = torch.empty((wl.n_angles, wl.n_det, wl.nz), dtype=torch.float32, device="cuda")
+    sipo.sipo_get_state(sep, y, lu, ll)
+    # the exported point is the tested one: the library certifies it again
+    again, z2 = sipo.sipo_farkas_from(c2, sep)
+    assert again and z2 == z
+    lab3 = partition(Geometry(n, n, n, wl.angles, n, vial_radius=wl.vial_radius), wl.target, wl.band_width)
+    g2 = Geometry(n, n, 1, wl.angles, n, vial_radius=wl.vial_radius)
+    lp2, ops2 = build_lp(g2, np.ascontiguousarray(wl.target[:, :, z:z + 1]),
+                         CaseParams(case=2, inhibit_ratio=r, band_width=wl.band_width))
+    lp2.labels = lab3[:, :, z].ravel().astype(np.uint8)
+    lam_up = lu[:, :, z].double().cpu().numpy().ravel()
+    lam_lo = ll[:, :, z].double().cpu().numpy().ravel()
+    assert pdhg.certificate(lp2, ops2, lam_up, lam_lo, *pdhg.certificate_data(lp2, ops2))
+    sipo.sipo_destroy(sep)
+    sipo.sipo_destroy(c2)
