@@ -99,6 +99,43 @@ k_conv_xy_fused(const TI* __restrict__ in, TO* __restrict__ out, const float* __
     const int txi = int(t1 % ntx), tyi = int(t1 / ntx);
     const int gx0 = txi * kXyT - rx, gy0 = tyi * kXyT - ry, zg0 = tz * kXyZG;
     __syncthreads();  // the previous tile is done with A and B (and the taps are staged)
+    if constexpr (RC >= 0) {
+      // staging by rows: warp w takes rows w, w + kWarps, ...; lane l keeps z
+      // group l % 4 and columns l / 4 + 8 j, so addresses advance by fixed
+      // strides; two rows (2 JN loads per lane) in flight before any store
+      constexpr int W = kXyT + 2 * (RC >= 0 ? RC : 0);
+      constexpr int JN = (W * kXyZG + 31) / 32;
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      const int zg = lane % kXyZG, xl = lane / kXyZG;
+      const bool zok = zg0 + zg < nzg;
+      const size_t row_stride = (size_t)nx * nz;
+      for (int yy0 = warp; yy0 < W; yy0 += 2 * kWarps) {
+        float v[2][JN][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int yy = yy0 + h * kWarps;
+          const int gy = gy0 + yy;
+          const bool yok = yy < W && gy >= 0 && gy < ny && zok;
+          const TI* prow = in + (size_t)(yok ? gy : 0) * row_stride + 4 * (zg0 + zg);
+#pragma unroll
+          for (int j = 0; j < JN; ++j) {
+            const int xx = xl + 8 * j, gx = gx0 + xx;
+            v[h][j][0] = v[h][j][1] = v[h][j][2] = v[h][j][3] = 0.0f;
+            if (yok && xx < W && gx >= 0 && gx < nx) load_group<TI, float, 4>(prow + (size_t)gx * nz, v[h][j]);
+          }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int yy = yy0 + h * kWarps;
+          if (yy >= W) break;
+#pragma unroll
+          for (int j = 0; j < JN; ++j) {
+            const int xx = xl + 8 * j;
+            if (xx < W) A[(yy * pa + xx) * kXyZG + zg] = make_float4(v[h][j][0], v[h][j][1], v[h][j][2], v[h][j][3]);
+          }
+        }
+      }
+    } else {
     // staging: kXyLoads loads per thread in flight before any is stored
     const int na = wy * wx * kXyZG;
     for (int e0 = 0; e0 < na; e0 += kXyLoads * kThreads) {
@@ -119,6 +156,7 @@ k_conv_xy_fused(const TI* __restrict__ in, TO* __restrict__ out, const float* __
         const int zg = e % kXyZG, r = e / kXyZG;
         A[(size_t(r / wx) * pa + r % wx) * kXyZG + zg] = make_float4(v[i][0], v[i][1], v[i][2], v[i][3]);
       }
+    }
     }
     __syncthreads();
     // x pass over every staged row: item = (row, run, z group)
@@ -236,11 +274,21 @@ k_conv_z_chunk(const TI* __restrict__ in, TO* __restrict__ out, const float* __r
     const int z0 = int(it % nch) * kZChunk;
     const TI* p = in + (size_t)col * nz;
     __syncwarp();  // the warp's previous item is done with w
-    for (int g = lane; g < SPAN / 4; g += 32) {
-      const int z = z0 - RP + 4 * g;
-      float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      if (z >= 0 && z < nz) load_group<TI, float, 4>(p + z, v);  // nz % 4 == 0: whole group in or out
-      reinterpret_cast<float4*>(w)[g] = make_float4(v[0], v[1], v[2], v[3]);
+    // the staged groups (at most 64 for R <= kZMaxR): both of a lane's loads
+    // in flight before either is stored
+    static_assert(SPAN / 4 <= 64, "two staged groups per lane");
+    float st[2][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int g = lane + 32 * h, z = z0 - RP + 4 * g;
+      st[h][0] = st[h][1] = st[h][2] = st[h][3] = 0.0f;
+      // nz % 4 == 0: a group is wholly inside the column or wholly outside
+      if (g < SPAN / 4 && z >= 0 && z < nz) load_group<TI, float, 4>(p + z, st[h]);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int g = lane + 32 * h;
+      if (g < SPAN / 4) reinterpret_cast<float4*>(w)[g] = make_float4(st[h][0], st[h][1], st[h][2], st[h][3]);
     }
     __syncwarp();
     const int zo = z0 + 4 * lane;
