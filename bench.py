@@ -590,7 +590,8 @@ def run_gpu(args, dist, rank, world, device):
                 # the separation LP runs in FP32 storage (BF16 iterates stall
                 # above the accuracy its certificate needs)
                 tol_s = dict(tol, kkt_tol=1e-4, max_iter=args.separation_iters,
-                             storage=sipo.SIPO_F64 if tol["storage"] == sipo.SIPO_F64 else sipo.SIPO_F32)
+                             storage=sipo.SIPO_F64 if tol["storage"] == sipo.SIPO_F64 else sipo.SIPO_F32,
+                             primal_weight=args.separation_omega)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 ws = sipo.case2_with_separation(geo, tgt, cpk["inhibit_ratio"], band_width=cpk["band_width"],
@@ -683,6 +684,8 @@ def main(argv=None):
     p.add_argument("--profile-iters", type=int, default=8)
     p.add_argument("--kkt-iters", type=int, default=2048)
     p.add_argument("--feasible-ratio", type=float, default=0.85)
+    p.add_argument("--separation-omega", type=float, default=0.0,
+                   help="initial primal weight of the separation LP (0: the library's rule)")
     p.add_argument("--separation-iters", type=int, default=16384,
                    help="iteration cap of the separation LP that settles Case-2 feasibility")
     p.add_argument("--probe-every", type=int, default=128,
