@@ -197,16 +197,18 @@ def test_full_size_psf_sampled(sipo, n, sigma):
     sipo.sipo_destroy(ctx)
 
 
-def test_full_size_sampled_outputs(sipo):
-    """256^3 x 360 views (the solver's measured configuration): sampled outputs
-    of the same launch configuration checked one by one against the oracle."""
-    n, na = 256, 360
+@pytest.mark.parametrize("n,na,vial,mu", [(256, 360, 120.0, 0.005), (512, 720, 240.0, 0.0025)])
+def test_full_size_sampled_outputs(sipo, n, na, vial, mu):
+    """256^3 x 360 views (the solver's measured configuration, with
+    attenuation) and 512^3 x 720 views (the large part's geometry): sampled
+    outputs of the same launch configuration checked one by one against the
+    oracle, and the adjointness of the whole launch."""
     ang = uniform_angles(na)
-    geo = dict(nx=n, ny=n, nz=n, angles=ang, n_det=n, vial_radius=120.0, mu=0.005)
-    tgt = csg_3d(n, vial_radius=120.0, band_width=10, seed=2)
+    geo = dict(nx=n, ny=n, nz=n, angles=ang, n_det=n, vial_radius=vial, mu=mu)
+    tgt = csg_3d(n, vial_radius=vial, band_width=10, seed=2)
     ctx = sipo.sipo_create(geo, tgt, dict(kase=2, band_width=10, inhibit_ratio=0.8),
                            dict(storage=sipo.SIPO_F32, max_iter=0))
-    ogeo = Geometry(n, n, n, ang, n, vial_radius=120.0, mu=0.005)
+    ogeo = Geometry(n, n, n, ang, n, vial_radius=vial, mu=mu)
     g = torch.Generator(device="cuda").manual_seed(5)
     vol = torch.rand((n, n, n), device="cuda", generator=g)
     sino = torch.rand((na, n, n), device="cuda", generator=g)
@@ -231,6 +233,7 @@ def test_full_size_sampled_outputs(sipo):
     lhs = float(torch.sum(out_s.double() * sino.double()))
     rhs = float(torch.sum(out_v.double() * vol.double()))
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+    sipo.sipo_destroy(ctx)
 
 
 def test_autograd_gradcheck_and_sigma_fd(sipo):
