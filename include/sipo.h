@@ -159,7 +159,9 @@ typedef struct sipo_result {
  * lives on the device current at creation; every later call on it must be
  * made with that device current.  On success *out owns all internal device
  * memory until sipo_destroy.  Errors:
- * INVALID_ARG (sizes, NaN/negative target, empty gel, mu > 0 without vial),
+ * INVALID_ARG (sizes, NaN/negative target, empty gel, mu > 0 without vial, an
+ * empty band in Case 1 or the general form: the band maximum u~ is then in no
+ * row and the LP is unbounded),
  * OOM, CUDA. */
 int sipo_create(const sipo_geometry *geo, const float *f_T, int f_T_location,
                 const sipo_case_params *cp, const sipo_tolerances *tol,

@@ -179,6 +179,10 @@ def build_lp(geo: Geometry, f_T: np.ndarray, cp: CaseParams,
     act = active_rays(ops, f_T)
     lp = LPData(cp.case, lab.astype(np.uint8), ft, lower, upper, act,
                 float(f_crit), fT, c_u, c_v)
+    if lp.has_u and c_u != 0.0 and not lp.band.any():
+        # u~ is the band maximum (Eqs. 20, 33): with no band row it is bound by
+        # nothing and the LP (free u~, Eqs. 9-24) is unbounded
+        raise ValueError("empty band: the band maximum u~ is in no row")
     return lp, ops
 
 

@@ -1055,6 +1055,10 @@ struct Solver final : SolverBase {
     fu_sum = fu ? sums[7] : 0.0;
     n_band = (long long)sums[0];
     n_gel = (long long)sums[1];
+    if (has_u && c_u != 0.0 && n_band == 0)
+      fail(SIPO_ERR_INVALID_ARG,
+           "empty band: the band maximum u~ is in no row (band_width 0 without a PSF in Case 1 or the general "
+           "form); the LP is unbounded");
     col_u = has_u ? sums[0] : 0.0;
     col_v = has_v ? sums[2] : 0.0;
     h_norm = std::sqrt(sums[0] * band_rhs * band_rhs + (cp.kase == SIPO_CASE1 ? sums[4] : 0.0) + sums[3]);

@@ -544,6 +544,29 @@ def test_bounded_wait_runs_out_and_reports_timeout(sipo):
     sipo.sipo_destroy(ctx)
 
 
+def test_empty_band(sipo):
+    """band_width 0 without a PSF leaves the band empty: Case 1 and the general
+    form (u~ in no row, unbounded LP) are refused at creation with INVALID_ARG
+    before any solve; Case 2 solves to the dense simplex's optimum."""
+    for case, extra in TINY[:2]:
+        lp_geo = _tiny(case, extra)
+        geo, tgt = lp_geo[2], lp_geo[3]
+        with pytest.raises(sipo.SipoError) as e:
+            sipo.sipo_create(geo, tgt, dict(kase=case, band_width=0, **extra),
+                             dict(storage=sipo.SIPO_F64, kkt_tol=1e-9, max_iter=1000))
+        assert e.value.code == -1 and "empty band" in str(e.value)
+    lp, ops, geo, tgt, cp = _tiny(2, dict(inhibit_ratio=0.6))
+    lp0, ops0 = build_lp(Geometry(10, 10, 1, geo["angles"], 15), tgt,
+                         CaseParams(case=2, band_width=0, inhibit_ratio=0.6))
+    st, obj, _ = simplex.solve_dense(lp0, ops0)
+    ctx = sipo.sipo_create(geo, tgt, dict(kase=2, band_width=0, inhibit_ratio=0.6),
+                           dict(storage=sipo.SIPO_F64, kkt_tol=1e-9, max_iter=100000))
+    res = sipo.sipo_solve(ctx)
+    assert st == "optimal" and res["status"] == sipo.SIPO_OPTIMAL
+    assert abs(res["pobj"] - obj) <= 1e-7 * abs(obj)
+    sipo.sipo_destroy(ctx)
+
+
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
 def test_backprojector_tiles_give_identical_solves(sipo, storage):
     """The fused dual step with every backprojector tile entry: the row-pattern

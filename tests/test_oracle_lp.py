@@ -697,3 +697,27 @@ def test_separation_lp_settles_case2_feasibility():
                 y = res["y"] / r
                 d = ops2.AT(y.reshape(ops2.geo.sino_shape)).ravel()
                 assert np.all(d[lp2.band] <= 1.0 + 1e-5) and np.all(d[lp2.gel] >= lp2.lower[lp2.gel] * (1 - 1e-5))
+
+
+def test_empty_band_reading():
+    """band_width 0 without a PSF: the band of Sec. 2.2 (supp(K f_T) minus the
+    gel, K = I) is empty.  With u~ free (Eqs. 9-24) and in no row, Case 1 and
+    the general form are unbounded - the dense simplex says so - and the
+    oracle refuses to build them; Case 2 has no u~ and stays a proper LP, its
+    PDHG optimum equal to the simplex's."""
+    tgt = discs_2d(10, n_discs=1, r_range=(2.0, 3.0), container_radius=4.0, seed=3)
+    geo = Geometry(10, 10, 1, uniform_angles(8), 15)
+    for case, extra in ((GENERAL, {}), (CASE1, dict(tol_lo=0.1, tol_hi=0.1))):
+        with pytest.raises(ValueError, match="empty band"):
+            build_lp(geo, tgt, CaseParams(case=case, band_width=0, **extra))
+    # the same LP written out without the refusal: unbounded for the simplex
+    lp, ops = build_lp(geo, tgt, CaseParams(case=CASE1, tol_lo=0.1, tol_hi=0.1, band_width=1))
+    lp.labels = np.where(lp.labels == BAND, EXT, lp.labels).astype(np.uint8)   # band rows removed
+    assert not lp.band.any()
+    assert simplex.solve_dense(lp, ops)[0] == "unbounded"
+    lp2, ops2 = build_lp(geo, tgt, CaseParams(case=CASE2, inhibit_ratio=0.6, band_width=0))
+    assert not lp2.band.any()
+    st, obj, _ = simplex.solve_dense(lp2, ops2)
+    res = pdhg.solve(lp2, ops2, kkt_tol=1e-9, max_iter=100000)
+    assert st == "optimal" and res["status"] == pdhg.OPTIMAL
+    assert abs(res["obj"] - obj) <= 1e-7 * abs(obj)
