@@ -1636,11 +1636,14 @@ static void create_impl(const sipo_geometry* geo, const float* f_T, const float*
   for (int a = 0; a < 3; ++a)
     if (!(geo->psf_sigma[a] >= 0) || geo->psf_sigma[a] > 64) sipo::fail(SIPO_ERR_INVALID_ARG, "psf sigma out of range");
   if (cp->kase < SIPO_GENERAL || cp->kase > SIPO_CASE2) sipo::fail(SIPO_ERR_INVALID_ARG, "unknown LP case");
-  if (cp->kase == SIPO_GENERAL && (!(cp->w1 >= 0) || !(cp->w2 >= 0)))
-    sipo::fail(SIPO_ERR_INVALID_ARG, "weights must be >= 0");
-  if (cp->kase == SIPO_CASE1 && (!(cp->tol_lo >= 0 && cp->tol_lo < 1) || !(cp->tol_hi >= 0)))
-    sipo::fail(SIPO_ERR_INVALID_ARG, "Case 1 tolerances must satisfy 0 <= tol_lo < 1, tol_hi >= 0");
-  if (cp->kase == SIPO_CASE2 && !(cp->inhibit_ratio > 0)) sipo::fail(SIPO_ERR_INVALID_ARG, "inhibit_ratio must be > 0");
+  if (cp->kase == SIPO_GENERAL && (!(cp->w1 >= 0) || !(cp->w2 >= 0) || !std::isfinite(cp->w1) ||
+                                   !std::isfinite(cp->w2)))
+    sipo::fail(SIPO_ERR_INVALID_ARG, "weights must be finite and >= 0");
+  if (cp->kase == SIPO_CASE1 && (!(cp->tol_lo >= 0 && cp->tol_lo < 1) || !(cp->tol_hi >= 0) ||
+                                 !std::isfinite(cp->tol_hi)))
+    sipo::fail(SIPO_ERR_INVALID_ARG, "Case 1 tolerances must satisfy 0 <= tol_lo < 1, 0 <= tol_hi < inf");
+  if (cp->kase == SIPO_CASE2 && !(cp->inhibit_ratio > 0 && std::isfinite(cp->inhibit_ratio)))
+    sipo::fail(SIPO_ERR_INVALID_ARG, "inhibit_ratio must be finite and > 0");
   if (cp->band_width > 1000) sipo::fail(SIPO_ERR_INVALID_ARG, "band_width too large");
   if (tol->storage != SIPO_F32 && tol->storage != SIPO_F64 && tol->storage != SIPO_BF16)
     sipo::fail(SIPO_ERR_INVALID_ARG, "unknown storage type");

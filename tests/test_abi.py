@@ -65,6 +65,20 @@ def test_invalid_arguments_fail_before_device_work(lib):
     rc = lib.sipo_create(ctypes.byref(g), ctypes.c_void_p(tgt.ctypes.data), 0, ctypes.byref(cp),
                          ctypes.byref(tl), None, ctypes.byref(out))
     assert rc == -1
+    # non-finite or out-of-range case parameters
+    inf, nan = float("inf"), float("nan")
+    for kase, w1, w2, lo, hi, r in ((0, inf, 1.0, 0.05, 0.05, 0.8), (0, 1.0, nan, 0.05, 0.05, 0.8),
+                                    (1, 1.0, 1.0, 0.05, inf, 0.8), (1, 1.0, 1.0, 1.0, 0.05, 0.8),
+                                    (2, 1.0, 1.0, 0.05, 0.05, inf), (2, 1.0, 1.0, 0.05, 0.05, 0.0)):
+        bad = _abi.sipo_case_params(kase, w1, w2, lo, hi, r, 2)
+        rc = lib.sipo_create(ctypes.byref(g), ctypes.c_void_p(tgt.ctypes.data), 0, ctypes.byref(bad),
+                             ctypes.byref(tl), None, ctypes.byref(out))
+        assert rc == -1, (kase, w1, w2, lo, hi, r)
+    # the problem-size limit (2^34 voxels) is checked before any allocation
+    g.nx, g.ny, g.nz = 1 << 12, 1 << 12, 1 << 11
+    rc = lib.sipo_create(ctypes.byref(g), ctypes.c_void_p(tgt.ctypes.data), 0, ctypes.byref(cp),
+                         ctypes.byref(tl), None, ctypes.byref(out))
+    assert rc == -1 and b"too large" in lib.sipo_last_error()
     assert lib.sipo_destroy(None) == 0
     assert lib.sipo_phase_count() >= 3
     assert lib.sipo_phase_name(0) == b"scalar_step"
