@@ -43,6 +43,10 @@ CASES = [
     (11, 9, 256, 7, 15, 4.0, 0.05, (0.0, 0.0, 0.0)),
     # one group per lane with a partly idle last warp (132 = 128 + 4)
     (10, 12, 132, 9, 17, 0.0, 0.0, (0.0, 0.0, 0.0)),
+    # degenerate sizes: one view and one detector bin; two views, three bins, a PSF
+    # wider than the grid along x
+    (9, 7, 5, 1, 1, 0.0, 0.0, (0.0, 0.0, 0.0)),
+    (6, 5, 8, 2, 3, 2.5, 0.1, (0.6, 0.0, 0.0)),
 ]
 
 
