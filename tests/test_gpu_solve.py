@@ -544,6 +544,40 @@ def test_bounded_wait_runs_out_and_reports_timeout(sipo):
     sipo.sipo_destroy(ctx)
 
 
+@pytest.mark.parametrize("case,extra", TINY)
+def test_scale_invariance_and_single_voxel_gel(sipo, case, extra):
+    """Scale invariance on the device (Secs. 2.5-2.6): the target times 2^10
+    normalises to the same f~ bit for bit, so the solve is identical (status,
+    iterations, objective, returned y) and only the dose-domain factor alpha*
+    scales by 2^10.  A gel of one voxel (the smallest part) solves to the
+    dense simplex's optimum."""
+    lp, ops, geo, tgt, cp = _tiny(case, extra)
+    tol = dict(storage=sipo.SIPO_F64, kkt_tol=1e-9, max_iter=100000)
+    outs = []
+    for scale in (1.0, 1024.0):
+        ctx = sipo.sipo_create(geo, (tgt * scale).astype(np.float32), cp, tol)
+        y = np.empty(lp.active.shape, np.float64)
+        res = sipo.sipo_solve(ctx, y)
+        outs.append((res, y))
+        sipo.sipo_destroy(ctx)
+    (r1, y1), (r2, y2) = outs
+    assert (r1["status"], r1["iters"], r1["pobj"], r1["kkt"]) == (r2["status"], r2["iters"], r2["pobj"], r2["kkt"])
+    np.testing.assert_array_equal(y1, y2)
+    assert r2["alpha"] == pytest.approx(1024.0 * r1["alpha"], rel=1e-12)
+    one = np.zeros_like(tgt)
+    one[5, 5, 0] = 1.0
+    lp1, ops1 = build_lp(Geometry(10, 10, 1, geo["angles"], 15), one,
+                         CaseParams(case=case, band_width=2, **extra))
+    st, obj, _ = simplex.solve_dense(lp1, ops1)
+    ctx = sipo.sipo_create(geo, one, cp, tol)
+    res = sipo.sipo_solve(ctx)
+    sipo.sipo_destroy(ctx)
+    if st == "optimal":
+        assert res["status"] == sipo.SIPO_OPTIMAL and abs(res["pobj"] - obj) <= 1e-7 * abs(obj)
+    else:
+        assert res["status"] == sipo.SIPO_PRIMAL_INFEASIBLE, (st, res["status_name"])
+
+
 def test_empty_band(sipo):
     """band_width 0 without a PSF leaves the band empty: Case 1 and the general
     form (u~ in no row, unbounded LP) are refused at creation with INVALID_ARG
