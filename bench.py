@@ -581,11 +581,18 @@ def run_gpu(args, dist, rank, world, device):
             if ctx_k is not ctx:
                 sipo.sipo_destroy(ctx_k)
         if wl.case == 2:
-            # Case 2 with its feasibility settled first: the separation LP
-            # (Case 1 of the part, tol_lo = 0) gives the best band-to-gel
-            # ratio; its dual is probed as a Farkas ray of Case 2 during the
-            # solve, and a converged point below the ratio starts Case 2
-            for label, cpk in [("requested", cp)]:
+            # Case 2 with its feasibility settled: the separation LP (Case 1
+            # of the part, tol_lo = 0) gives the best band-to-gel ratio and
+            # its dual is probed as a Farkas ray of Case 2 during the solve;
+            # the concurrent form solves Case 2 beside it on its own stream,
+            # the sequential one starts Case 2 after it
+            sep_runs = [("requested", cp, True)]
+            if args.feasible_ratio > 0:
+                sep_runs.append(("separation_feasible_ratio_%.2f" % args.feasible_ratio,
+                                 dict(cp, inhibit_ratio=args.feasible_ratio), True))
+            if args.separation_sequential:
+                sep_runs += [(lab + "_sequential", c, False) for lab, c, _ in list(sep_runs)]
+            for label, cpk, race in sep_runs:
                 tol_k = dict(tol, kkt_tol=1e-4, max_iter=args.kkt_iters)
                 # the separation LP runs in FP32 storage (BF16 iterates stall
                 # above the accuracy its certificate needs)
@@ -596,7 +603,7 @@ def run_gpu(args, dist, rank, world, device):
                 t0 = time.perf_counter()
                 ws = sipo.case2_with_separation(geo, tgt, cpk["inhibit_ratio"], band_width=cpk["band_width"],
                                                 tolerances=tol_k, separation_tolerances=tol_s,
-                                                probe_every=args.probe_every)
+                                                probe_every=args.probe_every, race=race)
                 torch.cuda.synchronize()
                 tk = time.perf_counter() - t0
                 sep, c2 = ws["separation"], ws["case2"]
@@ -607,11 +614,14 @@ def run_gpu(args, dist, rank, world, device):
                     "certified": ws["certified"], "cert_slice": ws["cert_slice"],
                     "ratio_bound": ws["ratio_bound"], "separation_status": sep["status_name"],
                     "separation_iters": sep["iters"], "separation_kkt": sep["kkt"],
-                    "separation_dobj": sep["dobj"],
+                    "separation_dobj": sep["dobj"], "form": "concurrent" if race else "sequential",
                     "case2_iters": c2["iters"] if c2 else 0, "case2_kkt": c2["kkt"] if c2 else None,
                     "objective": c2["pobj"] if c2 else None,
                     "separation_form": "Case 1 with tol_lo = 0, tol_hi = 10 (minimum band dose over gel dose >= target)",
-                    "includes": "context creation of both LPs, separation solve with Farkas probes, Case-2 solve"}
+                    "includes": ("context creation of the separation LP and two Case-2 contexts (probe target, "
+                                 "solve), separation solve with Farkas probes and Case-2 solve on two streams at "
+                                 "once" if race else
+                                 "context creation of both LPs, separation solve with Farkas probes, Case-2 solve")}
         if args.escalate > 0:
             # precision escalation: BF16 storage for at most N iterations, then
             # FP32 warm-started from its last check (both contexts created first)
@@ -690,6 +700,8 @@ def main(argv=None):
                    help="iteration cap of the separation LP that settles Case-2 feasibility")
     p.add_argument("--probe-every", type=int, default=128,
                    help="iterations between Farkas probes of the Case-2 LP during the separation solve")
+    p.add_argument("--separation-sequential", action="store_true",
+                   help="also time the sequential form of the separation workflow (separation LP first)")
     p.add_argument("--escalate", type=int, default=0,
                    help="also time BF16 storage for N iterations, then FP32 warm-started from it")
     p.add_argument("--sweep-sequential", action="store_true",

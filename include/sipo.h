@@ -350,6 +350,25 @@ int sipo_farkas_from(sipo_ctx *ctx, const sipo_ctx *src, int *certified, int *sl
 int sipo_solve_probe(sipo_ctx *ctx, sipo_ctx *target, long long probe_every, sipo_result *res, int *certified,
                      int *slice);
 
+/* sipo_solve_probe of ctx (Farkas probes of target) while a third context,
+ * rival, is solved at the same time on its own stream: each round launches
+ * one check period of every context still running (ctx and rival overlap on
+ * the device), then reads both states.  A context stops running at its own
+ * decision or its iteration cap while the other goes on.  The call ends at
+ * the first probe certificate (*certified = 1, *slice as in sipo_farkas_from;
+ * rival stopped at its last check), at the rival's own decision (optimal,
+ * infeasible by its own certificate, or non-finite; ctx stopped at its last
+ * check), or when both have stopped.  res and rival_res receive the two
+ * results as from sipo_solve (ITER_LIMIT for a solve the other one ended).
+ * For Case 2 with its feasibility settled (Secs. 2.7.1-2.7.2): ctx holds the
+ * separation LP, target and rival the Case-2 LP at ratio r (two contexts: a
+ * probe resets target's solver state); a feasible r ends with the rival's
+ * optimum, an infeasible one with the separation dual's certificate.  The
+ * three contexts must be distinct, ctx and rival on one device.  Errors: as
+ * sipo_solve and sipo_farkas_from. */
+int sipo_solve_race(sipo_ctx *ctx, sipo_ctx *target, sipo_ctx *rival, long long probe_every, sipo_result *res,
+                    sipo_result *rival_res, int *certified, int *slice);
+
 /* Solves n independent contexts as one batch (a parameter sweep): one CUDA
  * graph holds one check period of every context as parallel branches (each on
  * its context's stream), so small LPs share the device and the host waits

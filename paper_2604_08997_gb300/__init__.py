@@ -10,7 +10,7 @@ from ._abi import (SIPO_BF16, SIPO_CASE1, SIPO_CASE2, SIPO_F32, SIPO_F64, SIPO_G
                    load, sipo_backproject, sipo_create, sipo_destroy, sipo_get_array,
                    sipo_kernel_launch_count, sipo_tile_count, sipo_profile, sipo_project, sipo_psf_apply,
                    sipo_psf_grad, sipo_set_psf_sigma, sipo_set_tolerances, sipo_get_trace, sipo_solve,
-                   sipo_set_primal, sipo_set_primal_from, sipo_farkas_from, sipo_solve_probe, sipo_solve_batched, sipo_warm_start,
+                   sipo_set_primal, sipo_set_primal_from, sipo_farkas_from, sipo_solve_probe, sipo_solve_race, sipo_solve_batched, sipo_warm_start,
                    sipo_create_bounded, sipo_response_map, sipo_response_metrics,
                    sipo_get_state, sipo_set_state)
 from .build import build
@@ -21,7 +21,7 @@ from .response import (Richards, dose_to_response, response_case1, response_case
 
 __all__ = [
     "build", "load", "Context", "SipoError", "sipo_create", "sipo_solve", "sipo_solve_batched",
-    "sipo_warm_start", "sipo_set_primal", "sipo_set_primal_from", "sipo_farkas_from", "sipo_solve_probe", "sipo_get_state", "sipo_set_state", "two_stage_solve", "case2_with_separation",
+    "sipo_warm_start", "sipo_set_primal", "sipo_set_primal_from", "sipo_farkas_from", "sipo_solve_probe", "sipo_solve_race", "sipo_get_state", "sipo_set_state", "two_stage_solve", "case2_with_separation",
     "sipo_create_bounded",
     "sipo_response_map", "sipo_response_metrics", "Richards", "response_to_dose", "dose_to_response",
     "response_case1", "response_case2", "response_general", "response_metrics",

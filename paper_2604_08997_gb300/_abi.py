@@ -103,6 +103,8 @@ SIGNATURES = {
     "sipo_set_primal_from": (c_int, [c_void_p, c_void_p, c_double, c_double, c_double]),
     "sipo_farkas_from": (c_int, [c_void_p, c_void_p, POINTER(c_int), POINTER(c_int)]),
     "sipo_solve_probe": (c_int, [c_void_p, c_void_p, c_longlong, c_void_p, POINTER(c_int), POINTER(c_int)]),
+    "sipo_solve_race": (c_int, [c_void_p, c_void_p, c_void_p, c_longlong, c_void_p, c_void_p, POINTER(c_int),
+                                POINTER(c_int)]),
     "sipo_get_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, POINTER(c_double)]),
     "sipo_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, POINTER(c_double)]),
     "sipo_project": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
@@ -392,6 +394,18 @@ def sipo_solve_probe(ctx: Context, target: Context, probe_every: int = 1024) -> 
     _check(load().sipo_solve_probe(ctx.handle, target.handle, int(probe_every), ctypes.byref(res),
                                    ctypes.byref(cert), ctypes.byref(sl)))
     return res.as_dict(), bool(cert.value), int(sl.value)
+
+
+def sipo_solve_race(ctx: Context, target: Context, rival: Context, probe_every: int = 1024
+                    ) -> tuple[dict, dict, bool, int]:
+    """sipo_solve_probe of ctx (Farkas probes of target) with rival solved at
+    the same time on its own stream; returns (ctx's result, rival's result,
+    certified, slice or -1)."""
+    res, rres = sipo_result(), sipo_result()
+    cert, sl = c_int(0), c_int(-1)
+    _check(load().sipo_solve_race(ctx.handle, target.handle, rival.handle, int(probe_every), ctypes.byref(res),
+                                  ctypes.byref(rres), ctypes.byref(cert), ctypes.byref(sl)))
+    return res.as_dict(), rres.as_dict(), bool(cert.value), int(sl.value)
 
 
 def sipo_get_state(ctx: Context, y, lam_up, lam_lo) -> dict:

@@ -1735,6 +1735,73 @@ int sipo_solve_probe(sipo_ctx* ctx, sipo_ctx* target, long long probe_every, sip
   SIPO_CATCH
 }
 
+// run_solve_probe of s with a second solve, `rival`, advanced on its own
+// stream at the same time: each round launches one check period of every
+// context still running, then reads both states.  A context stops running at
+// its own decision (done flag) or iteration cap; the call ends at the first
+// probe certificate (rival stopped at its last check), at the rival's own
+// decision (s stopped at its last check), or when neither runs any more.
+static void run_solve_race(sipo::SolverBase* s, sipo::SolverBase* target, sipo::SolverBase* rival,
+                           long long probe_every, int* certified, int* slice) {
+  s->begin_solve();
+  rival->begin_solve();
+  const long long Ps = s->period(), Ms = s->max_iter();
+  const long long Pr = rival->period(), Mr = rival->max_iter();
+  long long ks = 0, kr = 0, next_probe = probe_every;
+  bool run_s = ks < Ms, run_r = kr < Mr;
+  *certified = 0;
+  *slice = -1;
+  while (run_s || run_r) {
+    long long ns = 0, nr = 0;
+    if (run_s) { ns = std::min(Ps, Ms - ks); s->launch_block(ns); }
+    if (run_r) { nr = std::min(Pr, Mr - kr); rival->launch_block(nr); }
+    if (run_s) s->request_done();
+    if (run_r) rival->request_done();
+    ks += ns;
+    kr += nr;
+    if (run_r) {
+      if (rival->done_flag()) {
+        // the rival decided its LP: the separation solve is not needed further
+        if (run_s) s->stop_at_last_check();
+        break;
+      }
+      run_r = kr < Mr;
+    }
+    if (run_s) {
+      const bool done = s->done_flag();
+      if (ks >= next_probe || done || ks >= Ms) {
+        next_probe = ks + probe_every;
+        int sl = -1;
+        if (target->farkas_from(*s, &sl)) {
+          *certified = 1;
+          *slice = sl;
+          s->stop_at_last_check();
+          if (run_r) rival->stop_at_last_check();
+          break;
+        }
+      }
+      run_s = !done && ks < Ms;
+    }
+  }
+}
+
+int sipo_solve_race(sipo_ctx* ctx, sipo_ctx* target, sipo_ctx* rival, long long probe_every, sipo_result* res,
+                    sipo_result* rival_res, int* certified, int* slice) {
+  SIPO_TRY
+  if (!ctx || !target || !rival || !res || !rival_res || !certified || !slice)
+    sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
+  if (ctx == target || ctx == rival || target == rival)
+    sipo::fail(SIPO_ERR_INVALID_ARG, "race: the solved, the tested and the rival context must be distinct");
+  if (probe_every <= 0) sipo::fail(SIPO_ERR_INVALID_ARG, "probe_every must be positive");
+  if (ctx->c.s->dev() != rival->c.s->dev())
+    sipo::fail(SIPO_ERR_INVALID_ARG, "race: the solved and the rival context are on different devices");
+  run_solve_race(ctx->c.s.get(), target->c.s.get(), rival->c.s.get(), probe_every, certified, slice);
+  ctx->c.s->finish_solve(nullptr, SIPO_DEVICE, res);
+  rival->c.s->finish_solve(nullptr, SIPO_DEVICE, rival_res);
+  return SIPO_OK;
+  SIPO_CATCH
+}
+
 int sipo_solve(sipo_ctx* ctx, void* y_out, int y_location, sipo_result* res) {
   SIPO_TRY
   if (!ctx || !res) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");

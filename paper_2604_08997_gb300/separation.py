@@ -12,42 +12,61 @@ it is always feasible and bounded and the PDHG converges on it where the
 Case-2 iterates of an infeasible ratio only drift.
 
 The workflow solves it while testing, every `probe_every` iterations, its
-current dual point as a Farkas ray of Case 2 at r (sipo_solve_probe runs the
-library's bound-based test, slice by slice where the PSF allows).  A ray is a
+current dual point as a Farkas ray of Case 2 at r (the library's bound-based
+test, slice by slice where the PSF allows).  A ray is a
 certificate by itself, whatever the accuracy of the iterate that gave it, so
 the first one that passes ends the workflow with PRIMAL_INFEASIBLE.  Passing
 duals can come and go between restarts (on the blurred 256^3 part one passes
 at iteration 1280 and none at 2048 or 3072), so the probes are frequent: every
-128 iterations by default, each about one projection.  If the
-separation LP ends instead with u~ <= r, its primal point over r satisfies
+128 iterations by default, each about one projection.  In the sequential
+form, if the separation LP ends instead with u~ <= r, its primal point over r satisfies
 every Case-2 row (up to its primal residual) and starts the Case-2 solve
 (sipo_set_primal_from), as the two-stage design of Sec. 3.2 does with a
-Case-1 point; otherwise Case 2 runs from zero.  Host orchestration only: every step runs in libsipo.
+Case-1 point; otherwise Case 2 runs from zero.
+
+That sequence (race=False) is slow where r is feasible: on the 256^3 part at
+r = 0.85 the separation LP had not reached KKT 1e-4 after 16384 iterations,
+and Case 2 started from its scaled point had not after 2048, where from zero
+it does in 1344 (26 s in all, against 1.9 s for Case 2 alone).  So by
+default (race=True) Case 2 itself is solved at the same time as the
+separation LP, on a stream of its own (sipo_solve_race): a feasible r ends
+with the Case-2 optimum, an infeasible one with the first certificate of the
+probes, whichever comes first.  Host orchestration only: every step runs in
+libsipo.
 """
 from __future__ import annotations
 
-from ._abi import (SIPO_CASE1, SIPO_CASE2, SIPO_OPTIMAL, SIPO_PRIMAL_INFEASIBLE, sipo_create, sipo_destroy,
-                   sipo_set_primal_from, sipo_solve, sipo_solve_probe)
+from ._abi import (SIPO_CASE1, SIPO_CASE2, SIPO_PRIMAL_INFEASIBLE, sipo_create, sipo_destroy,
+                   sipo_set_primal_from, sipo_solve, sipo_solve_probe, sipo_solve_race)
 
 
 def case2_with_separation(geometry: dict, f_T, ratio: float, band_width: int = 10,
                           tolerances: dict | None = None, separation_tolerances: dict | None = None,
-                          probe_every: int = 128, tol_hi: float = 10.0) -> dict:
+                          probe_every: int = 128, tol_hi: float = 10.0, race: bool = True) -> dict:
     """Case 2 at inhibition ratio `ratio`, preceded by the separation LP.
 
     Returns {"separation": result of the separation LP, "ratio_bound": its
     u~ (the best band-to-gel ratio found), "certified": bool, "cert_slice":
-    int, "case2": result of the Case-2 solve or None, "status": the Case-2
-    status (SIPO_PRIMAL_INFEASIBLE when certified)}.  `separation_tolerances`
-    defaults to `tolerances`.
+    int, "case2": result of the Case-2 solve (None when the sequential
+    form certified first), "status": the Case-2 status (SIPO_PRIMAL_INFEASIBLE
+    when certified)}.  `separation_tolerances` defaults to `tolerances`;
+    `race` picks the concurrent form (True) or the sequential one.
     """
     tol = dict(tolerances or {})
     tol_sep = dict(separation_tolerances if separation_tolerances is not None else tol)
     sep = sipo_create(geometry, f_T, dict(kase=SIPO_CASE1, tol_lo=0.0, tol_hi=tol_hi, band_width=band_width),
                       tol_sep)
-    ctx2 = None
+    ctx2 = rival = None
+    case2 = dict(kase=SIPO_CASE2, inhibit_ratio=ratio, band_width=band_width)
     try:
-        ctx2 = sipo_create(geometry, f_T, dict(kase=SIPO_CASE2, inhibit_ratio=ratio, band_width=band_width), tol)
+        ctx2 = sipo_create(geometry, f_T, case2, tol)
+        if race:
+            # a probe resets its target's solver state: the solved Case 2 is a
+            # context of its own
+            rival = sipo_create(geometry, f_T, case2, tol)
+            rs, r2, cert, sl = sipo_solve_race(sep, ctx2, rival, probe_every)
+            return {"separation": rs, "ratio_bound": rs["pobj"], "certified": cert, "cert_slice": sl,
+                    "case2": r2, "status": SIPO_PRIMAL_INFEASIBLE if cert else r2["status"]}
         rs, cert, sl = sipo_solve_probe(sep, ctx2, probe_every)
         out = {"separation": rs, "ratio_bound": rs["pobj"], "certified": cert, "cert_slice": sl,
                "case2": None, "status": None}
@@ -63,5 +82,6 @@ def case2_with_separation(geometry: dict, f_T, ratio: float, band_width: int = 1
         return out
     finally:
         sipo_destroy(sep)
-        if ctx2 is not None:
-            sipo_destroy(ctx2)
+        for c in (ctx2, rival):
+            if c is not None:
+                sipo_destroy(c)

@@ -705,7 +705,7 @@ def test_batched_sweep_invariants(sipo):
 
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 def test_case2_with_separation_certifies_or_starts(sipo, storage):
-    """The separation LP (Case 1 of the part with tol_lo = 0, tol_hi = 10) on
+    """Sequential form.  The separation LP (Case 1 of the part with tol_lo = 0, tol_hi = 10) on
     the 16-slice stack, probed as a Farkas ray of Case 2 at r = 0.62: with the
     infeasible slice the probe proves Case 2 infeasible on slice 8; without it
     the separation LP converges to HiGHS's optimum (below r) and Case 2 started
@@ -716,7 +716,7 @@ def test_case2_with_separation_certifies_or_starts(sipo, storage):
     tol = dict(storage=st, kkt_tol=1e-8 if storage == "f64" else 1e-5, max_iter=100000)
     for bad in (8, None):
         lp, ops, geo, tgt, cp = _slice_stack(16, bad)
-        out = case2_with_separation(geo, tgt, 0.62, band_width=2, tolerances=tol, probe_every=256)
+        out = case2_with_separation(geo, tgt, 0.62, band_width=2, tolerances=tol, probe_every=256, race=False)
         if bad is not None:
             assert out["status"] == sipo.SIPO_PRIMAL_INFEASIBLE and out["certified"], out
             assert out["cert_slice"] == bad
@@ -730,3 +730,42 @@ def test_case2_with_separation_certifies_or_starts(sipo, storage):
             ref2 = pdhg.solve(lp, ops, kkt_tol=1e-8, max_iter=100000)
             assert ref2["status"] == pdhg.OPTIMAL and out["status"] == sipo.SIPO_OPTIMAL
             assert out["case2"]["pobj"] == pytest.approx(ref2["obj"], rel=1e-7 if storage == "f64" else 1e-4)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_case2_race_decides_both_ways(sipo, storage):
+    """Concurrent form on the 16-slice stack at r = 0.62: with the infeasible
+    slice 8 the workflow ends PRIMAL_INFEASIBLE, by a probe certificate that
+    names slice 8 or by the Case-2 solve's own certificate (slice 8, or the
+    whole volume); without it the Case-2 solve ends OPTIMAL at the oracle
+    optimum, no probe certifies, and the separation solve is stopped there
+    (ITER_LIMIT) unless it reached its own optimum first.  Equal or repeated
+    contexts are refused."""
+    from paper_2604_08997_gb300 import case2_with_separation
+    st = sipo.SIPO_F64 if storage == "f64" else sipo.SIPO_F32
+    tol = dict(storage=st, kkt_tol=1e-8 if storage == "f64" else 1e-5, max_iter=100000)
+    lp, ops, geo, tgt, cp = _slice_stack(16, 8)
+    out = case2_with_separation(geo, tgt, 0.62, band_width=2, tolerances=tol, probe_every=256)
+    assert out["status"] == sipo.SIPO_PRIMAL_INFEASIBLE, out
+    if out["certified"]:
+        assert out["cert_slice"] == 8 and out["case2"]["status"] == sipo.SIPO_ITER_LIMIT
+    else:
+        assert out["case2"]["status"] == sipo.SIPO_PRIMAL_INFEASIBLE
+        assert out["case2"]["cert_slice"] in (8, -1)
+    lp, ops, geo, tgt, cp = _slice_stack(16, None)
+    out = case2_with_separation(geo, tgt, 0.62, band_width=2, tolerances=tol, probe_every=256)
+    ref2 = pdhg.solve(lp, ops, kkt_tol=1e-8, max_iter=100000)
+    assert ref2["status"] == pdhg.OPTIMAL
+    assert out["status"] == sipo.SIPO_OPTIMAL and not out["certified"], out
+    assert out["separation"]["status"] in (sipo.SIPO_ITER_LIMIT, sipo.SIPO_OPTIMAL)
+    assert out["case2"]["pobj"] == pytest.approx(ref2["obj"], rel=1e-7 if storage == "f64" else 1e-4)
+    a = sipo.sipo_create(geo, tgt, dict(kase=1, tol_lo=0.0, tol_hi=10.0, band_width=2), tol)
+    b = sipo.sipo_create(geo, tgt, cp, tol)
+    c = sipo.sipo_create(geo, tgt, cp, tol)
+    for args in ((a, a, c), (a, b, a), (a, b, b)):
+        with pytest.raises(sipo.SipoError):
+            sipo.sipo_solve_race(*args, 128)
+    with pytest.raises(sipo.SipoError):
+        sipo.sipo_solve_race(a, b, c, 0)
+    for x in (a, b, c):
+        sipo.sipo_destroy(x)
