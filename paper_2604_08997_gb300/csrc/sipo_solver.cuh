@@ -183,6 +183,8 @@ __device__ __forceinline__ void dual_update(const Bufs<S, C>& b, const StepScala
   const C w = sc.w;
   C o_lu[ZL], o_ll[ZL], o_q[ZL], o_d[ZL];
   C dcur[ZL], d0[ZL];
+  C acc[CHECK ? kCheckSlots : 1] = {};
+  (void)acc;
   if constexpr (CHECK) load_z<C, C, ZL>(b.d + base, dcur);
   else load_z<C, C, ZL>(b.d0 + base, d0);
 #pragma unroll
@@ -218,45 +220,57 @@ __device__ __forceinline__ void dual_update(const Bufs<S, C>& b, const StepScala
       if (band) red[0] += double(lun);
       else red[1] += double(f) * double(lun);
     } else {
+      // the check sums of one z-vector in the compute type, folded into the
+      // FP64 accumulators once per vector below (in FP32 a sum of ZL terms
+      // is exact to ~ZL ulp; FP64 arithmetic per voxel is slow on this part)
       const C dp = C(0.5) * (dbar[i] + dcur[i]);
       o_lu[i] = lup;
       o_ll[i] = llp;
       o_q[i] = lup - llp;
       o_d[i] = dp;
       const C Ucur = band ? (b.has_u ? sc.up : b.band_rhs) : (b.has_v ? sc.vp * f : fU);
-      const double eu = double(dp) > double(Ucur) ? double(dp) - double(Ucur) : 0.0;
-      red[0] += eu * eu;
-      if (rup > C(0)) red[1] += eu * eu / double(rup);
-      const double dlu = double(lup) - double(lu0[i]);
-      red[6] += double(rup) * (double(lu[i]) - double(lup)) * (double(lu[i]) - double(lup));
-      red[7] += double(rup) * dlu * dlu;
-      red[12] = fmax(red[12], -dlu);
+      const C eu = dp > Ucur ? dp - Ucur : C(0);
+      acc[0] += eu * eu;
+      if (rup > C(0)) acc[1] += eu * eu / rup;
+      const C dlu = lup - lu0[i];
+      const C du = lu[i] - lup;
+      acc[6] += rup * du * du;
+      acc[7] += rup * dlu * dlu;
+      acc[12] = acc[12] > -dlu ? acc[12] : -dlu;
       if (band) {
-        red[4] += double(lup);
-        red[9] += dlu;
+        acc[4] += lup;
+        acc[9] += dlu;
       } else {
-        const double el = double(f) > double(dp) ? double(f) - double(dp) : 0.0;
-        red[0] += el * el;
-        if (row[i] > C(0)) red[1] += el * el / double(row[i]);
-        const double dll = double(llp) - double(ll0[i]);
-        red[2] += double(f) * double(llp);
-        red[3] += double(fU) * double(lup);
-        red[5] += double(f) * double(lup);
-        red[6] += double(row[i]) * (double(ll[i]) - double(llp)) * (double(ll[i]) - double(llp));
-        red[7] += double(row[i]) * dll * dll;
-        red[8] += double(f) * dll;
-        red[10] += double(f) * dlu;
-        red[11] += double(fU) * dlu;
-        red[12] = fmax(red[12], -dll);
-        const double rl = double(llp) - double(ll[i]);
-        red[13] += double(f) * rl;
-        red[15] += double(f) * (double(lup) - double(lu[i]));
-        red[16] += double(fU) * (double(lup) - double(lu[i]));
-        red[17] = fmax(red[17], -rl);
+        const C el = f > dp ? f - dp : C(0);
+        acc[0] += el * el;
+        if (row[i] > C(0)) acc[1] += el * el / row[i];
+        const C dll = llp - ll0[i];
+        const C dl = ll[i] - llp;
+        acc[2] += f * llp;
+        acc[3] += fU * lup;
+        acc[5] += f * lup;
+        acc[6] += row[i] * dl * dl;
+        acc[7] += row[i] * dll * dll;
+        acc[8] += f * dll;
+        acc[10] += f * dlu;
+        acc[11] += fU * dlu;
+        acc[12] = acc[12] > -dll ? acc[12] : -dll;
+        const C rl = llp - ll[i];
+        acc[13] += f * rl;
+        acc[15] += f * (lup - lu[i]);
+        acc[16] += fU * (lup - lu[i]);
+        acc[17] = acc[17] > -rl ? acc[17] : -rl;
       }
-      const double ru = double(lup) - double(lu[i]);
-      if (band) red[14] += ru;
-      red[17] = fmax(red[17], -ru);
+      const C ru = lup - lu[i];
+      if (band) acc[14] += ru;
+      acc[17] = acc[17] > -ru ? acc[17] : -ru;
+    }
+  }
+  if constexpr (CHECK) {
+#pragma unroll
+    for (int j = 0; j < kCheckSlots; ++j) {
+      if ((kCheckMaxMask >> j) & 1u) red[j] = fmax(red[j], double(acc[j]));
+      else red[j] += double(acc[j]);
     }
   }
   if constexpr (!CHECK) {
@@ -322,8 +336,9 @@ __device__ __forceinline__ void cert_update(const Bufs<S, C>& b, size_t base, co
 #pragma unroll
   for (int i = 0; i < ZL; ++i) {
     if (col[i] > C(0) && g[i] < C(0)) {
-      const double v = -double(g[i]);
-      red[0] = fmax(red[0], bb[i] > C(0) ? v / double(bb[i]) : CUDART_INF);
+      // the ratio in the compute type (its rounding is far inside the
+      // certificate's relative margin; FP64 division is slow on this part)
+      red[0] = fmax(red[0], bb[i] > C(0) ? double(-g[i] / bb[i]) : CUDART_INF);
     }
   }
 }
@@ -341,7 +356,7 @@ __device__ __forceinline__ void cert_update_z(const Bufs<S, C>& b, size_t base, 
 #pragma unroll
   for (int i = 0; i < ZL; ++i) {
     if (col[i] > C(0) && g[i] < C(0)) {
-      const double v = bb[i] > C(0) ? -double(g[i]) / double(bb[i]) : CUDART_INF;
+      const double v = bb[i] > C(0) ? double(-g[i] / bb[i]) : CUDART_INF;
       atomicMax(kz + z0 + z_offset<C, ZL>(i), (unsigned long long)__double_as_longlong(v));
     }
   }
@@ -355,16 +370,24 @@ __device__ __forceinline__ void resid_update(const Bufs<S, C>& b, size_t base, c
   load_z<C, C, ZL>(b.col + base, col);
   load_z<C, C, ZL>(b.g0 + base, g0);
   load_z<C, C, ZL>(b.gc + base, gc);
+  // sums of one z-vector in the compute type, folded into FP64 once per
+  // vector (as in the check-step dual update)
+  C a0 = C(0), a1 = C(0), a2 = -CUDART_INF_F, a3 = -CUDART_INF_F;
 #pragma unroll
   for (int i = 0; i < ZL; ++i) {
     if (col[i] > C(0)) {
-      const double m = g[i] < C(0) ? double(g[i]) : 0.0;
-      red[0] += m * m;
-      red[1] += m * m / double(col[i]);
-      red[2] = fmax(red[2], double(g0[i]) - double(g[i]));
-      red[3] = fmax(red[3], double(gc[i]) - double(g[i]));
+      const C m = g[i] < C(0) ? g[i] : C(0);
+      a0 += m * m;
+      a1 += m * m / col[i];
+      const C d0 = g0[i] - g[i], dc = gc[i] - g[i];
+      a2 = a2 > d0 ? a2 : d0;
+      a3 = a3 > dc ? a3 : dc;
     }
   }
+  red[0] += double(a0);
+  red[1] += double(a1);
+  red[2] = fmax(red[2], double(a2));
+  red[3] = fmax(red[3], double(a3));
   store_z<C, C, ZL>(b.gp + base, g);
 }
 
