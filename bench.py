@@ -60,8 +60,8 @@ def sm_max_mhz(peaks: dict) -> float:
 # the code it is null until re-captured.
 KERNEL_SOURCES = ["sipo_device.cuh", "sipo_solver.cuh", "sipo_ops.cuh", "sipo_launch.h",
                   "sipo_project.cu", "sipo_backproject.cu", "sipo_bp_tma.cuh"]
-TRAFFIC = {("csg256", "f32"): {"sources_sha256_16": "d1c8050036cca9ee",
-                               "project": 278943488, "backproject": 222946048}}
+TRAFFIC = {("csg256", "f32"): {"sources_sha256_16": "b793cafb01817e69",
+                               "project": 278965120, "backproject": 228099328}}
 
 
 def _code_only(text: str) -> str:

@@ -346,7 +346,8 @@ int sipo_farkas_from(sipo_ctx *ctx, const sipo_ctx *src, int *certified, int *sl
  * state sipo_get_state exports, are then the check whose dual passed).  For the separation solve of
  * Case 2: ctx holds the same part as Case 1 with tol_lo = 0 (gel dose at least
  * its target, band dose at most u~), target the Case-2 LP.  Errors: as
- * sipo_solve and sipo_farkas_from. */
+ * sipo_solve and sipo_farkas_from (a target whose LP cannot test ctx's duals
+ * is refused before any iteration runs). */
 int sipo_solve_probe(sipo_ctx *ctx, sipo_ctx *target, long long probe_every, sipo_result *res, int *certified,
                      int *slice);
 
@@ -365,7 +366,8 @@ int sipo_solve_probe(sipo_ctx *ctx, sipo_ctx *target, long long probe_every, sip
  * probe resets target's solver state); a feasible r ends with the rival's
  * optimum, an infeasible one with the separation dual's certificate.  The
  * three contexts must be distinct, ctx and rival on one device.  Errors: as
- * sipo_solve and sipo_farkas_from. */
+ * sipo_solve and sipo_farkas_from (a target whose LP cannot test ctx's duals
+ * is refused before any iteration runs). */
 int sipo_solve_race(sipo_ctx *ctx, sipo_ctx *target, sipo_ctx *rival, long long probe_every, sipo_result *res,
                     sipo_result *rival_res, int *certified, int *slice);
 

@@ -106,6 +106,8 @@ struct SolverBase {
   // tests src's last returned dual point as a Farkas ray of this LP (bound-based
   // test); returns 1 if it proves infeasibility, with the slice in *slice
   virtual int farkas_from(const SolverBase& src, int* slice) = 0;
+  // throws INVALID_ARG where src's duals cannot be tested against this LP
+  virtual void farkas_compatible(const SolverBase& src) const = 0;
   virtual std::vector<double> label_counts() const = 0;
   virtual std::vector<double> geometry_fingerprint() const = 0;
   // the point T(z) of the last check: y, lam_up, lam_lo (compute type) and u~, v~, omega, k
@@ -412,10 +414,14 @@ struct Solver final : SolverBase {
   // the general form with w2 = 0 whose optimum u~* is the best achievable
   // band-to-gel ratio: its optimal dual, tested in Case 2 at a ratio below u~*,
   // is a Farkas ray.  Resets this context's solver state.
-  int farkas_from(const SolverBase& src, int* slice) override {
+  void farkas_compatible(const SolverBase& src) const override {
     if (src.geometry_fingerprint() != geometry_fingerprint() || src.label_counts() != label_counts())
       fail(SIPO_ERR_INVALID_ARG, "Farkas test: the contexts differ in geometry, device or labels");
     if (!cert_on) fail(SIPO_ERR_INVALID_ARG, "Farkas test: the general form has no bound-based certificate");
+  }
+
+  int farkas_from(const SolverBase& src, int* slice) override {
+    farkas_compatible(src);
     ck(cudaStreamSynchronize(src.strm()), "Farkas test: source");
     const Point pt = src.point();
     if (pt.st.k <= 0 && pt.st.done == 0)
@@ -1729,6 +1735,7 @@ int sipo_solve_probe(sipo_ctx* ctx, sipo_ctx* target, long long probe_every, sip
   if (!ctx || !target || !res || !certified || !slice) sipo::fail(SIPO_ERR_INVALID_ARG, "null argument");
   if (ctx == target) sipo::fail(SIPO_ERR_INVALID_ARG, "probe: the solved and the tested context are the same");
   if (probe_every <= 0) sipo::fail(SIPO_ERR_INVALID_ARG, "probe_every must be positive");
+  target->c.s->farkas_compatible(*ctx->c.s);  // refused before any iteration runs
   run_solve_probe(ctx->c.s.get(), target->c.s.get(), probe_every, certified, slice);
   ctx->c.s->finish_solve(nullptr, SIPO_DEVICE, res);
   return SIPO_OK;
@@ -1795,6 +1802,7 @@ int sipo_solve_race(sipo_ctx* ctx, sipo_ctx* target, sipo_ctx* rival, long long 
   if (probe_every <= 0) sipo::fail(SIPO_ERR_INVALID_ARG, "probe_every must be positive");
   if (ctx->c.s->dev() != rival->c.s->dev())
     sipo::fail(SIPO_ERR_INVALID_ARG, "race: the solved and the rival context are on different devices");
+  target->c.s->farkas_compatible(*ctx->c.s);
   run_solve_race(ctx->c.s.get(), target->c.s.get(), rival->c.s.get(), probe_every, certified, slice);
   ctx->c.s->finish_solve(nullptr, SIPO_DEVICE, res);
   rival->c.s->finish_solve(nullptr, SIPO_DEVICE, rival_res);

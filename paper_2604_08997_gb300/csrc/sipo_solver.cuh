@@ -183,8 +183,10 @@ __device__ __forceinline__ void dual_update(const Bufs<S, C>& b, const StepScala
   const C w = sc.w;
   C o_lu[ZL], o_ll[ZL], o_q[ZL], o_d[ZL];
   C dcur[ZL], d0[ZL];
-  C acc[CHECK ? kCheckSlots : 1] = {};
-  (void)acc;
+  // sums of this z-vector in the compute type, added to the FP64
+  // accumulators once per vector below (in FP32 a sum of ZL terms is within
+  // ~ZL ulp; FP64 arithmetic per voxel is slow on this part)
+  C acc[CHECK ? kCheckSlots : 2] = {};
   if constexpr (CHECK) load_z<C, C, ZL>(b.d + base, dcur);
   else load_z<C, C, ZL>(b.d0 + base, d0);
 #pragma unroll
@@ -217,12 +219,9 @@ __device__ __forceinline__ void dual_update(const Bufs<S, C>& b, const StepScala
       o_ll[i] = lln;
       o_q[i] = lun - lln;
       o_d[i] = w * dbar[i] + (C(1) - w) * d0[i];
-      if (band) red[0] += double(lun);
-      else red[1] += double(f) * double(lun);
+      if (band) acc[0] += lun;
+      else acc[1] += f * lun;
     } else {
-      // the check sums of one z-vector in the compute type, folded into the
-      // FP64 accumulators once per vector below (in FP32 a sum of ZL terms
-      // is exact to ~ZL ulp; FP64 arithmetic per voxel is slow on this part)
       const C dp = C(0.5) * (dbar[i] + dcur[i]);
       o_lu[i] = lup;
       o_ll[i] = llp;
@@ -272,6 +271,9 @@ __device__ __forceinline__ void dual_update(const Bufs<S, C>& b, const StepScala
       if ((kCheckMaxMask >> j) & 1u) red[j] = fmax(red[j], double(acc[j]));
       else red[j] += double(acc[j]);
     }
+  } else {
+    red[0] += double(acc[0]);
+    red[1] += double(acc[1]);
   }
   if constexpr (!CHECK) {
     store_z<S, C, ZL>(b.lu + base, o_lu);
@@ -301,6 +303,7 @@ __device__ __forceinline__ void primal_update(const Bufs<S, C>& b, const StepSca
   load_z<S, C, ZL>(b.y + base, y);
   load_z<S, C, ZL>(b.y0 + base, y0);
   const C w = sc.w;
+  C a0 = C(0), a1 = C(0);  // restart distances of this z-vector (compute type)
 #pragma unroll
   for (int i = 0; i < ZL; ++i) {
     const C tau = col[i] > C(0) ? C(kEta) / (sc.omega * col[i]) : C(0);
@@ -311,11 +314,14 @@ __device__ __forceinline__ void primal_update(const Bufs<S, C>& b, const StepSca
       yo[i] = w * yb[i] + (C(1) - w) * y0[i];
     } else {
       yo[i] = yp;
-      const double dx = double(y[i]) - double(yp), dz = double(yp) - double(y0[i]);
-      (void)dz;
-      red[0] += double(col[i]) * dx * dx;
-      red[1] += double(col[i]) * dz * dz;
+      const C dx = y[i] - yp, dz = yp - y0[i];
+      a0 += col[i] * dx * dx;
+      a1 += col[i] * dz * dz;
     }
+  }
+  if constexpr (CHECK) {
+    red[0] += double(a0);
+    red[1] += double(a1);
   }
   store_z<S, C, ZL>(b.ybar + base, yb);
   if constexpr (!CHECK) {

@@ -740,7 +740,8 @@ def test_case2_race_decides_both_ways(sipo, storage):
     whole volume); without it the Case-2 solve ends OPTIMAL at the oracle
     optimum, no probe certifies, and the separation solve is stopped there
     (ITER_LIMIT) unless it reached its own optimum first.  Equal or repeated
-    contexts are refused."""
+    contexts, and targets that cannot test the separation duals, are
+    refused."""
     from paper_2604_08997_gb300 import case2_with_separation
     st = sipo.SIPO_F64 if storage == "f64" else sipo.SIPO_F32
     tol = dict(storage=st, kkt_tol=1e-8 if storage == "f64" else 1e-5, max_iter=100000)
@@ -767,5 +768,15 @@ def test_case2_race_decides_both_ways(sipo, storage):
             sipo.sipo_solve_race(*args, 128)
     with pytest.raises(sipo.SipoError):
         sipo.sipo_solve_race(a, b, c, 0)
-    for x in (a, b, c):
+    # targets whose LP cannot test the separation duals: another geometry,
+    # and the general form (no bound-based certificate); refused up front
+    lp8, ops8, geo8, tgt8, cp8 = _slice_stack(8, None)
+    other = sipo.sipo_create(geo8, tgt8, cp8, tol)
+    general = sipo.sipo_create(geo, tgt, dict(kase=0, w1=1.0, w2=1.0, band_width=2), tol)
+    for t in (other, general):
+        with pytest.raises(sipo.SipoError):
+            sipo.sipo_solve_race(a, t, c, 128)
+        with pytest.raises(sipo.SipoError):
+            sipo.sipo_solve_probe(a, t, 128)
+    for x in (a, b, c, other, general):
         sipo.sipo_destroy(x)
