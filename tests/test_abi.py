@@ -128,6 +128,22 @@ def test_new_entries_validate_before_device_work(lib):
     fake = ctypes.c_void_p(1)
     assert lib.sipo_set_primal_from(fake, fake, 1.0, -1.0, -1.0) == -1
     assert b"same context" in lib.sipo_last_error()
+    # probe and race: null, repeated contexts and a non-positive probe period
+    # are refused on the pointers alone
+    res, res2 = _abi.sipo_result(), _abi.sipo_result()
+    cert, sl = ctypes.c_int(0), ctypes.c_int(0)
+    a, b, c = ctypes.c_void_p(1), ctypes.c_void_p(2), ctypes.c_void_p(3)
+    refs = (ctypes.byref(res), ctypes.byref(cert), ctypes.byref(sl))
+    assert lib.sipo_solve_probe(None, b, 128, *refs) == -1 and b"null" in lib.sipo_last_error()
+    assert lib.sipo_solve_probe(a, a, 128, *refs) == -1 and b"same" in lib.sipo_last_error()
+    assert lib.sipo_solve_probe(a, b, 0, *refs) == -1 and b"probe_every" in lib.sipo_last_error()
+    rrefs = (ctypes.byref(res), ctypes.byref(res2), ctypes.byref(cert), ctypes.byref(sl))
+    assert lib.sipo_solve_race(a, b, None, 128, *rrefs) == -1 and b"null" in lib.sipo_last_error()
+    assert lib.sipo_solve_race(a, b, c, 128, ctypes.byref(res), None, ctypes.byref(cert),
+                               ctypes.byref(sl)) == -1
+    for x, y, z in ((a, a, c), (a, b, a), (a, b, b)):
+        assert lib.sipo_solve_race(x, y, z, 128, *rrefs) == -1 and b"distinct" in lib.sipo_last_error()
+    assert lib.sipo_solve_race(a, b, c, 0, *rrefs) == -1 and b"probe_every" in lib.sipo_last_error()
     n_out = ctypes.c_uint(7)
     for budget, threads, outp in ((0, 32, ctypes.byref(n_out)), (1000, 0, ctypes.byref(n_out)),
                                   (1000, 1025, ctypes.byref(n_out)), (1000, 32, None)):
