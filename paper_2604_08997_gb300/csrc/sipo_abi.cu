@@ -27,6 +27,7 @@
 #include "sipo_ops.cuh"
 #include "sipo_psf.cuh"
 #include "sipo_response.cuh"
+#include "sipo_schedule.h"
 
 namespace sipo {
 namespace {
@@ -1701,32 +1702,11 @@ static void run_solve(sipo::SolverBase* s) {
 
 // run_solve that, every `probe_every` iterations (rounded up to check periods)
 // and when the solve stops, tests the last check's dual point as a Farkas ray
-// of `target`'s LP; stops at the first certificate.
+// of `target`'s LP; stops at the first certificate (sipo_schedule.h).
 static void run_solve_probe(sipo::SolverBase* s, sipo::SolverBase* target, long long probe_every, int* certified,
                             int* slice) {
-  s->begin_solve();
-  const long long P = s->period(), M = s->max_iter();
-  long long k = 0, next_probe = probe_every;
-  *certified = 0;
-  *slice = -1;
-  while (k < M) {
-    const long long n = std::min(P, M - k);
-    s->launch_block(n);
-    k += n;
-    s->request_done();
-    const bool done = s->done_flag();
-    if (k >= next_probe || done || k >= M) {
-      next_probe = k + probe_every;
-      int sl = -1;
-      if (target->farkas_from(*s, &sl)) {
-        *certified = 1;
-        *slice = sl;
-        s->stop_at_last_check();  // the returned and exported point is the certified dual's check
-        break;
-      }
-    }
-    if (done) break;
-  }
+  sipo::probe_schedule(*s, static_cast<sipo::SolverBase*>(nullptr), probe_every,
+                       [&](int* sl) { return target->farkas_from(*s, sl) != 0; }, certified, slice);
 }
 
 int sipo_solve_probe(sipo_ctx* ctx, sipo_ctx* target, long long probe_every, sipo_result* res, int* certified,
@@ -1744,52 +1724,11 @@ int sipo_solve_probe(sipo_ctx* ctx, sipo_ctx* target, long long probe_every, sip
 
 // run_solve_probe of s with a second solve, `rival`, advanced on its own
 // stream at the same time: each round launches one check period of every
-// context still running, then reads both states.  A context stops running at
-// its own decision (done flag) or iteration cap; the call ends at the first
-// probe certificate (rival stopped at its last check), at the rival's own
-// decision (s stopped at its last check), or when neither runs any more.
+// context still running, then reads both states (sipo_schedule.h).
 static void run_solve_race(sipo::SolverBase* s, sipo::SolverBase* target, sipo::SolverBase* rival,
                            long long probe_every, int* certified, int* slice) {
-  s->begin_solve();
-  rival->begin_solve();
-  const long long Ps = s->period(), Ms = s->max_iter();
-  const long long Pr = rival->period(), Mr = rival->max_iter();
-  long long ks = 0, kr = 0, next_probe = probe_every;
-  bool run_s = ks < Ms, run_r = kr < Mr;
-  *certified = 0;
-  *slice = -1;
-  while (run_s || run_r) {
-    long long ns = 0, nr = 0;
-    if (run_s) { ns = std::min(Ps, Ms - ks); s->launch_block(ns); }
-    if (run_r) { nr = std::min(Pr, Mr - kr); rival->launch_block(nr); }
-    if (run_s) s->request_done();
-    if (run_r) rival->request_done();
-    ks += ns;
-    kr += nr;
-    if (run_r) {
-      if (rival->done_flag()) {
-        // the rival decided its LP: the separation solve is not needed further
-        if (run_s) s->stop_at_last_check();
-        break;
-      }
-      run_r = kr < Mr;
-    }
-    if (run_s) {
-      const bool done = s->done_flag();
-      if (ks >= next_probe || done || ks >= Ms) {
-        next_probe = ks + probe_every;
-        int sl = -1;
-        if (target->farkas_from(*s, &sl)) {
-          *certified = 1;
-          *slice = sl;
-          s->stop_at_last_check();
-          if (run_r) rival->stop_at_last_check();
-          break;
-        }
-      }
-      run_s = !done && ks < Ms;
-    }
-  }
+  sipo::probe_schedule(*s, rival, probe_every, [&](int* sl) { return target->farkas_from(*s, sl) != 0; },
+                       certified, slice);
 }
 
 int sipo_solve_race(sipo_ctx* ctx, sipo_ctx* target, sipo_ctx* rival, long long probe_every, sipo_result* res,
