@@ -129,3 +129,20 @@ def test_contexts_released_when_creation_fails(monkeypatch):
     else:
         raise AssertionError("creation failure not raised")
     assert sorted(f.destroyed) == [0, 1]
+
+
+def test_contexts_released_when_the_race_fails(monkeypatch):
+    f = Fake(bound=0.7)
+
+    def race(ctx, target, rival, probe_every=1024):
+        raise RuntimeError("sipo error -5: non-finite iterates")
+
+    for name, fn in (("sipo_create", f.create), ("sipo_solve_race", race), ("sipo_destroy", f.destroy)):
+        monkeypatch.setattr(separation, name, fn)
+    try:
+        separation.case2_with_separation({}, None, 0.8)
+    except RuntimeError:
+        pass
+    else:
+        raise AssertionError("race failure not raised")
+    assert sorted(f.destroyed) == [0, 1, 2]
